@@ -1,0 +1,60 @@
+"""Synthetic workloads: seeded, valid seed tuples, and the documented shapes."""
+import numpy as np
+
+import synth
+
+
+def _seeds_exact(b, n=500):
+    p = b.pairs.astype(np.int64)
+    for r in p[:n]:
+        h = b.codes[b.offsets[r[0]]:b.offsets[r[0]] + b.lengths[r[0]]]
+        v = b.codes[b.offsets[r[1]]:b.offsets[r[1]] + b.lengths[r[1]]]
+        k = r[4]
+        assert r[2] + k <= len(h) and r[3] + k <= len(v)
+        assert np.array_equal(h[r[2]:r[2] + k], v[r[3]:r[3] + k])
+
+
+def test_dna_tiny_shape_and_determinism():
+    b = synth.dna_tiny()
+    assert b.n_pairs == 1000 and b.X == 15 and b.alphabet == "dna"
+    h_len = b.lengths[0::2]
+    assert h_len.min() >= 1000 and h_len.max() <= 5000
+    assert b.codes.max() < 4
+    _seeds_exact(b)
+    assert synth.dna_tiny().digest() == b.digest()
+    assert synth.dna_tiny(seed=1).digest() != b.digest()
+
+
+def test_longread_and_protein_small():
+    b = synth.dna_longread(n_pairs=2000)
+    assert b.lengths.min() >= 17 and b.lengths.max() <= 60000
+    _seeds_exact(b)
+    p = synth.protein(n_pairs=5000)
+    assert p.codes.max() < 20 and p.gap == -2 and p.X == 49 and p.matrix.shape == (20, 20)
+    _seeds_exact(p)
+    u = synth.uneven(n_pairs=300, delta=256)
+    assert u.delta == 256
+    _seeds_exact(u)
+
+
+def test_blosum62_invariants():
+    m = synth.BLOSUM62.astype(int)
+    assert m.shape == (20, 20) and (m == m.T).all()
+    assert m.min() >= -4 and m.max() <= 11
+    d = np.diag(m)
+    assert (d > 0).all()
+    for a in range(20):
+        assert all(d[a] > m[a, b] for b in range(20) if b != a)
+    assert abs(synth.BACKGROUND.sum() - 1) < 1e-12
+
+
+def test_subset_roundtrip():
+    b = synth.dna_tiny(n_pairs=50)
+    s = b.subset([3, 7, 11])
+    assert s.n_pairs == 3
+    for new, old in enumerate([3, 7, 11]):
+        for side in (0, 1):
+            o = b.pairs[old, side]
+            n_ = s.pairs[new, side]
+            assert np.array_equal(b.codes[b.offsets[o]:b.offsets[o] + b.lengths[o]],
+                                  s.codes[s.offsets[n_]:s.offsets[n_] + s.lengths[n_]])
