@@ -1,0 +1,205 @@
+/* xdrop.h -- C ABI of the batched X-Drop seed-extension library (CUDA, sm_103a).
+ *
+ * The library computes, for many independent seed extensions at once, the X-Drop
+ * semi-global alignment of the paper (Sec. 2.2 recurrence and X-Drop rule, Sec. 3 and
+ * Algorithm 1 for the anti-diagonal sweep, the live band and the memory-restricted
+ * window).  Every pair (H, V, H_s, V_s) with a seed of length k (the seed-extension tuple
+ * e_c of Sec. 4.4) is split into a left and a right extension (Sec. 4.1.2); each side is
+ * aligned from S(0,0) = 0 and the best cell is reported.
+ *
+ * Exact integer arithmetic throughout.  Results are bit-identical to the plain CPU
+ * definition of the method (score, end coordinates, overflow flag, evaluated cells).
+ *
+ * Conventions
+ *   - Every call returns an xd_status; nothing throws across the ABI.
+ *   - Host pointers passed to xd_submit_batch are read during the call only: the caller
+ *     may free or reuse them as soon as it returns.
+ *   - Residue codes are unpacked bytes: 0..3 for DNA (A, C, G, T), 0..19 for protein in
+ *     the order A R N D C Q E G H I L K M F P S T W Y V.  Packing (2-bit DNA, 5-bit
+ *     protein) happens inside the library.
+ *   - Side coordinates: right side H_R[t] = H[h_seed + k + t], V_R[t] = V[v_seed + k + t];
+ *     left side H_L[t] = H[h_seed - 1 - t], V_L[t] = V[v_seed - 1 - t] (the index
+ *     transform op() of Sec. 3).  h_ext / v_ext are the i / j of the best cell, i.e. the
+ *     extension lengths; the aligned span on H is [h_seed - left.h_ext,
+ *     h_seed + k + right.h_ext), and likewise on V.
+ *   - Readings of the paper where it is silent: X-Drop compares strictly (S < T - X)
+ *     against the best score T of the completed anti-diagonals; the next band is
+ *     [first live, last live + 1] clipped to the matrix; the end cell is the first
+ *     anti-diagonal reaching the best score, lowest i on it; the seed is not part of a
+ *     side's score and total = left + right + sum of Sim over the seed.
+ */
+#ifndef XDROP_H
+#define XDROP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct xd_ctx xd_ctx;
+
+typedef enum {
+    XD_OK = 0,
+    XD_PENDING = 1,      /* xd_poll: the batch has not finished yet */
+    XD_EINVAL = -1,      /* invalid argument; nothing was queued */
+    XD_ENOMEM = -2,      /* admission refused (device memory cap or no free slot); retry later */
+    XD_ETIMEDOUT = -3,   /* a bounded wait expired; the work is still in flight */
+    XD_EDEVICE = -4,     /* CUDA error or no usable device */
+    XD_ENOTFOUND = -5    /* unknown or already retired ticket */
+} xd_status;
+
+typedef enum { XD_DNA2 = 0, XD_PROT5 = 1 } xd_alphabet;
+
+/* Context configuration.  device: CUDA ordinal.  store_bytes_cap: device bytes the
+ * library may hold for in-flight batches (0 = 64 GiB).  max_inflight: concurrently
+ * admitted host batches (0 = 8).  tune_table: path of an autotune table written by
+ * xd_autotune, or NULL for built-in defaults. */
+typedef struct {
+    int32_t device;
+    uint64_t store_bytes_cap;
+    int32_t max_inflight;
+    const char* tune_table;
+} xd_config;
+
+/* Scoring (Sec. 2.2): DNA uses match (> 0), mismatch and gap scores; protein uses a
+ * 20x20 row-major substitution matrix (BLOSUM62 in Sec. 5.3) and the gap score.  gap is
+ * the (negative) score added per gap symbol: linear gaps only.  matrix20x20 is a host
+ * pointer, read during the call. */
+typedef struct {
+    int32_t match, mismatch, gap;
+    const int8_t* matrix20x20;
+} xd_scoring;
+
+/* One seed-extension tuple e_c = (H, V, H_s, V_s) plus the seed length k (Sec. 4.4):
+ * indices into the batch's sequence table and seed start positions. */
+typedef struct {
+    uint32_t h_id, v_id;
+    uint32_t h_seed, v_seed, seed_len;
+} xd_pair;
+
+/* A batch: sequence table (codes + per-sequence offsets/lengths, the detached sequence
+ * set of Sec. 4.1.1) and the list of seed tuples.  For xd_submit_batch every pointer is
+ * a host pointer; for xd_run_device, seq_codes, seq_offsets, seq_lengths and pairs are
+ * device pointers (scoring.matrix20x20 stays a host pointer).  n_codes is the length of
+ * seq_codes in bytes.  X >= 0; X >= 2^30 means no pruning (X = infinity).  delta_b = 0
+ * runs the unrestricted method, delta_b >= 1 the memory-restricted window of Sec. 3. */
+typedef struct {
+    xd_alphabet alpha;
+    uint32_t n_seqs;
+    uint64_t n_codes;
+    const uint8_t* seq_codes;
+    const uint64_t* seq_offsets;
+    const uint32_t* seq_lengths;
+    uint32_t n_pairs;
+    const xd_pair* pairs;
+    xd_scoring scoring;
+    int32_t X;
+    uint32_t delta_b;
+} xd_batch;
+
+/* Result of one side.  flags bit 0: the memory-restricted window was exceeded at least
+ * once (the band was clipped to delta_b cells). */
+typedef struct {
+    int32_t score;
+    uint32_t h_ext, v_ext;
+    uint32_t flags;
+    uint64_t cells;      /* DP cells evaluated, S(0,0) included (pruned cells included) */
+} xd_side;
+
+typedef struct {
+    xd_side left, right;
+    int64_t total;       /* left.score + right.score + seed score */
+} xd_result;
+
+/* Per-context counters, cumulative since xd_create. */
+typedef struct {
+    uint64_t batches;            /* batches run (host and device entry points) */
+    uint64_t pairs;
+    uint64_t cells;              /* sum of xd_side.cells over all sides */
+    uint64_t units_tier[3];      /* side extensions finished by the narrow, wide, generic tier */
+    uint64_t escalations;        /* side extensions restarted in a wider tier */
+    uint64_t kernel_launches;    /* kernels launched by the library */
+} xd_stats;
+
+/* Create a context on cfg->device (NULL cfg = defaults).  Allocates nothing large until
+ * the first batch.  Errors: XD_EINVAL (out == NULL), XD_EDEVICE (no such device or the
+ * device is not compute capability 10.3). */
+xd_status xd_create(const xd_config* cfg, xd_ctx** out);
+
+/* Validate and enqueue a host batch (Sec. 4.4 tuples; Sec. 3 method).  Copies every input
+ * to pinned staging memory before returning, so the caller may free its buffers at once.
+ * On XD_OK *ticket identifies the batch for xd_poll.  Errors: XD_EINVAL (codes out of the
+ * alphabet, a seed outside its sequence, X < 0, a protein batch without matrix, scores
+ * that could leave the exact integer range), XD_ENOMEM (the batch does not fit the
+ * store cap now or no in-flight slot is free: nothing was queued), XD_EDEVICE. */
+xd_status xd_submit_batch(xd_ctx* ctx, const xd_batch* batch, uint64_t* ticket);
+
+/* Wait up to wait_ms milliseconds (0 = do not wait, < 0 = wait without limit) for the
+ * batch of `ticket`; on XD_OK copies n_pairs results to the host array `out` and retires
+ * the ticket.  Returns XD_PENDING if not finished and wait_ms == 0, XD_ETIMEDOUT if the
+ * wait expired, XD_ENOTFOUND for an unknown ticket, XD_EDEVICE on a CUDA error. */
+xd_status xd_poll(xd_ctx* ctx, uint64_t ticket, xd_result* out, int32_t wait_ms);
+
+/* Run the whole hot path on device-resident inputs, asynchronously on `stream`
+ * (a cudaStream_t, NULL = the legacy default stream): pack, build work units, order them
+ * by cost, extend all sides, write n_pairs results to the device array d_out.  Scratch
+ * comes from the context and is grown on demand (call xd_reserve first to keep
+ * allocations out of a timed region).  Input validation happens on the device; read it
+ * with xd_device_status after the stream has finished.  Not reentrant per context.
+ * Errors: XD_EINVAL (null pointers, X < 0, protein without matrix), XD_ENOMEM, XD_EDEVICE. */
+xd_status xd_run_device(xd_ctx* ctx, const xd_batch* dev_batch, xd_result* d_out, void* stream);
+
+/* Pre-size the scratch used by xd_run_device for batches up to the given sizes. */
+xd_status xd_reserve(xd_ctx* ctx, uint64_t n_codes, uint32_t n_seqs, uint32_t n_pairs,
+                     uint32_t max_seq_len);
+
+/* Synchronise the context's device work and report the device-side validation word of
+ * the last xd_run_device batch: 0 = valid; bit 0 code outside the alphabet, bit 1 seed
+ * outside its sequence, bit 2 score range exceeded, bit 3 a bounded device wait gave up. */
+xd_status xd_device_status(xd_ctx* ctx, uint32_t* flags);
+
+xd_status xd_get_stats(const xd_ctx* ctx, xd_stats* out);
+
+/* Timing of the device pipeline, summed over every batch run since timing was enabled,
+ * recorded with CUDA events on the stream the kernels are launched on.  Stage times are
+ * in milliseconds; tier 0 = one thread per side extension (narrow bands), tier 1 = one
+ * warp per side extension (wide bands), tier 2 = generic (any band width).  tier_cells
+ * are the DP cells of the side extensions each tier finished; discarded_cells were
+ * evaluated by a tier before a side was escalated to a wider one. */
+typedef struct {
+    uint64_t batches;            /* batches summed below */
+    float pack_ms, units_ms, order_ms;
+    float tier_ms[3];
+    float totals_ms;
+    float total_ms;
+    uint64_t tier_units[3];
+    uint64_t tier_cells[3];
+    uint64_t escalations;
+    uint64_t discarded_cells;
+    uint64_t launches;           /* kernels the library launched */
+} xd_timing;
+
+/* enable != 0 synchronises the context, clears the timing sums and records stage events
+ * for every following batch (up to 4096 batches); enable == 0 stops recording. */
+xd_status xd_set_timing(xd_ctx* ctx, int32_t enable);
+
+/* Synchronises the context's device work and returns the sums since timing was enabled.
+ * XD_ENOTFOUND if no batch was recorded. */
+xd_status xd_get_timing(xd_ctx* ctx, xd_timing* out);
+
+/* Wait (bounded) for all in-flight work, then free every resource of the context. */
+xd_status xd_destroy(xd_ctx* ctx);
+
+/* Last error message of the context (never NULL; "" when none).  ctx may be NULL for
+ * errors of xd_create. */
+const char* xd_last_error(const xd_ctx* ctx);
+
+/* Library version string. */
+const char* xd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* XDROP_H */

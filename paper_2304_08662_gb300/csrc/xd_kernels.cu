@@ -1,0 +1,345 @@
+// Device pipeline of one batch: pack -> work units -> cost ordering -> tier kernels ->
+// pair totals.  The alignment tiers live in xd_tiers.cu; this file holds the
+// bandwidth-bound preparation kernels and the generic (any band width) tier.
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "xd_device.cuh"
+#include "xd_launch.h"
+
+namespace xd {
+
+// ---------------------------------------------------------------------------------------
+// a1: sequence store.  The caller's residue codes (one byte each) are packed in place of
+// their flat position: DNA 2 bits (16 per 32-bit word), protein 5 bits (6 per word).
+// One thread per output word; codes outside the alphabet raise kErrCode.
+__global__ void k_pack_dna(const uint8_t* __restrict__ codes, uint64_t n_codes,
+                           uint32_t* __restrict__ store, uint64_t n_words, uint32_t* err) {
+    uint64_t w = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x;
+    uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    bool aligned = (reinterpret_cast<uintptr_t>(codes) & 15u) == 0;
+    for (; w < n_words; w += stride) {
+        uint64_t base = w * 16;
+        uint32_t word = 0, bad = 0;
+        if (aligned && base + 16 <= n_codes) {
+            uint4 q = __ldg(reinterpret_cast<const uint4*>(codes + base));
+            uint32_t parts[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int p = 0; p < 4; p++) {
+                uint32_t x = parts[p];
+                bad |= x & 0xFCFCFCFCu;
+#pragma unroll
+                for (int b = 0; b < 4; b++) word |= ((x >> (8 * b)) & 3u) << (2 * (4 * p + b));
+            }
+        } else {
+            for (int t = 0; t < 16 && base + t < n_codes; t++) {
+                uint32_t c = codes[base + t];
+                bad |= c & ~3u;
+                word |= (c & 3u) << (2 * t);
+            }
+        }
+        store[w] = word;
+        if (bad) atomicOr(err, kErrCode);
+    }
+}
+
+__global__ void k_pack_prot(const uint8_t* __restrict__ codes, uint64_t n_codes,
+                            uint32_t* __restrict__ store, uint64_t n_words, uint32_t* err) {
+    uint64_t w = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x;
+    uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (; w < n_words; w += stride) {
+        uint64_t base = w * 6;
+        uint32_t word = 0;
+        bool bad = false;
+        for (int t = 0; t < 6 && base + t < n_codes; t++) {
+            uint32_t c = codes[base + t];
+            bad |= c >= 20u;
+            word |= (c & 31u) << (5 * t);
+        }
+        store[w] = word;
+        if (bad) atomicOr(err, kErrCode);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// a2: work units.  Each pair gives a right and a left unit (Sec. 4.1.2).  Cost proxy is
+// the quadratic maximum work m * n of Sec. 4.2; units are bucketed by its log2 so that
+// the most expensive run first.  Invalid tuples raise kErrSeed and become empty units;
+// sides whose scores could leave the exact range raise kErrRange and also become empty.
+__device__ __forceinline__ uint32_t cost_bucket(uint32_t m, uint32_t n) {
+    uint64_t c = uint64_t(m) * n + 1;
+    return 63u - uint32_t(__clzll(c));        // 0 .. 63
+}
+
+__global__ void k_units(const xd_pair* __restrict__ pairs, uint32_t n_pairs,
+                        const uint64_t* __restrict__ offsets, const uint32_t* __restrict__ lengths,
+                        uint32_t n_seqs, int32_t max_abs, uint32_t max_len,
+                        Unit* __restrict__ units, uint32_t* __restrict__ bucket_of,
+                        uint32_t* __restrict__ hist, uint32_t* err) {
+    __shared__ uint32_t sh[64];
+    for (int t = threadIdx.x; t < 64; t += blockDim.x) sh[t] = 0;
+    __syncthreads();
+    uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n_pairs) {
+        xd_pair e = pairs[p];
+        uint32_t bad = 0;
+        uint64_t ho = 0, vo = 0;
+        uint32_t lh = 0, lv = 0;
+        if (e.h_id >= n_seqs || e.v_id >= n_seqs) {
+            bad = kErrSeed;
+        } else {
+            ho = offsets[e.h_id]; vo = offsets[e.v_id];
+            lh = lengths[e.h_id]; lv = lengths[e.v_id];
+            if (uint64_t(e.h_seed) + e.seed_len > lh || uint64_t(e.v_seed) + e.seed_len > lv)
+                bad = kErrSeed;
+        }
+        Unit r{}, l{};
+        r.pair = l.pair = p;
+        r.side = 0; l.side = 1;
+        if (!bad) {
+            r.h0 = ho + e.h_seed + e.seed_len; r.m = lh - e.h_seed - e.seed_len;
+            r.v0 = vo + e.v_seed + e.seed_len; r.n = lv - e.v_seed - e.seed_len;
+            l.h0 = e.h_seed ? ho + e.h_seed - 1 : ho; l.m = e.h_seed;
+            l.v0 = e.v_seed ? vo + e.v_seed - 1 : vo; l.n = e.v_seed;
+            uint32_t range = 0;
+            if ((int64_t(r.m) + r.n) * max_abs >= kScoreLimit || r.m > max_len) { r.m = r.n = 0; range = kErrRange; }
+            if ((int64_t(l.m) + l.n) * max_abs >= kScoreLimit || l.m > max_len) { l.m = l.n = 0; range = kErrRange; }
+            bad |= range;
+        }
+        if (bad) atomicOr(err, bad);
+        units[2 * p] = r;
+        units[2 * p + 1] = l;
+        uint32_t br = cost_bucket(r.m, r.n), bl = cost_bucket(l.m, l.n);
+        bucket_of[2 * p] = br;
+        bucket_of[2 * p + 1] = bl;
+        atomicAdd(&sh[br], 1u);
+        atomicAdd(&sh[bl], 1u);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 64; t += blockDim.x)
+        if (sh[t]) atomicAdd(&hist[t], sh[t]);
+}
+
+// One block: exclusive offsets of the cost buckets in descending cost order; resets the
+// queue counters of the batch.
+__global__ void k_bucket_scan(uint32_t* hist, uint32_t* ctr, int n_ctr) {
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int b = 63; b >= 0; b--) {
+            uint32_t c = hist[b];
+            hist[b] = run;
+            run += c;
+        }
+    }
+    for (int t = threadIdx.x; t < n_ctr; t += blockDim.x) ctr[t] = 0;
+}
+
+__global__ void k_bucket_scatter(const uint32_t* __restrict__ bucket_of, uint32_t n_units,
+                                 uint32_t* hist_pos, uint32_t* __restrict__ order) {
+    uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u < n_units) order[atomicAdd(&hist_pos[bucket_of[u]], 1u)] = u;
+}
+
+// ---------------------------------------------------------------------------------------
+// Generic tier: one warp per unit, the three anti-diagonals in a global-memory ring
+// indexed by i (capacity max_m + 1 per array), any band width.  It is the fallback for
+// units whose band does not fit the register tiers.  The step follows the method
+// directly: band [lo, hi] from the previous anti-diagonal (Algorithm 1), optional
+// delta_b window centred on the previous anti-diagonal's best cell, the recurrence of
+// Sec. 2.2, the X-Drop test against T of completed anti-diagonals, then warp
+// reductions of first/last live cell and of the best cell (lowest i on ties).
+__device__ __forceinline__ int32_t sim_of(const int32_t* sim, int alpha, uint32_t a, uint32_t b) {
+    return sim[a * alpha + b];
+}
+
+__device__ void extend_generic(const Problem& P, const Unit& u, int32_t* A, int32_t* B,
+                               int32_t* Cc, const int32_t* sim, int lane) {
+    const int64_t m = u.m, n = u.n;
+    const int64_t hdir = u.side ? -1 : 1;
+    const int64_t vdir = hdir;
+    int32_t* P1 = A; int32_t* P2 = B; int32_t* C = Cc;
+    int64_t p1lo = 0, p1hi = 0, p2lo = 1, p2hi = 0;
+    if (lane == 0) P1[0] = 0;
+    __syncwarp();
+    int32_t T = 0, best = 0;
+    int64_t bi_best = 0, bj_best = 0;
+    int64_t L = 0, U = 0, prev_arg = 0;
+    uint64_t cells = 1;
+    uint32_t flags = 0;
+    const int32_t g = P.gap;
+    for (int64_t d = 1; d <= m + n; d++) {
+        int64_t lo = L, hi = U + 1;
+        if (d - n > lo) lo = d - n;
+        if (lo < 0) lo = 0;
+        if (hi > m) hi = m;
+        if (hi > d) hi = d;
+        if (P.delta && hi - lo + 1 > int64_t(P.delta)) {
+            flags = 1;
+            int64_t start = prev_arg - int64_t(P.delta / 2);
+            int64_t latest = hi - int64_t(P.delta) + 1;
+            if (latest < start) start = latest;
+            if (start > lo) lo = start;
+            hi = lo + int64_t(P.delta) - 1;
+        }
+        const int32_t thr = max(T - P.X, kDeadLine);
+        int32_t first = INT32_MAX, last = -1, bmax = kNeg, barg = INT32_MAX;
+        for (int64_t i = lo + lane; i <= hi; i += 32) {
+            const int64_t j = d - i;
+            int32_t c = kNeg;
+            if (i >= 1 && j >= 1 && i - 1 >= p2lo && i - 1 <= p2hi) {
+                uint32_t a = residue(P.store, P.alpha, u.h0 + hdir * (i - 1));
+                uint32_t b = residue(P.store, P.alpha, u.v0 + vdir * (j - 1));
+                c = P2[i - 1] + sim_of(sim, P.alpha, a, b);
+            }
+            if (i >= 1 && i - 1 >= p1lo && i - 1 <= p1hi) c = max(c, P1[i - 1] + g);
+            if (j >= 1 && i >= p1lo && i <= p1hi) c = max(c, P1[i] + g);
+            if (c < thr) c = kNeg;
+            C[i] = c;
+            if (c != kNeg) {
+                if (first == INT32_MAX) first = int32_t(i);
+                last = int32_t(i);
+                if (c > bmax) { bmax = c; barg = int32_t(i); }
+            }
+        }
+        cells += uint64_t(hi - lo + 1);
+        first = __reduce_min_sync(0xffffffffu, first);
+        last = __reduce_max_sync(0xffffffffu, last);
+        const int32_t wmax = __reduce_max_sync(0xffffffffu, bmax);
+        barg = __reduce_min_sync(0xffffffffu, bmax == wmax ? barg : INT32_MAX);
+        __syncwarp();
+        if (first == INT32_MAX) break;
+        if (wmax > T) { T = wmax; best = wmax; bi_best = barg; bj_best = d - barg; }
+        prev_arg = barg;
+        L = first; U = last;
+        int32_t* old = P2;
+        P2 = P1; p2lo = p1lo; p2hi = p1hi;
+        P1 = C; p1lo = lo; p1hi = hi;
+        C = old;
+    }
+    if (lane == 0) {
+        write_side(P.results, u.pair, u.side, best, uint32_t(bi_best), uint32_t(bj_best), flags, cells);
+        atomicAdd(&P.stats[2], 1ull);
+        atomicAdd(&P.stats[6], (unsigned long long)cells);
+    }
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(128) k_generic(Problem P, Queues Q, int32_t* scratch,
+                                                 uint64_t stride) {
+    __shared__ int32_t sim[400];
+    for (int t = threadIdx.x; t < P.alpha * P.alpha; t += blockDim.x) sim[t] = P.sim[t];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
+    int32_t* A = scratch + warp * 3 * stride;
+    const uint32_t n_q = *reinterpret_cast<volatile uint32_t*>(&Q.ctr[3]);
+    for (;;) {
+        uint32_t k = 0;
+        if (lane == 0) k = atomicAdd(&Q.ctr[4], 1u);
+        k = __shfl_sync(0xffffffffu, k, 0);
+        if (k >= n_q) break;
+        const Unit u = P.units[Q.q2[k]];
+        extend_generic(P, u, A, A + stride, A + 2 * stride, sim, lane);
+    }
+}
+
+// Queue every unit to the generic tier (used when the register tiers are disabled).
+__global__ void k_route_all_generic(Queues Q) {
+    uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < Q.n_units) Q.q2[t] = Q.order[t];
+    if (t == 0) Q.ctr[3] = Q.n_units;
+}
+
+// ---------------------------------------------------------------------------------------
+// a9: pair totals = left + right + sum of Sim over the seed.
+__global__ void k_totals(const xd_pair* __restrict__ pairs, uint32_t n_pairs,
+                         const uint64_t* __restrict__ offsets, const uint32_t* __restrict__ lengths,
+                         uint32_t n_seqs, Problem P) {
+    __shared__ int32_t sim[400];
+    for (int t = threadIdx.x; t < P.alpha * P.alpha; t += blockDim.x) sim[t] = P.sim[t];
+    __syncthreads();
+    uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_pairs) return;
+    xd_pair e = pairs[p];
+    int64_t seed = 0;
+    if (e.h_id < n_seqs && e.v_id < n_seqs) {
+        uint64_t ho = offsets[e.h_id] + e.h_seed, vo = offsets[e.v_id] + e.v_seed;
+        if (uint64_t(e.h_seed) + e.seed_len <= lengths[e.h_id] &&
+            uint64_t(e.v_seed) + e.seed_len <= lengths[e.v_id])
+            for (uint32_t t = 0; t < e.seed_len; t++)
+                seed += sim[residue(P.store, P.alpha, ho + t) * P.alpha + residue(P.store, P.alpha, vo + t)];
+    }
+    xd_result& r = P.results[p];
+    r.total = int64_t(r.left.score) + int64_t(r.right.score) + seed;
+}
+
+// Adds the per-batch counters into the context's cumulative ones.
+__global__ void k_accumulate(const unsigned long long* batch, unsigned long long* total, int n) {
+    int t = threadIdx.x;
+    if (t < n) total[t] += batch[t];
+}
+
+// ---------------------------------------------------------------------------------------
+// Host-side launchers.
+
+static int grid_for(uint64_t n, int block, int max_blocks) {
+    uint64_t g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > uint64_t(max_blocks)) g = max_blocks;
+    return int(g);
+}
+
+cudaError_t launch_pack(int alpha, const uint8_t* codes, uint64_t n_codes, uint32_t* store,
+                        uint32_t* err, int n_sm, cudaStream_t st) {
+    uint64_t per = alpha == 4 ? 16 : 6;
+    uint64_t n_words = (n_codes + per - 1) / per;
+    if (n_words == 0) return cudaSuccess;
+    int grid = grid_for(n_words, 256, n_sm * 16);
+    if (alpha == 4) k_pack_dna<<<grid, 256, 0, st>>>(codes, n_codes, store, n_words, err);
+    else k_pack_prot<<<grid, 256, 0, st>>>(codes, n_codes, store, n_words, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_units(const xd_pair* pairs, uint32_t n_pairs, const uint64_t* offsets,
+                         const uint32_t* lengths, uint32_t n_seqs, int32_t max_abs,
+                         uint32_t max_len, Unit* units, uint32_t* bucket_of, uint32_t* hist,
+                         uint32_t* err, cudaStream_t st) {
+    if (n_pairs == 0) return cudaSuccess;
+    k_units<<<(n_pairs + 255) / 256, 256, 0, st>>>(pairs, n_pairs, offsets, lengths, n_seqs,
+                                                   max_abs, max_len, units, bucket_of, hist, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_order(uint32_t* hist, uint32_t* ctr, int n_ctr, const uint32_t* bucket_of,
+                         uint32_t n_units, uint32_t* order, cudaStream_t st) {
+    k_bucket_scan<<<1, 32, 0, st>>>(hist, ctr, n_ctr);
+    if (n_units)
+        k_bucket_scatter<<<(n_units + 255) / 256, 256, 0, st>>>(bucket_of, n_units, hist, order);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_route_all_generic(const Queues& Q, cudaStream_t st) {
+    k_route_all_generic<<<(Q.n_units + 255) / 256 + 1, 256, 0, st>>>(Q);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_generic(const Problem& P, const Queues& Q, int32_t* scratch,
+                           uint64_t stride, int n_blocks, cudaStream_t st) {
+    k_generic<<<n_blocks, 128, 0, st>>>(P, Q, scratch, stride);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_totals(const xd_pair* pairs, uint32_t n_pairs, const uint64_t* offsets,
+                          const uint32_t* lengths, uint32_t n_seqs, const Problem& P,
+                          cudaStream_t st) {
+    if (n_pairs == 0) return cudaSuccess;
+    k_totals<<<(n_pairs + 255) / 256, 256, 0, st>>>(pairs, n_pairs, offsets, lengths, n_seqs, P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_accumulate(const unsigned long long* batch, unsigned long long* total, int n,
+                              cudaStream_t st) {
+    k_accumulate<<<1, 32, 0, st>>>(batch, total, n);
+    return cudaGetLastError();
+}
+
+}  // namespace xd

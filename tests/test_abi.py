@@ -1,0 +1,45 @@
+"""The C-ABI library builds, loads and exports every function include/xdrop.h declares;
+host-side argument handling that needs no GPU."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2304_08662_gb300 import xdrop
+
+
+def test_header_declares_the_boundary():
+    names = xdrop.header_symbols()
+    for required in ("xd_create", "xd_submit_batch", "xd_poll", "xd_destroy", "xd_last_error",
+                     "xd_run_device", "xd_reserve", "xd_device_status", "xd_get_stats", "xd_version"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    L = xdrop.lib()
+    for name in xdrop.header_symbols():
+        assert hasattr(L, name), name
+
+
+def test_struct_layouts_match_header():
+    assert ctypes.sizeof(xdrop.xd_batch) == 88
+    assert xdrop.RESULT_DTYPE.itemsize == 56
+    assert xdrop.SIDE_DTYPE.itemsize == 24
+    assert xdrop.PAIR_DTYPE.itemsize == 20
+
+
+def test_version_and_null_arguments():
+    assert "sm_103a" in xdrop.xd_version()
+    L = xdrop.lib()
+    assert L.xd_create(None, None) == xdrop.XD_EINVAL
+    assert L.xd_poll(None, 1, None, 0) == xdrop.XD_EINVAL
+    assert L.xd_destroy(None) == xdrop.XD_EINVAL
+
+
+def test_create_without_gpu_reports_edevice():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(xdrop.XdError) as e:
+        xdrop.xd_create(0)
+    assert e.value.status == xdrop.XD_EDEVICE

@@ -1,0 +1,254 @@
+"""GPU parity: the CUDA library (through the C ABI) against the CPU oracle, bit for bit.
+
+Every field is integer (score, h_ext, v_ext, flags, cells, total), so the tolerance is
+zero.  Cases cover the hand traces, random tiny and ragged inputs, empty and length-1
+sides, X = 0 and X = infinity, tiny and large restricted windows, every workload shape
+at reduced size, and the long-read workload at full size on sampled pairs through the
+device entry point in the launch configuration the bench times.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from synth import X_INF
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2304_08662_gb300 import xdrop  # noqa: E402
+
+THREADS = max(1, os.cpu_count() or 1)
+FIELDS = ("score", "h_ext", "v_ext", "flags", "cells")
+
+
+def _ctx(mode):
+    old = os.environ.get("XD_TIERS")
+    if mode == "generic":
+        os.environ["XD_TIERS"] = "generic"
+    else:
+        os.environ.pop("XD_TIERS", None)
+    try:
+        return xdrop.xd_create(0)
+    finally:
+        if old is None:
+            os.environ.pop("XD_TIERS", None)
+        else:
+            os.environ["XD_TIERS"] = old
+
+
+@pytest.fixture(scope="module", params=["tiered", "generic"])
+def ctx(request):
+    c = _ctx(request.param)
+    yield c
+    xdrop.xd_destroy(c)
+
+
+@pytest.fixture(scope="module")
+def tiered():
+    c = _ctx("tiered")
+    yield c
+    xdrop.xd_destroy(c)
+
+
+def assert_parity(got, batch, idx=None):
+    L, R, T = oracle.run_batch(batch, threads=THREADS)
+    if idx is not None:
+        L, R, T = L[idx], R[idx], T[idx]
+    for side, ref in (("left", L), ("right", R)):
+        for f in FIELDS:
+            g = got[side][f]
+            bad = np.nonzero(g != ref[f])[0]
+            assert bad.size == 0, (f"{side}.{f} differs at pairs {bad[:10].tolist()}: "
+                                   f"gpu {g[bad[:5]].tolist()} oracle {ref[f][bad[:5]].tolist()}")
+    bad = np.nonzero(got["total"] != T)[0]
+    assert bad.size == 0, f"total differs at {bad[:10].tolist()}"
+
+
+def random_pairs(rng, n, alphabet, max_len, k_max=8, related=True):
+    letters = "ACGT" if alphabet == "dna" else synth.AMINO_ACIDS
+    rows = []
+    for _ in range(n):
+        lh, lv = int(rng.integers(1, max_len + 1)), int(rng.integers(1, max_len + 1))
+        k = int(rng.integers(1, min(k_max, lh, lv) + 1))
+        h = rng.choice(list(letters), lh)
+        if related:
+            v = h.copy()
+            v = v[:lv] if lv <= lh else np.concatenate([v, rng.choice(list(letters), lv - lh)])
+            flip = rng.random(lv) < rng.uniform(0.0, 0.4)
+            v[flip] = rng.choice(list(letters), int(flip.sum()))
+        else:
+            v = rng.choice(list(letters), lv)
+        hs, vs = int(rng.integers(0, lh - k + 1)), int(rng.integers(0, lv - k + 1))
+        v[vs:vs + k] = h[hs:hs + k]
+        rows.append(("".join(h), "".join(v), hs, vs, k))
+    return rows
+
+
+def test_hand_traces(ctx):
+    """The hand-derived traces of tests/golden, run as right extensions with an empty seed."""
+    here = os.path.dirname(os.path.abspath(__file__))
+    cases, cur = [], None
+    for ln in open(os.path.join(here, "golden", "hand_traces.txt")):
+        ln = ln.rstrip("\n")
+        if ln.startswith("case "):
+            cur = {}
+            cases.append(cur)
+        elif cur is not None and ln and not ln.startswith("#"):
+            k, _, v = ln.partition(" ")
+            cur[k] = v.strip()
+    for c in cases:
+        b = synth.from_strings([(c["H"], c["V"], 0, 0, 0)], X=int(c["X"]), delta=int(c["delta"]))
+        got = xdrop.extend_host(ctx, b)
+        want = [int(x) for x in c["expect"].split()]
+        assert [int(got["right"][0][f]) for f in FIELDS] == want, c
+        assert_parity(got, b)
+
+
+@pytest.mark.parametrize("alphabet", ["dna", "protein"])
+@pytest.mark.parametrize("X", [0, 1, 3, 10, 49, X_INF])
+def test_random_tiny(ctx, alphabet, X):
+    rng = np.random.default_rng(100 + X % 1000 + (alphabet == "protein"))
+    rows = random_pairs(rng, 300, alphabet, 40)
+    gap = -1 if alphabet == "dna" else -2
+    b = synth.from_strings(rows, alphabet=alphabet, gap=gap, X=X)
+    assert_parity(xdrop.extend_host(ctx, b), b)
+
+
+@pytest.mark.parametrize("delta", [1, 2, 3, 7, 32, 33, 100])
+def test_random_restricted(ctx, delta):
+    rng = np.random.default_rng(delta)
+    rows = random_pairs(rng, 200, "dna", 300)
+    for X in (5, 30):
+        b = synth.from_strings(rows, X=X, delta=delta)
+        assert_parity(xdrop.extend_host(ctx, b), b)
+
+
+def test_edges(ctx):
+    rows = [
+        ("ACGT", "ACGT", 0, 0, 4),          # both sides empty
+        ("ACGTA", "ACGT", 0, 0, 4),         # right side m = 1, n = 0
+        ("AACGT", "ACGT", 1, 0, 4),         # left side m = 1, n = 0
+        ("A", "A", 0, 0, 1),
+        ("CA", "GA", 1, 1, 1),              # left side 1 x 1 mismatch
+        ("ACCCCCCCCCC", "AGGGGGGGGGG", 0, 0, 1),
+        ("T" * 200, "T" * 200, 100, 100, 1),
+        ("ACGT" * 50, "TGCA" * 50, 0, 0, 1),
+    ]
+    for X in (0, 1, 2, 15, X_INF):
+        for delta in (0, 1, 4):
+            b = synth.from_strings(rows, X=X, delta=delta)
+            assert_parity(xdrop.extend_host(ctx, b), b)
+
+
+def test_dna_tiny_workload(ctx):
+    b = synth.dna_tiny()
+    assert_parity(xdrop.extend_host(ctx, b), b)
+
+
+@pytest.mark.parametrize("X", [10, 20, 50])
+def test_longread_shape(ctx, X):
+    b = synth.dna_longread(n_pairs=1500).with_params(X=X)
+    assert_parity(xdrop.extend_host(ctx, b), b)
+
+
+def test_protein_shape(ctx):
+    b = synth.protein(n_pairs=20000)
+    assert_parity(xdrop.extend_host(ctx, b), b)
+
+
+@pytest.mark.parametrize("delta", [0, 256, 1024, 4096])
+def test_uneven_restricted_shape(ctx, delta):
+    b = synth.uneven(n_pairs=150, delta=delta)
+    assert_parity(xdrop.extend_host(ctx, b), b)
+
+
+def test_uneven_small_window_overflows(tiered):
+    b = synth.uneven(n_pairs=100, delta=24, X=50)
+    got = xdrop.extend_host(tiered, b)
+    assert (got["left"]["flags"] | got["right"]["flags"]).any()
+    assert_parity(got, b)
+
+
+def _device_args(b):
+    dev = torch.device("cuda", 0)
+    codes = torch.from_numpy(b.codes).to(dev)
+    offs = torch.from_numpy(b.offsets.view(np.int64)).to(dev)
+    lens = torch.from_numpy(b.lengths.view(np.int32)).to(dev)
+    pairs = torch.from_numpy(np.ascontiguousarray(b.pairs).view(np.int32)).to(dev)
+    args = xdrop.BatchArgs(b.alphabet, codes, offs, lens, pairs, b.match, b.mismatch, b.gap,
+                           b.matrix, b.X, b.delta)
+    out = torch.zeros(b.n_pairs * xdrop.RESULT_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    return args, out
+
+
+def _results(out):
+    return out.cpu().numpy().view(xdrop.RESULT_DTYPE)
+
+
+def test_device_entry_matches_host_entry(tiered):
+    b = synth.dna_longread(n_pairs=800)
+    args, out = _device_args(b)
+    xdrop.xd_run_device(tiered, args, out, None)
+    torch.cuda.synchronize()
+    assert xdrop.xd_device_status(tiered) == 0
+    got = _results(out)
+    host = xdrop.extend_host(tiered, b)
+    assert np.array_equal(got, host)
+    assert_parity(got, b)
+
+
+def test_full_size_longread_sampled(tiered):
+    """100,000 long-read pairs, X = 20, through xd_run_device as the bench runs it; 400
+    sampled pairs are recomputed by the oracle one by one; every result is also checked
+    for properties that hold at any size."""
+    b = synth.dna_longread()
+    args, out = _device_args(b)
+    xdrop.xd_reserve(tiered, b.codes.size, b.n_seqs, b.n_pairs, int(b.lengths.max()))
+    xdrop.xd_run_device(tiered, args, out, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert xdrop.xd_device_status(tiered) == 0
+    got = _results(out)
+    rng = np.random.default_rng(2024)
+    idx = np.sort(rng.choice(b.n_pairs, 400, replace=False))
+    sub = b.subset(idx)
+    assert_parity(got[idx], sub)
+    p = b.pairs.astype(np.int64)
+    lh, lv = b.lengths[p[:, 0]].astype(np.int64), b.lengths[p[:, 1]].astype(np.int64)
+    r, l = got["right"], got["left"]
+    assert (r["score"] >= 0).all() and (l["score"] >= 0).all()
+    assert (r["h_ext"] <= lh - p[:, 2] - p[:, 4]).all() and (l["h_ext"] <= p[:, 2]).all()
+    assert (r["v_ext"] <= lv - p[:, 3] - p[:, 4]).all() and (l["v_ext"] <= p[:, 3]).all()
+    assert (r["cells"] >= 1).all() and (r["flags"] == 0).all()
+    assert (got["total"] == r["score"].astype(np.int64) + l["score"] + p[:, 4]).all()
+
+
+def test_invalid_inputs_rejected(tiered):
+    good = synth.from_strings([("ACGT", "ACGT", 0, 0, 2)], X=3)
+    bad_code = synth.from_strings([("ACGT", "ACGT", 0, 0, 2)], X=3)
+    bad_code.codes = bad_code.codes.copy()
+    bad_code.codes[1] = 7
+    with pytest.raises(xdrop.XdError) as e:
+        xdrop.extend_host(tiered, bad_code)
+    assert e.value.status == xdrop.XD_EINVAL
+    bad_seed = synth.from_strings([("ACGT", "ACGT", 3, 0, 2)], X=3)
+    with pytest.raises(xdrop.XdError):
+        xdrop.extend_host(tiered, bad_seed)
+    neg_x = good.with_params(X=-1)
+    with pytest.raises(xdrop.XdError):
+        xdrop.extend_host(tiered, neg_x)
+    prot = synth.from_strings([("ACDE", "ACDE", 0, 0, 2)], alphabet="protein", X=3)
+    prot.matrix = None
+    with pytest.raises(xdrop.XdError):
+        xdrop.extend_host(tiered, prot)
+    # the context stays usable
+    assert_parity(xdrop.extend_host(tiered, good), good)
+
+
+def test_poll_unknown_ticket(tiered):
+    out = np.zeros(1, dtype=xdrop.RESULT_DTYPE)
+    with pytest.raises(xdrop.XdError) as e:
+        xdrop.xd_poll(tiered, 987654321, out, 0)
+    assert e.value.status == xdrop.XD_ENOTFOUND
