@@ -291,6 +291,8 @@ xd_status run_pipeline(xd_ctx* c, Scratch& s, const BatchView& b, xd_result* d_o
     XD_CUDA(c, mark(1));
     Problem P{};
     P.store = store;
+    P.n_words = std::max<uint64_t>(1, (b.n_codes + (b.alpha == 4 ? 15 : 5)) / (b.alpha == 4 ? 16 : 6));
+    P.max_abs = b.max_abs;
     P.units = static_cast<const Unit*>(s.units.p);
     P.results = d_out;
     P.err = err;

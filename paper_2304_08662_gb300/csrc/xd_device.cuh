@@ -33,6 +33,7 @@ static_assert(sizeof(Unit) == 32, "unit layout");
 // Everything a tier kernel needs about the batch.
 struct Problem {
     const uint32_t* store;      // packed residues of the whole codes buffer
+    uint64_t n_words;           // words in store
     const Unit* units;
     xd_result* results;         // per pair
     uint32_t* err;              // validation / wait error word
@@ -42,6 +43,7 @@ struct Problem {
     int32_t gap;
     int32_t X;
     uint32_t delta;             // 0 = unrestricted
+    int32_t max_abs;            // largest |score| of one step (similarity or gap)
     int8_t sim[400];            // alpha x alpha similarity, row-major with stride alpha
 };
 
