@@ -301,6 +301,8 @@ def main():
                                   "order": tim["order_ms"] / nb, "tiers": tier_ms,
                                   "totals": tim["totals_ms"] / nb},
                     "tier_units": [u / nb for u in tim["tier_units"]],
+                    "tier_cells": [c_ / nb for c_ in tim["tier_cells"]],
+                    "discarded_cells_per_step": tim["discarded_cells"] / nb,
                     "escalations_per_step": tim["escalations"] / nb,
                     "clocks": clk}
             print(json.dumps(line), flush=True)

@@ -63,11 +63,11 @@ cudaError_t grow_pinned(HostBuf& b, size_t bytes) {
 
 // Device working memory of one batch in flight.
 struct Scratch {
-    DevBuf store, units, bucket, order, q1, q2, ctr, hist, err, generic, bstats;
+    DevBuf store, units, bucket, order, q0, q1, q2, ctr, hist, err, generic, bstats;
 };
 
 void release(Scratch& s) {
-    for (DevBuf* b : {&s.store, &s.units, &s.bucket, &s.order, &s.q1, &s.q2, &s.ctr, &s.hist,
+    for (DevBuf* b : {&s.store, &s.units, &s.bucket, &s.order, &s.q0, &s.q1, &s.q2, &s.ctr, &s.hist,
                       &s.err, &s.generic, &s.bstats})
         release(*b);
 }
@@ -248,7 +248,7 @@ ScratchPlan plan_scratch(const xd_ctx* c, int alpha, uint64_t n_codes, uint32_t 
 }
 
 size_t plan_bytes(const ScratchPlan& p) {
-    return p.store + p.units + p.bucket + p.order + 2 * p.q + p.generic + 4096;
+    return p.store + p.units + p.bucket + p.order + 3 * p.q + p.generic + 4096;
 }
 
 cudaError_t ensure_scratch(Scratch& s, const ScratchPlan& p) {
@@ -257,6 +257,7 @@ cudaError_t ensure_scratch(Scratch& s, const ScratchPlan& p) {
     if ((e = grow(s.units, p.units)) != cudaSuccess) return e;
     if ((e = grow(s.bucket, p.bucket)) != cudaSuccess) return e;
     if ((e = grow(s.order, p.order)) != cudaSuccess) return e;
+    if ((e = grow(s.q0, p.q)) != cudaSuccess) return e;
     if ((e = grow(s.q1, p.q)) != cudaSuccess) return e;
     if ((e = grow(s.q2, p.q)) != cudaSuccess) return e;
     if ((e = grow(s.ctr, kNumCtr * 4)) != cudaSuccess) return e;
@@ -309,8 +310,9 @@ xd_status run_pipeline(xd_ctx* c, Scratch& s, const BatchView& b, xd_result* d_o
     Queues Q{};
     Q.order = static_cast<const uint32_t*>(s.order.p);
     Q.n_units = 2 * b.n_pairs;
-    Q.q1 = static_cast<uint32_t*>(s.q1.p);
-    Q.q2 = static_cast<uint32_t*>(s.q2.p);
+    Q.q[0] = static_cast<uint32_t*>(s.q0.p);
+    Q.q[1] = static_cast<uint32_t*>(s.q1.p);
+    Q.q[2] = static_cast<uint32_t*>(s.q2.p);
     Q.ctr = static_cast<uint32_t*>(s.ctr.p);
     XD_CUDA(c, launch_order(static_cast<uint32_t*>(s.hist.p), Q.ctr, kNumCtr,
                             static_cast<const uint32_t*>(s.bucket.p), Q.n_units,
@@ -329,7 +331,7 @@ xd_status run_pipeline(xd_ctx* c, Scratch& s, const BatchView& b, xd_result* d_o
             XD_CUDA(c, mark(4));
             XD_CUDA(c, launch_wide(P, Q, c->tiers, st));
             XD_CUDA(c, mark(5));
-            launches += 2;
+            launches += 3;
         }
         XD_CUDA(c, launch_generic(P, Q, static_cast<int32_t*>(s.generic.p), plan.generic_stride,
                                   plan.generic_blocks, st));
@@ -351,12 +353,18 @@ xd_status run_pipeline(xd_ctx* c, Scratch& s, const BatchView& b, xd_result* d_o
     return XD_OK;
 }
 
+int env_int(const char* name, int dflt) {
+    const char* v = std::getenv(name);
+    return v && *v ? std::atoi(v) : dflt;
+}
+
 void default_tiers(xd_ctx* c) {
+    c->tiers.narrow_minb = env_int("XD_NARROW_MINB", 3);
     c->tiers.narrow_threads = 128;
-    c->tiers.narrow_blocks = c->n_sm * 4;
+    c->tiers.narrow_blocks = c->n_sm * env_int("XD_NARROW_BLOCKS_PER_SM", c->tiers.narrow_minb);
     c->tiers.wide_threads = 128;
-    c->tiers.wide_blocks = c->n_sm * 4;
-    c->tiers.chunk = 1;
+    c->tiers.wide_blocks = c->n_sm * env_int("XD_WIDE_BLOCKS_PER_SM", 4);
+    c->tiers.chunk = std::max(1, env_int("XD_CHUNK", 1));
 }
 
 }  // namespace

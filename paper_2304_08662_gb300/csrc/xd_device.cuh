@@ -47,15 +47,19 @@ struct Problem {
     int8_t sim[400];            // alpha x alpha similarity, row-major with stride alpha
 };
 
-// Queue state of one batch: unit lists per tier and their pull / append counters.
+// Queue state of one batch.  Tier 0 pulls the cost-ordered unit list; a side whose band
+// does not fit a tier is appended to the next queue: q[0] feeds the 256-slot warp tier,
+// q[1] the 1024-slot warp tier, q[2] the generic tier.
 struct Queues {
     const uint32_t* order;      // all units, most expensive first (tier-0 input)
     uint32_t n_units;
-    uint32_t* q1;               // units escalated to the wide tier
-    uint32_t* q2;               // units escalated to the generic tier
-    uint32_t* ctr;              // [0] tier-0 pull, [1] q1 length, [2] tier-1 pull,
-                                // [3] q2 length, [4] tier-2 pull
+    uint32_t* q[3];
+    uint32_t* ctr;              // [0] order pull; [1 + 2k] length of q[k]; [2 + 2k] pull of q[k]
 };
+
+__device__ __forceinline__ void push_unit(const Queues& Q, int k, uint32_t unit) {
+    Q.q[k][atomicAdd(&Q.ctr[1 + 2 * k], 1u)] = unit;
+}
 
 // Residue at absolute position pos of the packed store.
 // DNA: 16 residues of 2 bits per word.  Protein: 6 residues of 5 bits per word.

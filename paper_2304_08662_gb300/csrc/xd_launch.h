@@ -30,6 +30,7 @@ struct TierConfig {
     int narrow_blocks, narrow_threads;
     int wide_blocks, wide_threads;
     int chunk;                  // units pulled per queue access in tier 0
+    int narrow_minb;            // tier-0 register budget: resident 128-thread blocks per SM
 };
 cudaError_t launch_narrow(const Problem& P, const Queues& Q, const TierConfig& cfg, cudaStream_t st);
 cudaError_t launch_wide(const Problem& P, const Queues& Q, const TierConfig& cfg, cudaStream_t st);
