@@ -188,6 +188,18 @@ xd_status xd_set_timing(xd_ctx* ctx, int32_t enable);
  * XD_ENOTFOUND if no batch was recorded. */
 xd_status xd_get_timing(xd_ctx* ctx, xd_timing* out);
 
+/* Throughput microbenchmarks on the context's device: the measured integer/DPX
+ * denominators of the alignment kernels' roofline (the method is bound by plain integer
+ * arithmetic, Sec. 2.2 recurrence and X-Drop test).  op selects one instruction kind run
+ * as eight independent dependency chains per thread:
+ *   0 add, 1 max, 2 DPX add-max, 3 DPX 3-way max, 4 3-input logic, 5 multiply-add,
+ *   6 compare + select (two instructions), 7 byte permute, 8 DPX add-max on 16x2,
+ *   9 DPX 3-way max on 16x2, 10 max on 16x2,
+ * or op 100: the register tiers' complete DNA cell update on 32 in-register slots.
+ * *rate receives operations (op 100: cells) per second for the whole GPU.  Synchronous;
+ * runs for a few tens of milliseconds.  Errors: XD_EINVAL (unknown op), XD_EDEVICE. */
+xd_status xd_probe(xd_ctx* ctx, int32_t op, double* rate);
+
 /* Wait (bounded) for all in-flight work, then free every resource of the context. */
 xd_status xd_destroy(xd_ctx* ctx);
 

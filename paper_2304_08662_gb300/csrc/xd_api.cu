@@ -63,13 +63,15 @@ cudaError_t grow_pinned(HostBuf& b, size_t bytes) {
 
 // Device working memory of one batch in flight.
 struct Scratch {
-    DevBuf store, units, bucket, order, q0, q1, q2, ctr, hist, err, generic, bstats;
+    DevBuf store, units, bucket, order, ctr, hist, err, generic, bstats;
+    DevBuf q[kLevels];           // escalation queues, one per register level plus generic
 };
 
 void release(Scratch& s) {
-    for (DevBuf* b : {&s.store, &s.units, &s.bucket, &s.order, &s.q0, &s.q1, &s.q2, &s.ctr, &s.hist,
-                      &s.err, &s.generic, &s.bstats})
+    for (DevBuf* b : {&s.store, &s.units, &s.bucket, &s.order, &s.ctr, &s.hist, &s.err, &s.generic,
+                      &s.bstats})
         release(*b);
+    for (DevBuf& q : s.q) release(q);
 }
 
 // A batch as the device pipeline sees it (device pointers).
@@ -133,7 +135,7 @@ struct xd_ctx {
     uint32_t reserved_len = 0;
     cudaStream_t dev_stream = nullptr;
     bool generic_only = false;
-    TierConfig tiers{};
+    TierConfig tiers{}, tiers_small_x{}, tiers_large_x{};
     DevBuf stats;                // uint64 [16]: cumulative per-batch counters (see Problem::stats)
     uint64_t batches = 0, pairs = 0, launches = 0;
     bool timing = false;
@@ -248,7 +250,7 @@ ScratchPlan plan_scratch(const xd_ctx* c, int alpha, uint64_t n_codes, uint32_t 
 }
 
 size_t plan_bytes(const ScratchPlan& p) {
-    return p.store + p.units + p.bucket + p.order + 3 * p.q + p.generic + 4096;
+    return p.store + p.units + p.bucket + p.order + kLevels * p.q + p.generic + 4096;
 }
 
 cudaError_t ensure_scratch(Scratch& s, const ScratchPlan& p) {
@@ -257,14 +259,58 @@ cudaError_t ensure_scratch(Scratch& s, const ScratchPlan& p) {
     if ((e = grow(s.units, p.units)) != cudaSuccess) return e;
     if ((e = grow(s.bucket, p.bucket)) != cudaSuccess) return e;
     if ((e = grow(s.order, p.order)) != cudaSuccess) return e;
-    if ((e = grow(s.q0, p.q)) != cudaSuccess) return e;
-    if ((e = grow(s.q1, p.q)) != cudaSuccess) return e;
-    if ((e = grow(s.q2, p.q)) != cudaSuccess) return e;
+    for (DevBuf& q : s.q)
+        if ((e = grow(q, p.q)) != cudaSuccess) return e;
     if ((e = grow(s.ctr, kNumCtr * 4)) != cudaSuccess) return e;
     if ((e = grow(s.hist, 64 * 4)) != cudaSuccess) return e;
     if ((e = grow(s.err, 16)) != cudaSuccess) return e;
     if ((e = grow(s.bstats, 16 * 8)) != cudaSuccess) return e;
     return grow(s.generic, p.generic);
+}
+
+int env_int(const char* name, int dflt) {
+    const char* v = std::getenv(name);
+    return v && *v ? std::atoi(v) : dflt;
+}
+
+// Register-level chains.  The first level's window should hold the typical live band of
+// the batch's X (a few tens of cells for X up to ~30 with DNA scoring); wider bands escalate.
+void set_chain(TierConfig& t, std::initializer_list<int> vs) {
+    t.n_levels = 0;
+    for (int v : vs) t.variant[t.n_levels++] = v;
+}
+
+void default_tiers(xd_ctx* c) {
+    TierConfig& t = c->tiers;
+    for (int v = 0; v < kNumGroupVariants; v++) t.blocks_per_sm[v] = 3;
+    t.blocks_per_sm[kG1C32] = 2;
+    t.blocks_per_sm[kG32C32] = 2;
+    t.chunk = std::max(1, env_int("XD_CHUNK", 1));
+    t.fused = env_int("XD_FUSED", 1) != 0;
+    t.every1 = std::max(0, env_int("XD_EVERY1", 4));
+    t.every2 = std::max(0, env_int("XD_EVERY2", 16));
+    set_chain(t, {kG1C32, kG16C16, kG32C16, kG32C32});
+    c->tiers_small_x = t;
+    set_chain(c->tiers_small_x, {kG1C16, kG4C16, kG16C16, kG32C32});
+    c->tiers_large_x = t;
+    set_chain(c->tiers_large_x, {kG4C16, kG16C16, kG32C32});
+    if (const char* ch = std::getenv("XD_CHAIN")) {
+        // comma-separated variant ids, used for every X
+        TierConfig forced = t;
+        forced.n_levels = 0;
+        for (const char* q = ch; *q && forced.n_levels < kLevels - 1;) {
+            forced.variant[forced.n_levels++] = std::atoi(q);
+            while (*q && *q != ',') q++;
+            if (*q == ',') q++;
+        }
+        c->tiers = c->tiers_small_x = c->tiers_large_x = forced;
+    }
+}
+
+const TierConfig& tiers_for(const xd_ctx* c, const BatchView& b) {
+    if (b.X <= 15) return c->tiers_small_x;
+    if (b.X <= 30) return c->tiers;
+    return c->tiers_large_x;
 }
 
 // The hot path of one batch (Sec. 3 method on every side extension), all on stream st.
@@ -310,9 +356,10 @@ xd_status run_pipeline(xd_ctx* c, Scratch& s, const BatchView& b, xd_result* d_o
     Queues Q{};
     Q.order = static_cast<const uint32_t*>(s.order.p);
     Q.n_units = 2 * b.n_pairs;
-    Q.q[0] = static_cast<uint32_t*>(s.q0.p);
-    Q.q[1] = static_cast<uint32_t*>(s.q1.p);
-    Q.q[2] = static_cast<uint32_t*>(s.q2.p);
+    for (int k = 0; k < kLevels; k++) {
+        Q.q[k] = static_cast<uint32_t*>(s.q[k].p);
+        if (!Q.q[k]) return fail(c, XD_EDEVICE, "escalation queue not allocated");
+    }
     Q.ctr = static_cast<uint32_t*>(s.ctr.p);
     XD_CUDA(c, launch_order(static_cast<uint32_t*>(s.hist.p), Q.ctr, kNumCtr,
                             static_cast<const uint32_t*>(s.bucket.p), Q.n_units,
@@ -327,11 +374,23 @@ xd_status run_pipeline(xd_ctx* c, Scratch& s, const BatchView& b, xd_result* d_o
             XD_CUDA(c, mark(4));
             XD_CUDA(c, mark(5));
         } else {
-            XD_CUDA(c, launch_narrow(P, Q, c->tiers, st));
-            XD_CUDA(c, mark(4));
-            XD_CUDA(c, launch_wide(P, Q, c->tiers, st));
+            const TierConfig& tc = tiers_for(c, b);
+            int lv = 0;
+            if (tc.fused && fused_supported(tc)) {
+                // the live queues' slots start unpublished
+                XD_CUDA(c, cudaMemsetAsync(Q.q[0], 0xff, sizeof(uint32_t) * size_t(Q.n_units), st));
+                XD_CUDA(c, cudaMemsetAsync(Q.q[1], 0xff, sizeof(uint32_t) * size_t(Q.n_units), st));
+                XD_CUDA(c, launch_fused_levels(P, Q, tc, c->n_sm, st));
+                XD_CUDA(c, mark(4));
+                lv = 3;
+                launches += 1;
+            }
+            for (; lv < tc.n_levels; lv++) {
+                XD_CUDA(c, launch_level(P, Q, tc, lv, c->n_sm, st));
+                if (lv == 0) XD_CUDA(c, mark(4));
+                launches += 1;
+            }
             XD_CUDA(c, mark(5));
-            launches += 3;
         }
         XD_CUDA(c, launch_generic(P, Q, static_cast<int32_t*>(s.generic.p), plan.generic_stride,
                                   plan.generic_blocks, st));
@@ -351,20 +410,6 @@ xd_status run_pipeline(xd_ctx* c, Scratch& s, const BatchView& b, xd_result* d_o
     c->batches += 1;
     c->pairs += b.n_pairs;
     return XD_OK;
-}
-
-int env_int(const char* name, int dflt) {
-    const char* v = std::getenv(name);
-    return v && *v ? std::atoi(v) : dflt;
-}
-
-void default_tiers(xd_ctx* c) {
-    c->tiers.narrow_minb = env_int("XD_NARROW_MINB", 3);
-    c->tiers.narrow_threads = 128;
-    c->tiers.narrow_blocks = c->n_sm * env_int("XD_NARROW_BLOCKS_PER_SM", c->tiers.narrow_minb);
-    c->tiers.wide_threads = 128;
-    c->tiers.wide_blocks = c->n_sm * env_int("XD_WIDE_BLOCKS_PER_SM", 4);
-    c->tiers.chunk = std::max(1, env_int("XD_CHUNK", 1));
 }
 
 }  // namespace
@@ -618,6 +663,17 @@ xd_status xd_get_timing(xd_ctx* c, xd_timing* out) {
     out->escalations = d[3];
     out->discarded_cells = d[7];
     out->launches = c->launches - c->launches_at_enable;
+    return XD_OK;
+}
+
+xd_status xd_probe(xd_ctx* c, int32_t op, double* rate) {
+    if (!c || !rate) return XD_EINVAL;
+    if (!((op >= 0 && op <= 10) || op == 100)) return fail(c, XD_EINVAL, "unknown probe op");
+    std::lock_guard<std::mutex> lk(c->mu);
+    XD_CUDA(c, cudaSetDevice(c->device));
+    XD_CUDA(c, cudaDeviceSynchronize());
+    float ms = 0;
+    XD_CUDA(c, probe_rate(op, c->n_sm, rate, &ms));
     return XD_OK;
 }
 

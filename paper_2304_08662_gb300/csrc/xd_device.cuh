@@ -47,13 +47,15 @@ struct Problem {
     int8_t sim[400];            // alpha x alpha similarity, row-major with stride alpha
 };
 
-// Queue state of one batch.  Tier 0 pulls the cost-ordered unit list; a side whose band
-// does not fit a tier is appended to the next queue: q[0] feeds the 256-slot warp tier,
-// q[1] the 1024-slot warp tier, q[2] the generic tier.
+// Queue state of one batch.  The first register level pulls the cost-ordered unit list;
+// a side whose band does not fit a level's window is appended to the next level's queue.
+// q[kLevels - 1] feeds the generic tier.
+constexpr int kLevels = 5;
+
 struct Queues {
-    const uint32_t* order;      // all units, most expensive first (tier-0 input)
+    const uint32_t* order;      // all units, most expensive first (first level's input)
     uint32_t n_units;
-    uint32_t* q[3];
+    uint32_t* q[kLevels];
     uint32_t* ctr;              // [0] order pull; [1 + 2k] length of q[k]; [2 + 2k] pull of q[k]
 };
 

@@ -231,13 +231,14 @@ __global__ void __launch_bounds__(128) k_generic(Problem P, Queues Q, int32_t* s
     const int lane = threadIdx.x & 31;
     const uint64_t warp = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
     int32_t* A = scratch + warp * 3 * stride;
-    const uint32_t n_q = *reinterpret_cast<volatile uint32_t*>(&Q.ctr[5]);
+    constexpr int G = kLevels - 1;
+    const uint32_t n_q = *reinterpret_cast<volatile uint32_t*>(&Q.ctr[1 + 2 * G]);
     for (;;) {
         uint32_t k = 0;
-        if (lane == 0) k = atomicAdd(&Q.ctr[6], 1u);
+        if (lane == 0) k = atomicAdd(&Q.ctr[2 + 2 * G], 1u);
         k = __shfl_sync(0xffffffffu, k, 0);
         if (k >= n_q) break;
-        const Unit u = P.units[Q.q[2][k]];
+        const Unit u = P.units[Q.q[G][k]];
         extend_generic(P, u, A, A + stride, A + 2 * stride, sim, lane);
     }
 }
@@ -245,8 +246,8 @@ __global__ void __launch_bounds__(128) k_generic(Problem P, Queues Q, int32_t* s
 // Queue every unit to the generic tier (used when the register tiers are disabled).
 __global__ void k_route_all_generic(Queues Q) {
     uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < Q.n_units) Q.q[2][t] = Q.order[t];
-    if (t == 0) Q.ctr[5] = Q.n_units;
+    if (t < Q.n_units) Q.q[kLevels - 1][t] = Q.order[t];
+    if (t == 0) Q.ctr[1 + 2 * (kLevels - 1)] = Q.n_units;
 }
 
 // ---------------------------------------------------------------------------------------

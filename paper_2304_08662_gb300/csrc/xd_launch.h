@@ -5,7 +5,7 @@
 
 namespace xd {
 
-constexpr int kNumCtr = 8;
+constexpr int kNumCtr = 4 + 2 * kLevels;   // last two: producer warps finished (fused levels)
 
 cudaError_t launch_pack(int alpha, const uint8_t* codes, uint64_t n_codes, uint32_t* store,
                         uint32_t* err, int n_sm, cudaStream_t st);
@@ -25,14 +25,37 @@ cudaError_t launch_totals(const xd_pair* pairs, uint32_t n_pairs, const uint64_t
 cudaError_t launch_accumulate(const unsigned long long* batch, unsigned long long* total, int n,
                               cudaStream_t st);
 
-// Register tiers (xd_tiers.cu).  tier 0: one thread per unit; tier 1: one warp per unit.
-struct TierConfig {
-    int narrow_blocks, narrow_threads;
-    int wide_blocks, wide_threads;
-    int chunk;                  // units pulled per queue access in tier 0
-    int narrow_minb;            // tier-0 register budget: resident 128-thread blocks per SM
+// Register tiers (xd_tiers.cu): a chain of up to kLevels - 1 register levels, each a
+// group kernel with G lanes per side extension and CG slots per lane (window G * CG),
+// followed by the generic tier.  Variant ids name the compiled (G, CG) pairs.
+enum GroupVariant {
+    kG1C16 = 0, kG1C32 = 1, kG4C16 = 2, kG8C16 = 3, kG16C16 = 4, kG32C16 = 5, kG32C32 = 6,
+    kNumGroupVariants = 7
 };
-cudaError_t launch_narrow(const Problem& P, const Queues& Q, const TierConfig& cfg, cudaStream_t st);
-cudaError_t launch_wide(const Problem& P, const Queues& Q, const TierConfig& cfg, cudaStream_t st);
+
+struct TierConfig {
+    int n_levels;                       // register levels before the generic tier
+    int variant[kLevels - 1];           // GroupVariant of each level
+    int blocks_per_sm[kNumGroupVariants];
+    int chunk;                          // units pulled per queue access (single-lane groups)
+    bool fused;                         // fuse levels 0-2 into one persistent grid
+    int every1, every2;                 // fused grid: warps starting in role 1 / role 2
+};
+
+// Runs register level `level` of the chain: pulls the cost-ordered list (level 0) or
+// q[level - 1], escalates to q[level] (the generic queue after the last level).
+cudaError_t launch_level(const Problem& P, const Queues& Q, const TierConfig& cfg, int level,
+                         int n_sm, cudaStream_t st);
+int variant_window(int variant);
+
+// Levels 0-2 fused into one cooperatively launched persistent grid (consumers of the
+// escalation queues start while the narrower levels still run).  Only some variant
+// triples are compiled.
+bool fused_supported(const TierConfig& cfg);
+cudaError_t launch_fused_levels(const Problem& P, const Queues& Q, const TierConfig& cfg, int n_sm,
+                                cudaStream_t st);
+
+// Throughput probes (xd_roof.cu).
+cudaError_t probe_rate(int op, int n_sm, double* rate, float* ms);
 
 }  // namespace xd

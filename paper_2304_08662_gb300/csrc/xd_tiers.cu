@@ -1,28 +1,27 @@
-// Register tiers of the X-Drop library.
+// Register tiers of the X-Drop library: one templated group kernel.
 //
-// Slot layout shared by both tiers.  The live band of the paper's sweep (Sec. 3,
-// Algorithm 1) is a few tens to a few hundred cells for realistic X, so the two previous
-// anti-diagonals of a side extension live in registers: a window of W slots per
-// anti-diagonal, where slot s of anti-diagonal d holds cell i = floor(d/2) + rb + s.  In
-// these coordinates the diagonal predecessor S(i-1, j-1) sits in the same slot two
-// anti-diagonals back, the two gap predecessors sit in slots (s-1, s) on odd d and
-// (s, s+1) on even d, and a band that follows the main diagonal does not move; it only
-// drifts with the indels of the alignment.  The window is re-centred when the band nears
-// its edge (one guard slot on each side keeps the gap predecessors of the band's end
-// cells), and a side whose band outgrows the window is handed to the next tier, which
-// restarts it.  The two anti-diagonals are the paper's memory-restricted pair (Gotoh's
-// two-diagonal scheme, Sec. 3): the new anti-diagonal overwrites d-2 slot by slot.
+// A side extension is owned by a group of G lanes (G = 1 .. 32); lane l of the group holds
+// slots [l*CG, (l+1)*CG) of a window of W = G*CG slots per anti-diagonal.  Slot s of
+// anti-diagonal d holds cell i = floor(d/2) + rb + s.  In these coordinates the diagonal
+// predecessor S(i-1, j-1) sits in the same slot two anti-diagonals back and the two gap
+// predecessors sit in slots (s-1, s) on odd d and (s, s+1) on even d, so a band that
+// follows the main diagonal does not move in the window; it drifts only with the indels of
+// the alignment.  The window is re-centred through shared memory when the band nears its
+// edge (one guard slot on each side holds the gap predecessors of the band's end cells).
+// A side whose band outgrows the window is appended to the next level's queue and
+// restarted there with a wider window.  The two anti-diagonals are the paper's
+// memory-restricted pair (Gotoh's two-diagonal scheme, Sec. 3): the new anti-diagonal
+// overwrites d-2 slot by slot.
 //
-// Tier 0 ("narrow"): one thread per side extension, W = 32 slots.
-// Tier 1 ("wide"):   one warp per side extension, W = 32 lanes x CW slots (256 or 1024);
-//                    lanes exchange the boundary slot with a shuffle and reduce the
-//                    anti-diagonal with REDUX.
+// Per anti-diagonal (Sec. 3, Algorithm 1): band [first live, last live + 1] of d-1 clipped
+// to the matrix and, when restricted, to delta_b cells centred on d-1's best cell; per cell
+// the recurrence of Sec. 2.2 as max(S(i-1,j-1) + Sim, max(S(i-1,j), S(i,j-1)) + gap) with
+// the DPX add-max, the X-Drop test against T of the completed anti-diagonals; then group
+// reductions of the live range and of the best cell (lowest i on ties).
 //
-// Per cell: the similarity from two packed 2-bit residue slices (xor + field test), the
-// recurrence of Sec. 2.2 as max(S(i-1,j-1) + Sim, max(S(i-1,j), S(i,j-1)) + gap) with the
-// DPX add-max, the X-Drop test against T of the completed anti-diagonals, a live bit for
-// the band update, and a key v * 64 + (63 - t) whose maximum yields both the best score
-// of the anti-diagonal and its lowest-i cell.
+// Residues: each lane keeps 2-bit slices of H and V for its slots.  On odd d the V slice
+// gains one residue, on even d the H slice does; residues come from two oriented streams per
+// lane whose next store word is always prefetched.
 #include <cstdint>
 #include <cuda_runtime.h>
 #include "xd_device.cuh"
@@ -30,7 +29,7 @@
 
 namespace xd {
 
-// Register tiers keep scores in a narrower range so that a (score, slot) key fits 32 bits.
+// Register levels keep scores in a narrower range so that a (score, slot) key fits 32 bits.
 constexpr int32_t kNegR = -(1 << 24);
 constexpr int32_t kDeadR = -(1 << 23);
 constexpr int64_t kRegLimit = int64_t(1) << 23;
@@ -43,27 +42,15 @@ __device__ __forceinline__ uint32_t ld_word(const uint32_t* store, uint64_t n_wo
     return __ldg(store + w);
 }
 
-// Three raw store words from which a 32-residue slice is cut; loaded ahead of use.
-struct Raw {
-    uint32_t a, b, c, sh;
-};
-
-// Words covering residues [p, p + 32) of the packed DNA store (positions outside the store
-// read clamped words; only cells outside the band ever use them).
-__device__ __forceinline__ Raw load_raw(const uint32_t* store, uint64_t nw, int64_t p) {
+// 32 residues from position p: field f (bits 2f, 2f+1) = residue p + f, or p + 31 - f
+// when rev.  Positions outside the store read clamped words (only cells outside the band
+// ever use them).
+__device__ __forceinline__ uint64_t slice_at(const uint32_t* store, uint64_t nw, int64_t p, bool rev) {
     const int64_t w = p >> 4;
-    Raw r;
-    r.a = ld_word(store, nw, w);
-    r.b = ld_word(store, nw, w + 1);
-    r.c = ld_word(store, nw, w + 2);
-    r.sh = uint32_t(p & 15) * 2u;
-    return r;
-}
-
-// Field f (bits 2f, 2f+1) = residue p + f, or residue p + 31 - f when rev.
-__device__ __forceinline__ uint64_t make_slice(const Raw& r, bool rev) {
-    const uint64_t lo = (uint64_t(r.b) << 32) | r.a;
-    uint64_t x = r.sh ? (lo >> r.sh) | (uint64_t(r.c) << (64 - r.sh)) : lo;
+    const uint32_t sh = uint32_t(p & 15) * 2u;
+    const uint64_t lo = (uint64_t(ld_word(store, nw, w + 1)) << 32) | ld_word(store, nw, w);
+    const uint64_t hi = ld_word(store, nw, w + 2);
+    uint64_t x = sh ? (lo >> sh) | (hi << (64 - sh)) : lo;
     if (rev) {
         x = __brevll(x);
         x = ((x >> 1) & 0x5555555555555555ull) | ((x & 0x5555555555555555ull) << 1);
@@ -71,90 +58,45 @@ __device__ __forceinline__ uint64_t make_slice(const Raw& r, bool rev) {
     return x;
 }
 
-// Slice positions.  Field t of the H slice is H_side[hpos + t]; field t of the V slice is
-// V_side[vpos - t].  H_side[k] = store[h0 + k] (right side) or store[h0 - k] (left side).
-__device__ __forceinline__ int64_t h_base(int64_t h0, uint32_t side, int64_t hpos) {
-    return side ? h0 - hpos - 31 : h0 + hpos;
-}
-__device__ __forceinline__ int64_t v_base(int64_t v0, uint32_t side, int64_t vpos) {
-    return side ? v0 - vpos : v0 + vpos - 31;
+// Oriented residue stream: next() returns store[p], store[p + dir], store[p + 2 dir], ...
+struct Stream {
+    int64_t word;      // index of cur
+    uint32_t cur, nxt; // current word and the following one (prefetched)
+    int32_t off;       // bit offset of the next residue in cur
+    int32_t dir;       // +1 or -1
+};
+
+__device__ __forceinline__ void stream_init(Stream& s, const uint32_t* store, uint64_t nw, int64_t p, int32_t dir) {
+    s.word = p >> 4;
+    s.off = int32_t(p & 15) * 2;
+    s.dir = dir;
+    s.cur = ld_word(store, nw, s.word);
+    s.nxt = ld_word(store, nw, s.word + dir);
 }
 
-// Per-side state shared by both tiers (replicated across the lanes of a warp in tier 1).
+__device__ __forceinline__ uint32_t stream_next(Stream& s, const uint32_t* store, uint64_t nw) {
+    const uint32_t c = (s.cur >> s.off) & 3u;
+    s.off += 2 * s.dir;
+    if (s.off < 0 || s.off > 30) {
+        s.word += s.dir;
+        s.cur = s.nxt;
+        s.nxt = ld_word(store, nw, s.word + s.dir);
+        s.off &= 31;
+    }
+    return c;
+}
+
+// Per-side state, replicated across the lanes of a group (slices and streams per lane).
 struct SideState {
     int64_t h0, v0;
     uint64_t cells;
-    uint64_t hs, vs;          // residue slices of the current window (this lane's slots)
-    Raw hn, vn;               // prefetched words of the next slice advance
-    int32_t m, n, d, rb;
+    uint64_t hs, vs;          // residue slices of this lane's slots
+    Stream sh, sv;            // next residue entering the H / V slice
+    int32_t m, n, d, rb, dir;
     int32_t L, U, T, best, bi, bj, barg;
     uint32_t flags, side;
     bool refresh;
 };
-
-// Band [lo, hi] of anti-diagonal d: [first live, last live + 1] of d-1 clipped to the
-// matrix (Algorithm 1), then to delta_b cells centred on d-1's best cell when restricted.
-__device__ __forceinline__ void band_of(const SideState& s, const Problem& P, int32_t d,
-                                        int32_t& lo, int32_t& hi, uint32_t& flags) {
-    lo = max(max(s.L, d - s.n), 0);
-    hi = min(min(s.U + 1, s.m), d);
-    if (P.delta && hi - lo + 1 > int32_t(P.delta)) {
-        flags |= 1u;
-        const int32_t start = min(s.barg - int32_t(P.delta >> 1), hi - int32_t(P.delta) + 1);
-        lo = max(lo, start);
-        hi = lo + int32_t(P.delta) - 1;
-    }
-}
-
-// Keep the slices in step with the window: the H slice advances on even d, the V slice on
-// odd d; the words of the next advance are always loaded one advance ahead.
-template <bool ODD>
-__device__ __forceinline__ void update_slices(SideState& s, const Problem& P, int64_t hpos, int64_t vpos) {
-    if (s.refresh) {
-        s.hs = make_slice(load_raw(P.store, P.n_words, h_base(s.h0, s.side, hpos)), s.side);
-        s.vs = make_slice(load_raw(P.store, P.n_words, v_base(s.v0, s.side, vpos)), !s.side);
-        s.hn = load_raw(P.store, P.n_words, h_base(s.h0, s.side, hpos + 1));
-        s.vn = load_raw(P.store, P.n_words, v_base(s.v0, s.side, vpos + 1));
-        s.refresh = false;
-    } else if (!ODD) {
-        s.hs = make_slice(s.hn, s.side);
-        s.hn = load_raw(P.store, P.n_words, h_base(s.h0, s.side, hpos + 1));
-    } else {
-        s.vs = make_slice(s.vn, !s.side);
-        s.vn = load_raw(P.store, P.n_words, v_base(s.v0, s.side, vpos + 1));
-    }
-}
-
-// Cells of one lane's CW slots.  P1 holds d-1, P2 holds d-2 and receives d.  upb / lfb are
-// the neighbours beyond the lane's first / last slot (another lane's, or -inf).
-template <int CW, bool ODD>
-__device__ __forceinline__ void cells_of(int32_t (&P1)[CW], int32_t (&P2)[CW], int32_t upb,
-                                         int32_t lfb, uint64_t x, uint32_t bm, int32_t thr,
-                                         int32_t gap, int32_t mat, int32_t mis, int32_t& kmax,
-                                         uint32_t& lm) {
-    kmax = INT32_MIN;
-    lm = 0;
-#pragma unroll
-    for (int t = 0; t < CW; t++) {
-        const int32_t up = ODD ? (t > 0 ? P1[t - 1] : upb) : P1[t];
-        const int32_t lf = ODD ? P1[t] : (t < CW - 1 ? P1[t + 1] : lfb);
-        const int32_t sig = ((x >> (2 * t)) & 3ull) ? mis : mat;
-        const int32_t raw = __viaddmax_s32(max(up, lf), gap, P2[t] + sig);
-        const bool live = raw >= thr && ((bm >> t) & 1u);
-        const int32_t v = live ? raw : kNegR;
-        P2[t] = v;
-        lm |= live ? (1u << t) : 0u;
-        kmax = max(kmax, v * 64 + (63 - t));
-    }
-}
-
-__device__ __forceinline__ uint32_t slot_mask(int32_t from, int32_t to, int cw) {
-    // bits [from, to] of a cw-bit lane mask, empty when the range misses the lane
-    const int32_t a = max(from, 0), b = min(to + 1, cw);
-    if (a >= b) return 0u;
-    const uint64_t m = ((1ull << b) - 1ull) & ~((1ull << a) - 1ull);
-    return uint32_t(m);
-}
 
 __device__ __forceinline__ void init_side(SideState& s, const Unit& u, int32_t rb) {
     s.h0 = int64_t(u.h0);
@@ -162,6 +104,7 @@ __device__ __forceinline__ void init_side(SideState& s, const Unit& u, int32_t r
     s.m = int32_t(u.m);
     s.n = int32_t(u.n);
     s.side = u.side;
+    s.dir = u.side ? -1 : 1;
     s.rb = rb;
     s.d = 1;
     s.L = s.U = 0;
@@ -172,190 +115,152 @@ __device__ __forceinline__ void init_side(SideState& s, const Unit& u, int32_t r
     s.refresh = true;
 }
 
-// ---------------------------------------------------------------------------------------
-// Tier 0: one thread per side extension, 32 slots.
+// Slot t of this lane pairs H_side[hb + t] with V_side[vb - t]; H_side[k] = store[h0 + dir k].
+template <int CG, bool ODD>
+__device__ __forceinline__ void update_slices(SideState& s, const Problem& P, int64_t hb, int64_t vb) {
+    if (s.refresh) {
+        s.hs = s.dir > 0 ? slice_at(P.store, P.n_words, s.h0 + hb, false)
+                         : slice_at(P.store, P.n_words, s.h0 - hb - 31, true);
+        if (CG < 32) s.hs &= (1ull << (2 * CG)) - 1ull;   // fields >= CG stay zero while shifting
+        s.vs = s.dir > 0 ? slice_at(P.store, P.n_words, s.v0 + vb - 31, true)
+                         : slice_at(P.store, P.n_words, s.v0 - vb, false);
+        stream_init(s.sh, P.store, P.n_words, s.h0 + s.dir * (hb + CG), s.dir);
+        stream_init(s.sv, P.store, P.n_words, s.v0 + s.dir * (vb + 1), s.dir);
+        s.refresh = false;
+    } else if (!ODD) {
+        const uint64_t c = stream_next(s.sh, P.store, P.n_words);
+        s.hs = (s.hs >> 2) | (c << (2 * (CG - 1)));
+    } else {
+        const uint64_t c = stream_next(s.sv, P.store, P.n_words);
+        s.vs = (s.vs << 2) | c;
+    }
+}
 
-template <bool ODD>
-__device__ __forceinline__ int narrow_step(SideState& s, int32_t (&P1)[32], int32_t (&P2)[32],
-                                           const Problem& P, int32_t mat, int32_t mis,
-                                           int32_t* shbuf, int stride) {
-    constexpr int C = 32;
+// Band [lo, hi] of anti-diagonal d: [first live, last live + 1] of d-1 clipped to the
+// matrix, then to delta_b cells centred on d-1's best cell when restricted.
+__device__ __forceinline__ void band_of(SideState& s, const Problem& P, int32_t d, int32_t& lo, int32_t& hi) {
+    lo = max(max(s.L, d - s.n), 0);
+    hi = min(min(s.U + 1, s.m), d);
+    if (P.delta && hi - lo + 1 > int32_t(P.delta)) {
+        s.flags |= 1u;
+        const int32_t start = min(s.barg - int32_t(P.delta >> 1), hi - int32_t(P.delta) + 1);
+        lo = max(lo, start);
+        hi = lo + int32_t(P.delta) - 1;
+    }
+}
+
+// The lane's CG cells.  P1 holds d-1, P2 holds d-2 and receives d.  upb / lfb are the
+// neighbours beyond the lane's first / last slot.  Returns the lane's live mask and the
+// maximum key v * 64 + (63 - t) over its cells (dead cells hold kNegR).
+template <int CG, bool ODD>
+__device__ __forceinline__ void cells_of(int32_t (&P1)[CG], int32_t (&P2)[CG], int32_t upb,
+                                         int32_t lfb, uint64_t x, uint32_t bm, int32_t thr,
+                                         int32_t gap, int32_t mat, int32_t mis, int32_t& kmax,
+                                         uint32_t& lm) {
+    kmax = INT32_MIN;
+    lm = 0;
+#pragma unroll
+    for (int t = 0; t < CG; t++) {
+        const int32_t up = ODD ? (t > 0 ? P1[t - 1] : upb) : P1[t];
+        const int32_t lf = ODD ? P1[t] : (t < CG - 1 ? P1[t + 1] : lfb);
+        const int32_t sig = ((x >> (2 * t)) & 3ull) ? mis : mat;
+        const int32_t raw = __viaddmax_s32(max(up, lf), gap, P2[t] + sig);
+        const bool live = raw >= thr && ((bm >> t) & 1u);
+        const int32_t v = live ? raw : kNegR;
+        P2[t] = v;
+        lm |= live ? (1u << t) : 0u;
+        kmax = max(kmax, v * 64 + (63 - t));
+    }
+}
+
+template <int G>
+__device__ __forceinline__ int32_t gmax(int32_t v, uint32_t gm) {
+    if (G == 32) return __reduce_max_sync(0xffffffffu, v);
+#pragma unroll
+    for (int k = G / 2; k >= 1; k >>= 1) v = max(v, __shfl_xor_sync(gm, v, k));
+    return v;
+}
+
+template <int G>
+__device__ __forceinline__ int32_t gmin(int32_t v, uint32_t gm) {
+    if (G == 32) return __reduce_min_sync(0xffffffffu, v);
+#pragma unroll
+    for (int k = G / 2; k >= 1; k >>= 1) v = min(v, __shfl_xor_sync(gm, v, k));
+    return v;
+}
+
+__device__ __forceinline__ uint32_t slot_mask(int32_t from, int32_t to, int cw) {
+    const int32_t a = max(from, 0), b = min(to + 1, cw);
+    if (a >= b) return 0u;
+    return uint32_t(((1ull << b) - 1ull) & ~((1ull << a) - 1ull));
+}
+
+// One anti-diagonal of the group's side extension.
+template <int G, int CG, bool ODD>
+__device__ __forceinline__ int group_step(SideState& s, int32_t (&P1)[CG], int32_t (&P2)[CG],
+                                          const Problem& P, int32_t mat, int32_t mis, int gl,
+                                          uint32_t gm, int32_t* gsm) {
+    constexpr int W = G * CG;
     const int32_t d = s.d;
     int32_t ib = (d >> 1) + s.rb;
     int32_t lo, hi;
-    band_of(s, P, d, lo, hi, s.flags);
+    band_of(s, P, d, lo, hi);
     int32_t slo = lo - ib, shi = hi - ib;
-    if (slo < 1 || shi > C - 2) {
+    if (slo < 1 || shi > W - 2) {
         const int32_t w = hi - lo + 1;
-        if (w > C - 2) return kOverflow;
-        const int32_t k = slo - (1 + (C - 2 - w) / 2);
+        if (w > W - 2) return kOverflow;
+        const int32_t k = slo - (1 + (W - 2 - w) / 2);
+        // re-centre: every lane parks its slots in the group's shared row and reads back
+        // the slots k positions further
 #pragma unroll
-        for (int t = 0; t < C; t++) {
-            shbuf[t * stride] = P1[t];
-            shbuf[(C + t) * stride] = P2[t];
+        for (int t = 0; t < CG; t++) {
+            gsm[gl * CG + t] = P1[t];
+            gsm[W + gl * CG + t] = P2[t];
         }
+        if (G > 1) __syncwarp(gm);
 #pragma unroll
-        for (int t = 0; t < C; t++) {
-            const int src = t + k;
-            const bool in = src >= 0 && src < C;
-            P1[t] = in ? shbuf[src * stride] : kNegR;
-            P2[t] = in ? shbuf[(C + src) * stride] : kNegR;
+        for (int t = 0; t < CG; t++) {
+            const int src = gl * CG + t + k;
+            const bool in = src >= 0 && src < W;
+            P1[t] = in ? gsm[src] : kNegR;
+            P2[t] = in ? gsm[W + src] : kNegR;
         }
+        if (G > 1) __syncwarp(gm);
         s.rb += k;
         ib += k;
         slo -= k;
         shi -= k;
         s.refresh = true;
     }
-    update_slices<ODD>(s, P, int64_t(ib) - 1, int64_t(d) - ib - 1);
-    const uint32_t bm = (0xffffffffu >> (31 - shi)) & (0xffffffffu << slo);
-    const int32_t thr = max(s.T - P.X, kDeadR);
-    int32_t kmax;
-    uint32_t lm;
-    cells_of<C, ODD>(P1, P2, kNegR, kNegR, s.hs ^ s.vs, bm, thr, P.gap, mat, mis, kmax, lm);
-    s.cells += uint64_t(hi - lo + 1);
-    if (lm == 0) return kDone;
-    s.L = ib + __ffs(lm) - 1;
-    s.U = ib + 31 - __clz(lm);
-    const int32_t vmax = kmax >> 6;
-    const int32_t arg = ib + (63 - (kmax & 63));
-    if (vmax > s.T) {
-        s.T = vmax;
-        s.best = vmax;
-        s.bi = arg;
-        s.bj = d - arg;
-    }
-    s.barg = arg;
-    s.d = d + 1;
-    return d == s.m + s.n ? kDone : kCont;
-}
-
-template <int MINB>
-__global__ void __launch_bounds__(128, MINB) k_narrow(Problem P, Queues Q, int chunk) {
-    constexpr int C = 32;
-    extern __shared__ int32_t shift_smem[];
-    int32_t* shbuf = shift_smem + threadIdx.x;
-    const int stride = blockDim.x;
-    const int32_t mat = P.sim[0], mis = P.sim[1];
-    int32_t A[C], B[C];
-    SideState s{};
-    uint32_t uidx = 0, pair = 0, next = 0, end = 0;
-    bool active = false;
-    for (;;) {
-        if (!active) {
-            // pull the next unit; units this tier cannot run go to the wider tiers
-            bool got = false;
-            for (;;) {
-                if (next >= end) {
-                    const uint32_t base = atomicAdd(&Q.ctr[0], uint32_t(chunk));
-                    if (base >= Q.n_units) break;
-                    next = base;
-                    end = min(base + uint32_t(chunk), Q.n_units);
-                }
-                uidx = Q.order[next++];
-                const Unit u = P.units[uidx];
-                if ((int64_t(u.m) + u.n) * P.max_abs >= kRegLimit || P.alpha != 4) {
-                    push_unit(Q, 2, uidx);
-                    continue;
-                }
-                init_side(s, u, -C / 2);
-                pair = u.pair;
-                got = true;
-                break;
-            }
-            if (!got) break;
-            if (s.m + s.n == 0) {
-                write_side(P.results, pair, s.side, 0, 0, 0, 0, 1);
-                atomicAdd(&P.stats[0], 1ull);
-                atomicAdd(&P.stats[4], 1ull);
-                continue;
-            }
-            // S(0,0) = 0 in the middle of the window, every other cell -inf (Sec. 2.2)
-#pragma unroll
-            for (int t = 0; t < C; t++) {
-                A[t] = kNegR;
-                B[t] = kNegR;
-            }
-            A[C / 2] = 0;
-            active = true;
-        }
-        int r = narrow_step<true>(s, A, B, P, mat, mis, shbuf, stride);
-        if (r == kCont) r = narrow_step<false>(s, B, A, P, mat, mis, shbuf, stride);
-        if (r == kCont) continue;
-        active = false;
-        if (r == kDone) {
-            write_side(P.results, pair, s.side, s.best, uint32_t(s.bi), uint32_t(s.bj), s.flags, s.cells);
-            atomicAdd(&P.stats[0], 1ull);
-            atomicAdd(&P.stats[4], (unsigned long long)s.cells);
-        } else {
-            push_unit(Q, 0, uidx);
-            atomicAdd(&P.stats[3], 1ull);
-            atomicAdd(&P.stats[7], (unsigned long long)s.cells);
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------------------
-// Tier 1: one warp per side extension, 32 lanes x CW slots.  Lane l holds slots
-// [l*CW, (l+1)*CW).  Every lane computes the band bookkeeping redundantly; the
-// anti-diagonal's live range and best cell come from warp reductions.
-
-template <int CW, bool ODD>
-__device__ __forceinline__ int wide_step(SideState& s, int32_t (&P1)[CW], int32_t (&P2)[CW],
-                                         const Problem& P, int32_t mat, int32_t mis, int lane) {
-    constexpr int W = 32 * CW;
-    const int32_t d = s.d;
-    int32_t ib = (d >> 1) + s.rb;
-    int32_t lo, hi;
-    band_of(s, P, d, lo, hi, s.flags);
-    int32_t slo = lo - ib, shi = hi - ib;
-    if (slo < 1 || shi > W - 2) {
-        // re-centre by whole lanes; any band of up to W - 2 - CW cells can be placed
-        const int32_t w = hi - lo + 1;
-        if (w > W - 2 - CW) return kOverflow;
-        const int32_t target = (W - w) / 2;
-        const int32_t diff = slo - target;
-        const int32_t kl = diff >= 0 ? (diff + CW / 2) / CW : -((-diff + CW / 2) / CW);
-        const int src = lane + kl;
-        const bool in = src >= 0 && src < 32;
-#pragma unroll
-        for (int t = 0; t < CW; t++) {
-            const int32_t a = __shfl_sync(0xffffffffu, P1[t], src & 31);
-            const int32_t b = __shfl_sync(0xffffffffu, P2[t], src & 31);
-            P1[t] = in ? a : kNegR;
-            P2[t] = in ? b : kNegR;
-        }
-        s.rb += kl * CW;
-        ib += kl * CW;
-        slo -= kl * CW;
-        shi -= kl * CW;
-        s.refresh = true;
-    }
-    const int32_t sb = lane * CW;
-    update_slices<ODD>(s, P, int64_t(ib) - 1 + sb, int64_t(d) - ib - 1 - sb);
-    const uint32_t bm = slot_mask(slo - sb, shi - sb, CW);
+    const int32_t sb = gl * CG;
+    update_slices<CG, ODD>(s, P, int64_t(ib) - 1 + sb, int64_t(d) - ib - 1 - sb);
+    const uint32_t bm = slot_mask(slo - sb, shi - sb, CG);
     const int32_t thr = max(s.T - P.X, kDeadR);
     int32_t upb = kNegR, lfb = kNegR;
-    if (ODD) {
-        upb = __shfl_up_sync(0xffffffffu, P1[CW - 1], 1);
-        if (lane == 0) upb = kNegR;
-    } else {
-        lfb = __shfl_down_sync(0xffffffffu, P1[0], 1);
-        if (lane == 31) lfb = kNegR;
+    if (G > 1) {
+        if (ODD) {
+            upb = __shfl_up_sync(gm, P1[CG - 1], 1, G);
+            if (gl == 0) upb = kNegR;
+        } else {
+            lfb = __shfl_down_sync(gm, P1[0], 1, G);
+            if (gl == G - 1) lfb = kNegR;
+        }
     }
     int32_t kmax;
     uint32_t lm;
-    cells_of<CW, ODD>(P1, P2, upb, lfb, s.hs ^ s.vs, bm, thr, P.gap, mat, mis, kmax, lm);
+    cells_of<CG, ODD>(P1, P2, upb, lfb, s.hs ^ s.vs, bm, thr, P.gap, mat, mis, kmax, lm);
     s.cells += uint64_t(hi - lo + 1);
     const bool any = lm != 0;
-    if (__ballot_sync(0xffffffffu, any) == 0u) return kDone;
-    const int32_t first = __reduce_min_sync(0xffffffffu, any ? sb + __ffs(lm) - 1 : INT32_MAX);
-    const int32_t last = __reduce_max_sync(0xffffffffu, any ? sb + 31 - __clz(lm) : -1);
+    int32_t first = any ? sb + __ffs(lm) - 1 : INT32_MAX;
+    int32_t last = any ? sb + 31 - __clz(lm) : -1;
+    first = gmin<G>(first, gm);
+    if (first == INT32_MAX) return kDone;
+    last = gmax<G>(last, gm);
     s.L = ib + first;
     s.U = ib + last;
     const int32_t lv = kmax >> 6;
-    const int32_t wmax = __reduce_max_sync(0xffffffffu, lv);
-    const int32_t arg = ib + __reduce_min_sync(0xffffffffu, lv == wmax ? sb + (63 - (kmax & 63)) : INT32_MAX);
+    const int32_t wmax = gmax<G>(lv, gm);
+    const int32_t arg = ib + gmin<G>(lv == wmax ? sb + (63 - (kmax & 63)) : INT32_MAX, gm);
     if (wmax > s.T) {
         s.T = wmax;
         s.best = wmax;
@@ -367,82 +272,314 @@ __device__ __forceinline__ int wide_step(SideState& s, int32_t (&P1)[CW], int32_
     return d == s.m + s.n ? kDone : kCont;
 }
 
-template <int CW>
-__global__ void __launch_bounds__(128) k_wide(Problem P, Queues Q, int level) {
-    constexpr int W = 32 * CW;
-    const int lane = threadIdx.x & 31;
-    const int32_t mat = P.sim[0], mis = P.sim[1];
-    const uint32_t n_q = *reinterpret_cast<volatile uint32_t*>(&Q.ctr[1 + 2 * level]);
-    int32_t A[CW], B[CW];
-    SideState s{};
-    for (;;) {
-        uint32_t k = 0;
-        if (lane == 0) k = atomicAdd(&Q.ctr[2 + 2 * level], 1u);
-        k = __shfl_sync(0xffffffffu, k, 0);
-        if (k >= n_q) break;
-        const uint32_t uidx = Q.q[level][k];
-        const Unit u = P.units[uidx];
-        init_side(s, u, -W / 2);
-        // S(0,0) = 0 in the middle of the window (lane 16, slot 0), every other cell -inf
-#pragma unroll
-        for (int t = 0; t < CW; t++) {
-            A[t] = kNegR;
-            B[t] = kNegR;
+// Where a group takes its next side extension from.  A static source is a finished list
+// (the cost-ordered units, or a queue filled by an earlier launch).  A live source is a
+// queue that producers of the same launch may still append to: slots are reserved with an
+// atomic counter and published by storing the unit index over the kNoUnit sentinel.
+constexpr uint32_t kNoUnit = 0xffffffffu;
+constexpr uint32_t kMaxSpin = 1u << 24;
+
+struct Source {
+    const uint32_t* list;
+    uint32_t* pull;             // pull counter
+    uint32_t n;                 // length of a static source
+    bool live;
+    uint32_t* reserve;          // live: length counter
+    uint32_t* producers_done;   // live: producer warps that have finished
+    uint32_t n_producers;
+};
+
+// Next unit for the group (group-uniform result).  Returns false when the source is
+// exhausted.  Waits on a live source are bounded; a wait that gives up raises kErrWait.
+template <int G>
+__device__ __forceinline__ bool next_unit(const Source& S, int gl, int lane, uint32_t gm, int chunk,
+                                          uint32_t& next, uint32_t& end, uint32_t& uidx, uint32_t* err) {
+    if (!S.live) {
+        if (next >= end) {
+            uint32_t base = 0;
+            const uint32_t take = G == 1 ? uint32_t(chunk) : 1u;
+            if (gl == 0) base = atomicAdd(S.pull, take);
+            if (G > 1) base = __shfl_sync(gm, base, lane - gl);
+            if (base >= S.n) return false;
+            next = base;
+            end = min(base + take, S.n);
         }
-        if (lane == 16) A[0] = 0;
-        int r = kDone;
-        if (s.m + s.n > 0) {
-            for (;;) {
-                r = wide_step<CW, true>(s, A, B, P, mat, mis, lane);
-                if (r != kCont) break;
-                r = wide_step<CW, false>(s, B, A, P, mat, mis, lane);
-                if (r != kCont) break;
+        uidx = S.list[next++];
+        return true;
+    }
+    uint32_t u = kNoUnit;
+    int got = 0;
+    if (gl == 0) {
+        const uint32_t ticket = atomicAdd(S.pull, 1u);
+        for (uint32_t it = 0;; it++) {
+            if (ticket < atomicAdd(S.reserve, 0u)) {
+                const volatile uint32_t* slot = S.list + ticket;
+                uint32_t v = *slot;
+                for (uint32_t w = 0; v == kNoUnit && w < kMaxSpin; w++) {
+                    __nanosleep(64);
+                    v = *slot;
+                }
+                if (v == kNoUnit) atomicOr(err, kErrWait);
+                else { u = v; got = 1; }
+                break;
             }
+            if (atomicAdd(S.producers_done, 0u) >= S.n_producers) {
+                __threadfence();
+                if (ticket < atomicAdd(S.reserve, 0u)) continue;   // a final push landed meanwhile
+                break;
+            }
+            if (it >= kMaxSpin) {
+                atomicOr(err, kErrWait);
+                break;
+            }
+            __nanosleep(256);
         }
-        if (lane == 0) {
+    }
+    if (G > 1) {
+        got = __shfl_sync(gm, got, lane - gl);
+        u = __shfl_sync(gm, u, lane - gl);
+    }
+    uidx = u;
+    return got != 0;
+}
+
+// Runs side extensions from S with groups of G lanes until S is exhausted; overflows go to
+// q[out_q].  gsm_block: the block's shared rows (2W ints per group).
+template <int G, int CG>
+__device__ __forceinline__ void group_loop(const Problem& P, const Queues& Q, const Source& S, int out_q,
+                                           int chunk, int32_t* gsm_block) {
+    constexpr int W = G * CG;
+    const int lane = threadIdx.x & 31;
+    const int gl = lane % G;
+    const uint32_t gm = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane - gl));
+    int32_t* gsm = gsm_block + (threadIdx.x / G) * 2 * W;
+    const int32_t mat = P.sim[0], mis = P.sim[1];
+    int32_t A[CG], B[CG];
+    SideState s{};
+    uint32_t uidx = 0, pair = 0, next = 0, end = 0;
+    bool active = false;
+    for (;;) {
+        if (!active) {
+            bool got = false;
+            while (next_unit<G>(S, gl, lane, gm, chunk, next, end, uidx, P.err)) {
+                const Unit u = P.units[uidx];
+                if ((int64_t(u.m) + u.n) * P.max_abs >= kRegLimit || P.alpha != 4) {
+                    if (gl == 0) push_unit(Q, kLevels - 1, uidx);
+                    continue;
+                }
+                init_side(s, u, -W / 2);
+                pair = u.pair;
+                got = true;
+                break;
+            }
+            if (!got) break;
+            if (s.m + s.n == 0) {
+                if (gl == 0) {
+                    write_side(P.results, pair, s.side, 0, 0, 0, 0, 1);
+                    atomicAdd(&P.stats[0], 1ull);
+                    atomicAdd(&P.stats[4], 1ull);
+                }
+                continue;
+            }
+            // S(0,0) = 0 in the middle of the window, every other cell -inf (Sec. 2.2)
+#pragma unroll
+            for (int t = 0; t < CG; t++) {
+                A[t] = kNegR;
+                B[t] = kNegR;
+            }
+            if (gl == (W / 2) / CG) A[(W / 2) % CG] = 0;
+            active = true;
+        }
+        int r = group_step<G, CG, true>(s, A, B, P, mat, mis, gl, gm, gsm);
+        if (r == kCont) r = group_step<G, CG, false>(s, B, A, P, mat, mis, gl, gm, gsm);
+        if (r == kCont) continue;
+        active = false;
+        if (gl == 0) {
             if (r == kDone) {
-                write_side(P.results, u.pair, s.side, s.best, uint32_t(s.bi), uint32_t(s.bj), s.flags, s.cells);
-                atomicAdd(&P.stats[1], 1ull);
-                atomicAdd(&P.stats[5], (unsigned long long)s.cells);
+                write_side(P.results, pair, s.side, s.best, uint32_t(s.bi), uint32_t(s.bj), s.flags, s.cells);
+                const int tier = W <= 32 ? 0 : 1;
+                atomicAdd(&P.stats[tier], 1ull);
+                atomicAdd(&P.stats[4 + tier], (unsigned long long)s.cells);
             } else {
-                push_unit(Q, level + 1, uidx);
+                push_unit(Q, out_q, uidx);
                 atomicAdd(&P.stats[3], 1ull);
                 atomicAdd(&P.stats[7], (unsigned long long)s.cells);
             }
         }
-        __syncwarp();
     }
 }
 
-template <int MINB>
-static cudaError_t launch_narrow_v(const Problem& P, const Queues& Q, const TierConfig& cfg, cudaStream_t st) {
-    constexpr int C = 32;
-    const size_t smem = size_t(2) * C * cfg.narrow_threads * sizeof(int32_t);
+__device__ __forceinline__ Source static_source(const Queues& Q, int in_q) {
+    Source S{};
+    S.list = in_q < 0 ? Q.order : Q.q[in_q];
+    S.pull = in_q < 0 ? &Q.ctr[0] : &Q.ctr[2 + 2 * in_q];
+    S.n = in_q < 0 ? Q.n_units : *reinterpret_cast<volatile uint32_t*>(&Q.ctr[1 + 2 * in_q]);
+    S.live = false;
+    return S;
+}
+
+// One register level over a finished list.  in_q < 0: the cost-ordered units, else q[in_q].
+template <int G, int CG, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_group(Problem P, Queues Q, int in_q, int out_q, int chunk) {
+    extern __shared__ int32_t group_smem[];
+    group_loop<G, CG>(P, Q, static_source(Q, in_q), out_q, chunk, group_smem);
+}
+
+// The first register levels fused into one persistent, cooperatively launched grid.
+// Each warp walks the role sequence 0 -> 1 -> 2: role 0 runs the cost-ordered units with
+// groups of G0 lanes and appends overflows to the live queue q[0]; role 1 consumes q[0]
+// with groups of G1 lanes and appends its overflows to the live queue q[1]; role 2
+// consumes q[1] with groups of G2 lanes, overflows go to q[2] for the later launches.
+// Some warps start directly in role 1 or 2, so wider sides begin while narrower levels
+// still run.  A warp that leaves role 0 (1) counts itself in done[0] (done[1]); consumers
+// stop once their queue is drained and all its producers have counted themselves.
+struct RolePlan {
+    int every1, every2;         // warp gw starts in role 2 if gw % every2 == every2 - 1,
+                                // else in role 1 if gw % every1 == 0, else in role 0
+    uint32_t producers0;        // warps that start in role 0
+    uint32_t producers1;        // warps that start in role 0 or 1
+};
+
+__host__ __device__ __forceinline__ int start_role(uint32_t gw, int every1, int every2) {
+    if (every2 > 0 && gw % uint32_t(every2) == uint32_t(every2 - 1)) return 2;
+    if (every1 > 0 && gw % uint32_t(every1) == 0) return 1;
+    return 0;
+}
+
+__device__ __forceinline__ Source live_source(const Queues& Q, int k, uint32_t* done, uint32_t producers) {
+    Source S{};
+    S.list = Q.q[k];
+    S.pull = &Q.ctr[2 + 2 * k];
+    S.live = true;
+    S.reserve = &Q.ctr[1 + 2 * k];
+    S.producers_done = done;
+    S.n_producers = producers;
+    return S;
+}
+
+__device__ __forceinline__ void signal_done(uint32_t* done) {
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) {
+        __threadfence();
+        atomicAdd(done, 1u);
+    }
+    __syncwarp();
+}
+
+template <int G0, int C0, int G1, int C1, int G2, int C2, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_fused(Problem P, Queues Q, RolePlan R, int chunk) {
+    extern __shared__ int32_t group_smem[];
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    uint32_t* done0 = &Q.ctr[1 + 2 * kLevels];
+    uint32_t* done1 = &Q.ctr[2 + 2 * kLevels];
+    const int role = start_role(gw, R.every1, R.every2);
+    if (role == 0) {
+        group_loop<G0, C0>(P, Q, static_source(Q, -1), 0, chunk, group_smem);
+        signal_done(done0);
+    }
+    if (role <= 1) {
+        group_loop<G1, C1>(P, Q, live_source(Q, 0, done0, R.producers0), 1, 1, group_smem);
+        signal_done(done1);
+    }
+    group_loop<G2, C2>(P, Q, live_source(Q, 1, done1, R.producers1), 2, 1, group_smem);
+}
+
+template <int G, int CG, int MINB>
+static cudaError_t launch_group(const Problem& P, const Queues& Q, int in_q, int out_q, int blocks,
+                                int chunk, cudaStream_t st) {
+    const size_t smem = size_t(128 / G) * 2 * G * CG * sizeof(int32_t);
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_narrow<MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        cudaError_t e = cudaFuncSetAttribute(k_group<G, CG, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k_narrow<MINB><<<cfg.narrow_blocks, cfg.narrow_threads, smem, st>>>(P, Q, cfg.chunk);
+    k_group<G, CG, MINB><<<blocks, 128, smem, st>>>(P, Q, in_q, out_q, chunk);
     return cudaGetLastError();
 }
 
-cudaError_t launch_narrow(const Problem& P, const Queues& Q, const TierConfig& cfg, cudaStream_t st) {
-    // register budget variants: 2 (255 registers), 3 (168), 4 (128) resident blocks per SM
-    switch (cfg.narrow_minb) {
-        case 2: return launch_narrow_v<2>(P, Q, cfg, st);
-        case 4: return launch_narrow_v<4>(P, Q, cfg, st);
-        default: return launch_narrow_v<3>(P, Q, cfg, st);
+template <int G, int CG>
+constexpr size_t group_smem_bytes() {
+    return size_t(128 / G) * 2 * G * CG * sizeof(int32_t);
+}
+
+template <int G0, int C0, int G1, int C1, int G2, int C2, int MINB>
+static cudaError_t launch_fused(const Problem& P, const Queues& Q, const TierConfig& cfg, int n_sm,
+                                cudaStream_t st) {
+    size_t smem = group_smem_bytes<G0, C0>();
+    if (group_smem_bytes<G1, C1>() > smem) smem = group_smem_bytes<G1, C1>();
+    if (group_smem_bytes<G2, C2>() > smem) smem = group_smem_bytes<G2, C2>();
+    auto fn = k_fused<G0, C0, G1, C1, G2, C2, MINB>;
+    static int occ = 0;
+    if (occ == 0) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 128, smem);
+        if (e != cudaSuccess) return e;
+        if (occ < 1) return cudaErrorInvalidConfiguration;
+    }
+    // every block must be resident at once: consumers wait for producers of the same grid
+    const int blocks = n_sm * occ;
+    const uint32_t n_warps = uint32_t(blocks) * 4;
+    RolePlan R{cfg.every1, cfg.every2, 0, 0};
+    for (uint32_t w = 0; w < n_warps; w++) {
+        const int r = start_role(w, R.every1, R.every2);
+        R.producers0 += r == 0;
+        R.producers1 += r <= 1;
+    }
+    Problem p = P;
+    Queues q = Q;
+    int ch = cfg.chunk;
+    void* args[] = {&p, &q, &R, &ch};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(fn), dim3(blocks), dim3(128), args, smem, st);
+}
+
+int variant_window(int v) {
+    switch (v) {
+        case kG1C16: return 16;
+        case kG1C32: return 32;
+        case kG4C16: return 64;
+        case kG8C16: return 128;
+        case kG16C16: return 256;
+        case kG32C16: return 512;
+        case kG32C32: return 1024;
+        default: return 0;
     }
 }
 
-cudaError_t launch_wide(const Problem& P, const Queues& Q, const TierConfig& cfg, cudaStream_t st) {
-    k_wide<8><<<cfg.wide_blocks, cfg.wide_threads, 0, st>>>(P, Q, 0);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k_wide<32><<<cfg.wide_blocks, cfg.wide_threads, 0, st>>>(P, Q, 1);
-    return cudaGetLastError();
+cudaError_t launch_level(const Problem& P, const Queues& Q, const TierConfig& cfg, int level,
+                         int n_sm, cudaStream_t st) {
+    const int v = cfg.variant[level];
+    const int in_q = level == 0 ? -1 : level - 1;
+    const int out_q = level == cfg.n_levels - 1 ? kLevels - 1 : level;
+    const int blocks = n_sm * cfg.blocks_per_sm[v];
+    switch (v) {
+        case kG1C16: return launch_group<1, 16, 3>(P, Q, in_q, out_q, blocks, cfg.chunk, st);
+        case kG1C32: return launch_group<1, 32, 2>(P, Q, in_q, out_q, blocks, cfg.chunk, st);
+        case kG4C16: return launch_group<4, 16, 3>(P, Q, in_q, out_q, blocks, cfg.chunk, st);
+        case kG8C16: return launch_group<8, 16, 3>(P, Q, in_q, out_q, blocks, cfg.chunk, st);
+        case kG16C16: return launch_group<16, 16, 3>(P, Q, in_q, out_q, blocks, cfg.chunk, st);
+        case kG32C16: return launch_group<32, 16, 3>(P, Q, in_q, out_q, blocks, cfg.chunk, st);
+        case kG32C32: return launch_group<32, 32, 2>(P, Q, in_q, out_q, blocks, cfg.chunk, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+bool fused_supported(const TierConfig& c) {
+    if (c.n_levels < 3) return false;
+    const int a = c.variant[0], b = c.variant[1], d = c.variant[2];
+    return (a == kG1C32 && b == kG16C16 && d == kG32C16) || (a == kG1C32 && b == kG8C16 && d == kG32C16) ||
+           (a == kG1C16 && b == kG4C16 && d == kG16C16) || (a == kG1C16 && b == kG8C16 && d == kG32C16);
+}
+
+cudaError_t launch_fused_levels(const Problem& P, const Queues& Q, const TierConfig& cfg, int n_sm,
+                                cudaStream_t st) {
+    const int a = cfg.variant[0], b = cfg.variant[1], d = cfg.variant[2];
+    if (a == kG1C32 && b == kG16C16 && d == kG32C16) return launch_fused<1, 32, 16, 16, 32, 16, 2>(P, Q, cfg, n_sm, st);
+    if (a == kG1C32 && b == kG8C16 && d == kG32C16) return launch_fused<1, 32, 8, 16, 32, 16, 2>(P, Q, cfg, n_sm, st);
+    if (a == kG1C16 && b == kG4C16 && d == kG16C16) return launch_fused<1, 16, 4, 16, 16, 16, 3>(P, Q, cfg, n_sm, st);
+    if (a == kG1C16 && b == kG8C16 && d == kG32C16) return launch_fused<1, 16, 8, 16, 32, 16, 3>(P, Q, cfg, n_sm, st);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace xd

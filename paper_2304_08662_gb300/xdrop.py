@@ -77,12 +77,13 @@ def lib():
         L.xd_get_stats.argtypes = [P, ctypes.POINTER(xd_stats)]
         L.xd_set_timing.argtypes = [P, ctypes.c_int32]
         L.xd_get_timing.argtypes = [P, ctypes.POINTER(xd_timing)]
+        L.xd_probe.argtypes = [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
         L.xd_destroy.argtypes = [P]
         L.xd_last_error.argtypes = [P]
         L.xd_last_error.restype = ctypes.c_char_p
         L.xd_version.restype = ctypes.c_char_p
         for name in ("xd_create", "xd_submit_batch", "xd_poll", "xd_run_device", "xd_reserve",
-                     "xd_device_status", "xd_get_stats", "xd_destroy", "xd_set_timing", "xd_get_timing"):
+                     "xd_device_status", "xd_get_stats", "xd_destroy", "xd_set_timing", "xd_get_timing", "xd_probe"):
             getattr(L, name).restype = ctypes.c_int
         _LIB = L
     return _LIB
@@ -211,6 +212,19 @@ def xd_get_timing(ctx):
             "tier_units": list(t.tier_units), "tier_cells": list(t.tier_cells),
             "escalations": t.escalations, "discarded_cells": t.discarded_cells,
             "launches": t.launches}
+
+
+PROBE_OPS = {"add": 0, "max": 1, "dpx_addmax": 2, "dpx_max3": 3, "lop3": 4, "imad": 5,
+             "cmp_sel": 6, "prmt": 7, "dpx_addmax_16x2": 8, "dpx_max3_16x2": 9, "max_16x2": 10,
+             "cell_dna": 100}
+
+
+def xd_probe(ctx, op):
+    r = ctypes.c_double()
+    rc = lib().xd_probe(ctx, PROBE_OPS.get(op, op) if isinstance(op, str) else int(op), ctypes.byref(r))
+    if rc != XD_OK:
+        raise XdError(rc, xd_last_error(ctx))
+    return r.value
 
 
 # ----------------------------------------------------------------------------- helpers

@@ -24,22 +24,26 @@ THREADS = max(1, os.cpu_count() or 1)
 FIELDS = ("score", "h_ext", "v_ext", "flags", "cells")
 
 
+MODES = {"tiered": {}, "generic": {"XD_TIERS": "generic"}, "split": {"XD_FUSED": "0"}}
+
+
 def _ctx(mode):
-    old = os.environ.get("XD_TIERS")
-    if mode == "generic":
-        os.environ["XD_TIERS"] = "generic"
-    else:
-        os.environ.pop("XD_TIERS", None)
+    keys = ("XD_TIERS", "XD_FUSED")
+    old = {k: os.environ.get(k) for k in keys}
+    for k in keys:
+        os.environ.pop(k, None)
+    os.environ.update(MODES[mode])
     try:
         return xdrop.xd_create(0)
     finally:
-        if old is None:
-            os.environ.pop("XD_TIERS", None)
-        else:
-            os.environ["XD_TIERS"] = old
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
 
 
-@pytest.fixture(scope="module", params=["tiered", "generic"])
+@pytest.fixture(scope="module", params=["tiered", "split", "generic"])
 def ctx(request):
     c = _ctx(request.param)
     yield c
