@@ -200,6 +200,28 @@ xd_status xd_get_timing(xd_ctx* ctx, xd_timing* out);
  * runs for a few tens of milliseconds.  Errors: XD_EINVAL (unknown op), XD_EDEVICE. */
 xd_status xd_probe(xd_ctx* ctx, int32_t op, double* rate);
 
+/* Allocation-free variant of xd_run_device (the paper has no counterpart: this exists for
+ * callers that cannot allocate device memory, such as code running in a host callback, a
+ * pipeline whose device memory is fixed up front, or a process whose memory is managed by
+ * another allocator under a strict budget).  It needs no context and calls no allocating
+ * routine: the caller passes device inputs (dev_batch as for xd_run_device) and the device
+ * output array d_out[n_pairs]; the anti-diagonal rows live in a 64 MiB array inside the
+ * library that every GPU loading the library keeps until the process exits.  Results are
+ * identical to xd_run_device.  It runs one warp per pair with the generic sweep, so it is
+ * much slower than xd_run_device.
+ *   max_side_len: an upper bound on every side's H length (h_seed and
+ *   length(H) - h_seed - seed_len); XD_EINVAL if three rows of max_side_len + 1 scores do
+ *   not fit the 64 MiB array.  Pairs with invalid inputs (bad ids, seeds outside their
+ *   sequence, codes outside the alphabet, a side longer than max_side_len) get flags bit 31
+ *   set on both sides instead of a result.
+ * The first call on a device looks up the array's device address with that device current
+ * (uses the calling thread's current device); make that first call before any stream
+ * capture.  The array is shared by all calls: calls that overlap on the GPU (for instance
+ * on two streams at once) race and give wrong results.  Asynchronous on `stream`.
+ * Errors: XD_EINVAL, XD_EDEVICE. */
+xd_status xd_run_device_noalloc(const xd_batch* dev_batch, uint32_t max_side_len, xd_result* d_out,
+                                void* stream);
+
 /* Wait (bounded) for all in-flight work, then free every resource of the context. */
 xd_status xd_destroy(xd_ctx* ctx);
 

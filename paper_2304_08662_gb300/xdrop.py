@@ -78,12 +78,13 @@ def lib():
         L.xd_set_timing.argtypes = [P, ctypes.c_int32]
         L.xd_get_timing.argtypes = [P, ctypes.POINTER(xd_timing)]
         L.xd_probe.argtypes = [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
+        L.xd_run_device_noalloc.argtypes = [ctypes.POINTER(xd_batch), ctypes.c_uint32, V, V]
         L.xd_destroy.argtypes = [P]
         L.xd_last_error.argtypes = [P]
         L.xd_last_error.restype = ctypes.c_char_p
         L.xd_version.restype = ctypes.c_char_p
         for name in ("xd_create", "xd_submit_batch", "xd_poll", "xd_run_device", "xd_reserve",
-                     "xd_device_status", "xd_get_stats", "xd_destroy", "xd_set_timing", "xd_get_timing", "xd_probe"):
+                     "xd_device_status", "xd_get_stats", "xd_destroy", "xd_set_timing", "xd_get_timing", "xd_probe", "xd_run_device_noalloc"):
             getattr(L, name).restype = ctypes.c_int
         _LIB = L
     return _LIB
@@ -170,6 +171,11 @@ def xd_run_device(ctx, args, d_out, stream=None):
     rc = lib().xd_run_device(ctx, ctypes.byref(args.c), _ptr(d_out), stream)
     if rc != XD_OK:
         raise XdError(rc, xd_last_error(ctx))
+
+
+def xd_run_device_noalloc(args, max_side_len, d_out, stream=None):
+    """Allocation-free run on device inputs (see include/xdrop.h); returns the status."""
+    return lib().xd_run_device_noalloc(ctypes.byref(args.c), int(max_side_len), _ptr(d_out), stream)
 
 
 def xd_reserve(ctx, n_codes, n_seqs, n_pairs, max_seq_len):
