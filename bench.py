@@ -304,6 +304,7 @@ def main():
                     "tier_cells": [c_ / nb for c_ in tim["tier_cells"]],
                     "discarded_cells_per_step": tim["discarded_cells"] / nb,
                     "escalations_per_step": tim["escalations"] / nb,
+                    "window_shifts_per_step": tim["window_shifts"] / nb,
                     "clocks": clk}
             print(json.dumps(line), flush=True)
     finally:

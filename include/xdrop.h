@@ -178,6 +178,7 @@ typedef struct {
     uint64_t escalations;
     uint64_t discarded_cells;
     uint64_t launches;           /* kernels the library launched */
+    uint64_t window_shifts;      /* register-window re-centrings */
 } xd_timing;
 
 /* enable != 0 synchronises the context, clears the timing sums and records stage events

@@ -63,13 +63,13 @@ cudaError_t grow_pinned(HostBuf& b, size_t bytes) {
 
 // Device working memory of one batch in flight.
 struct Scratch {
-    DevBuf store, units, bucket, order, ctr, hist, err, generic, bstats;
+    DevBuf store, units, bucket, order, ctr, hist, err, generic, bstats, rec, rec_of;
     DevBuf q[kLevels];           // escalation queues, one per register level plus generic
 };
 
 void release(Scratch& s) {
     for (DevBuf* b : {&s.store, &s.units, &s.bucket, &s.order, &s.ctr, &s.hist, &s.err, &s.generic,
-                      &s.bstats})
+                      &s.bstats, &s.rec, &s.rec_of})
         release(*b);
     for (DevBuf& q : s.q) release(q);
 }
@@ -103,24 +103,67 @@ struct Slot {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// Multi-threaded memcpy for large host staging copies.
-void par_memcpy(void* dst, const void* src, size_t n) {
-    const size_t kMin = size_t(64) << 20;
-    if (n < kMin) {
-        std::memcpy(dst, src, n);
-        return;
+// Residue check of one block: true if every byte is below alpha.  Eight bytes at a time.
+bool codes_valid(const uint8_t* p, size_t n, int alpha) {
+    size_t t = 0;
+    if (alpha == 4) {
+        uint64_t bad = 0;
+        for (; t + 8 <= n; t += 8) {
+            uint64_t w;
+            std::memcpy(&w, p + t, 8);
+            bad |= w & 0xFCFCFCFCFCFCFCFCull;
+        }
+        if (bad) return false;
+    } else {
+        for (; t + 8 <= n; t += 8) {
+            uint64_t w;
+            std::memcpy(&w, p + t, 8);
+            // a byte b >= 20 has bit 7 set in b or in b + 108 (a carry out of a byte that is
+            // itself >= 148 can only add to an already invalid word)
+            if ((w | (w + 0x6C6C6C6C6C6C6C6Cull)) & 0x8080808080808080ull) return false;
+        }
+    }
+    for (; t < n; t++)
+        if (p[t] >= alpha) return false;
+    return true;
+}
+
+// Copies n bytes to dst with up to 16 host threads; when alpha > 0 also checks that every
+// byte is a residue code below alpha (each block is checked right after it is copied, while
+// it is still in cache).  Returns the index of a block holding an invalid code, or SIZE_MAX.
+size_t par_copy_check(void* dst, const void* src, size_t n, int alpha) {
+    const size_t kBlock = size_t(256) << 10;
+    const size_t kMinParallel = size_t(32) << 20;
+    auto run = [&](size_t a, size_t b, std::atomic<size_t>* bad) {
+        for (size_t s = a; s < b; s += kBlock) {
+            const size_t e = std::min(b, s + kBlock);
+            std::memcpy(static_cast<char*>(dst) + s, static_cast<const char*>(src) + s, e - s);
+            if (alpha > 0 && !codes_valid(static_cast<const uint8_t*>(dst) + s, e - s, alpha)) {
+                size_t cur = bad->load();
+                while (s < cur && !bad->compare_exchange_weak(cur, s)) {
+                }
+            }
+        }
+    };
+    std::atomic<size_t> bad{SIZE_MAX};
+    if (n < kMinParallel) {
+        run(0, n, &bad);
+        return bad.load();
     }
     unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-    size_t per = align_up((n + hw - 1) / hw, 4096);
+    size_t per = align_up((n + hw - 1) / hw, kBlock);
     std::vector<std::thread> th;
     for (unsigned t = 0; t < hw; t++) {
         size_t a = t * per;
         if (a >= n) break;
         size_t b = std::min(n, a + per);
-        th.emplace_back([=] { std::memcpy(static_cast<char*>(dst) + a, static_cast<const char*>(src) + a, b - a); });
+        th.emplace_back(run, a, b, &bad);
     }
     for (auto& t : th) t.join();
+    return bad.load();
 }
+
+void par_memcpy(void* dst, const void* src, size_t n) { par_copy_check(dst, src, n, 0); }
 
 }  // namespace
 
@@ -205,9 +248,7 @@ xd_status validate_host(xd_ctx* c, const xd_batch* b, const BatchView& v, uint32
     if (b->n_pairs && (!b->pairs || !b->seq_offsets || !b->seq_lengths))
         return fail(c, XD_EINVAL, "null pointer in batch");
     if (b->n_codes && !b->seq_codes) return fail(c, XD_EINVAL, "null seq_codes");
-    const uint8_t lim = uint8_t(v.alpha);
-    for (uint64_t t = 0; t < b->n_codes; t++)
-        if (b->seq_codes[t] >= lim) return fail(c, XD_EINVAL, "residue code outside the alphabet at byte " + std::to_string(t));
+    // residue codes are checked while they are staged (par_copy_check)
     for (uint32_t s = 0; s < b->n_seqs; s++)
         if (b->seq_offsets[s] + b->seq_lengths[s] > b->n_codes)
             return fail(c, XD_EINVAL, "sequence " + std::to_string(s) + " extends past n_codes");
@@ -228,8 +269,14 @@ xd_status validate_host(xd_ctx* c, const xd_batch* b, const BatchView& v, uint32
     return XD_OK;
 }
 
+// Escalation-record pool: 256 ints per unit on average (a 32-slot record takes 80, a
+// 512-slot one 1040), at most 64 Mi ints.
+constexpr uint64_t kRecIntsPerUnit = 256;
+constexpr uint64_t kRecPoolMax = uint64_t(1) << 26;
+
 struct ScratchPlan {
-    size_t store, units, bucket, order, q, generic;
+    size_t store, units, bucket, order, q, generic, rec, rec_of;
+    uint32_t rec_cap;
     uint64_t generic_stride;
     int generic_blocks;
 };
@@ -243,6 +290,9 @@ ScratchPlan plan_scratch(const xd_ctx* c, int alpha, uint64_t n_codes, uint32_t 
     p.bucket = nu * 4;
     p.order = nu * 4;
     p.q = nu * 4;
+    p.rec_cap = uint32_t(std::min<uint64_t>(nu * kRecIntsPerUnit, kRecPoolMax));
+    p.rec = size_t(p.rec_cap) * 4;
+    p.rec_of = nu * 4;
     p.generic_blocks = c->n_sm * 2;
     p.generic_stride = align_up(uint64_t(max_len) + 1, 32);
     p.generic = size_t(p.generic_blocks) * 4 * 3 * p.generic_stride * 4;
@@ -250,7 +300,7 @@ ScratchPlan plan_scratch(const xd_ctx* c, int alpha, uint64_t n_codes, uint32_t 
 }
 
 size_t plan_bytes(const ScratchPlan& p) {
-    return p.store + p.units + p.bucket + p.order + kLevels * p.q + p.generic + 4096;
+    return p.store + p.units + p.bucket + p.order + kLevels * p.q + p.generic + p.rec + p.rec_of + 4096;
 }
 
 cudaError_t ensure_scratch(Scratch& s, const ScratchPlan& p) {
@@ -265,6 +315,8 @@ cudaError_t ensure_scratch(Scratch& s, const ScratchPlan& p) {
     if ((e = grow(s.hist, 64 * 4)) != cudaSuccess) return e;
     if ((e = grow(s.err, 16)) != cudaSuccess) return e;
     if ((e = grow(s.bstats, 16 * 8)) != cudaSuccess) return e;
+    if ((e = grow(s.rec, p.rec)) != cudaSuccess) return e;
+    if ((e = grow(s.rec_of, p.rec_of)) != cudaSuccess) return e;
     return grow(s.generic, p.generic);
 }
 
@@ -283,22 +335,22 @@ void set_chain(TierConfig& t, std::initializer_list<int> vs) {
 void default_tiers(xd_ctx* c) {
     TierConfig& t = c->tiers;
     for (int v = 0; v < kNumGroupVariants; v++) t.blocks_per_sm[v] = 3;
-    t.blocks_per_sm[kG1C32] = 2;
-    t.blocks_per_sm[kG32C32] = 2;
+    for (int v : {kG1C32, kG32C32, kG4C32, kG8C32, kG16C32}) t.blocks_per_sm[v] = 2;
     t.chunk = std::max(1, env_int("XD_CHUNK", 1));
     t.fused = env_int("XD_FUSED", 1) != 0;
     t.every1 = std::max(0, env_int("XD_EVERY1", 4));
     t.every2 = std::max(0, env_int("XD_EVERY2", 16));
+    t.fused_minb = env_int("XD_FUSED_MINB", 2);
     set_chain(t, {kG1C32, kG16C16, kG32C16, kG32C32});
     c->tiers_small_x = t;
-    set_chain(c->tiers_small_x, {kG1C16, kG4C16, kG16C16, kG32C32});
+    set_chain(c->tiers_small_x, {kG1C32, kG16C16, kG32C16, kG32C32});
     c->tiers_large_x = t;
     set_chain(c->tiers_large_x, {kG4C16, kG16C16, kG32C32});
     if (const char* ch = std::getenv("XD_CHAIN")) {
         // comma-separated variant ids, used for every X
         TierConfig forced = t;
         forced.n_levels = 0;
-        for (const char* q = ch; *q && forced.n_levels < kLevels - 1;) {
+        for (const char* q = ch; *q && forced.n_levels < kLevels - 2;) {
             forced.variant[forced.n_levels++] = std::atoi(q);
             while (*q && *q != ',') q++;
             if (*q == ',') q++;
@@ -344,6 +396,11 @@ xd_status run_pipeline(xd_ctx* c, Scratch& s, const BatchView& b, xd_result* d_o
     P.results = d_out;
     P.err = err;
     P.stats = static_cast<unsigned long long*>(s.bstats.p);
+    P.rec = static_cast<int32_t*>(s.rec.p);
+    P.rec_of = static_cast<uint32_t*>(s.rec_of.p);
+    P.rec_ctr = static_cast<uint32_t*>(s.ctr.p) + (3 + 2 * kLevels);
+    P.rec_cap = plan.rec_cap;
+    if (b.n_pairs) XD_CUDA(c, cudaMemsetAsync(s.rec_of.p, 0xff, size_t(2) * b.n_pairs * 4, st));
     P.alpha = b.alpha;
     P.gap = b.gap;
     P.X = b.X;
@@ -390,6 +447,8 @@ xd_status run_pipeline(xd_ctx* c, Scratch& s, const BatchView& b, xd_result* d_o
                 if (lv == 0) XD_CUDA(c, mark(4));
                 launches += 1;
             }
+            XD_CUDA(c, launch_band(P, Q, c->n_sm, st));
+            launches += 1;
             XD_CUDA(c, mark(5));
         }
         XD_CUDA(c, launch_generic(P, Q, static_cast<int32_t*>(s.generic.p), plan.generic_stride,
@@ -541,7 +600,12 @@ xd_status xd_submit_batch(xd_ctx* c, const xd_batch* b, uint64_t* ticket) {
     XD_CUDA(c, grow_pinned(slot->h_in, in_bytes));
     XD_CUDA(c, grow_pinned(slot->h_out, out_bytes));
     char* h = static_cast<char*>(slot->h_in.p);
-    par_memcpy(h + o_codes, b->seq_codes, b->n_codes);
+    const size_t bad_block = par_copy_check(h + o_codes, b->seq_codes, b->n_codes, v.alpha);
+    if (bad_block != SIZE_MAX) {
+        size_t t = bad_block;
+        while (t < b->n_codes && b->seq_codes[t] < v.alpha) t++;
+        return fail(c, XD_EINVAL, "residue code outside the alphabet at byte " + std::to_string(t));
+    }
     std::memcpy(h + o_offs, b->seq_offsets, 8ull * b->n_seqs);
     std::memcpy(h + o_lens, b->seq_lengths, 4ull * b->n_seqs);
     std::memcpy(h + o_pairs, b->pairs, sizeof(xd_pair) * b->n_pairs);
@@ -662,6 +726,7 @@ xd_status xd_get_timing(xd_ctx* c, xd_timing* out) {
     }
     out->escalations = d[3];
     out->discarded_cells = d[7];
+    out->window_shifts = d[8];
     out->launches = c->launches - c->launches_at_enable;
     return XD_OK;
 }

@@ -44,13 +44,21 @@ struct Problem {
     int32_t X;
     uint32_t delta;             // 0 = unrestricted
     int32_t max_abs;            // largest |score| of one step (similarity or gap)
+    // Escalation records: a side that outgrows a register level's window saves its two
+    // anti-diagonals and band state so that the next level continues instead of restarting.
+    int32_t* rec;               // record pool of rec_cap ints
+    uint32_t* rec_of;           // per unit: offset of its record, or 0xffffffff (start from scratch)
+    uint32_t* rec_ctr;          // pool allocation counter (ints)
+    uint32_t rec_cap;
     int8_t sim[400];            // alpha x alpha similarity, row-major with stride alpha
 };
 
 // Queue state of one batch.  The first register level pulls the cost-ordered unit list;
 // a side whose band does not fit a level's window is appended to the next level's queue.
-// q[kLevels - 1] feeds the generic tier.
-constexpr int kLevels = 5;
+// q[kBandQ] feeds the shared-memory band tier, q[kGenericQ] the generic tier.
+constexpr int kLevels = 7;
+constexpr int kBandQ = kLevels - 2;
+constexpr int kGenericQ = kLevels - 1;
 
 struct Queues {
     const uint32_t* order;      // all units, most expensive first (first level's input)

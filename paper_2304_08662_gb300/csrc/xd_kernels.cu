@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(128) k_generic(Problem P, Queues Q, int32_t* s
     const int lane = threadIdx.x & 31;
     const uint64_t warp = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
     int32_t* A = scratch + warp * 3 * stride;
-    constexpr int G = kLevels - 1;
+    constexpr int G = kGenericQ;
     const uint32_t n_q = *reinterpret_cast<volatile uint32_t*>(&Q.ctr[1 + 2 * G]);
     for (;;) {
         uint32_t k = 0;
@@ -243,11 +243,201 @@ __global__ void __launch_bounds__(128) k_generic(Problem P, Queues Q, int32_t* s
     }
 }
 
+
+// ---------------------------------------------------------------------------------------
+// Band tier: one warp per side extension, the two previous anti-diagonals in a shared
+// memory ring of kBandW slots per row.  Slot s of anti-diagonal d is cell
+// i = floor(d/2) + rb + s (the register tiers' layout: the diagonal predecessor is the same
+// slot of row d-2, the gap predecessors slots s-1, s (odd d) or s, s+1 (even d) of row
+// d-1); slot s lives at ring position (s + base) mod kBandW, so re-centring the window
+// only moves base and clears the slots it exposes.  Each anti-diagonal is swept over its
+// band only, 32 cells at a time; the new anti-diagonal overwrites row d-2 in place, and
+// the two slots just outside the band are set to -inf so that the next two anti-diagonals
+// read correct neighbours.  Takes DNA and protein, any band up to kBandW - 2 cells, and
+// continues sides from escalation records of the register levels.
+constexpr int kBandW = 8192;
+
+__device__ __forceinline__ int32_t band_load_rec(const Problem& P, uint32_t ri, int32_t* R0, int32_t* R1,
+                                                 int32_t& rb, int64_t& d, int32_t& L, int32_t& U, int32_t& T,
+                                                 int32_t& best, int64_t& bi, int64_t& bj, int64_t& barg,
+                                                 uint32_t& flags, uint64_t& cells, int lane) {
+    const int32_t* r = P.rec + ri;
+    const int32_t w0 = __ldcg(r + 0);
+    const int32_t off = (kBandW - w0) / 2;
+    d = __ldcg(r + 1);
+    rb = __ldcg(r + 2) - off;
+    L = __ldcg(r + 3);
+    U = __ldcg(r + 4);
+    T = __ldcg(r + 5);
+    best = __ldcg(r + 6);
+    bi = __ldcg(r + 7);
+    bj = __ldcg(r + 8);
+    barg = __ldcg(r + 9);
+    flags = uint32_t(__ldcg(r + 10));
+    cells = uint64_t(uint32_t(__ldcg(r + 11))) | (uint64_t(uint32_t(__ldcg(r + 12))) << 32);
+    // record rows: d-1 then d-2, slots 0 .. w0-1
+    for (int s = lane; s < w0; s += 32) {
+        R0[s + off] = __ldcg(r + 16 + s);
+        R1[s + off] = __ldcg(r + 16 + w0 + s);
+    }
+    return w0;
+}
+
+// Returns false when the band outgrew the ring (the side then goes to the generic tier).
+__device__ bool extend_band(const Problem& P, const Unit& u, uint32_t uidx, int32_t* R0, int32_t* R1,
+                            const int32_t* sim, int lane) {
+    constexpr int W = kBandW;
+    const int64_t m = u.m, n = u.n;
+    const int64_t dir = u.side ? -1 : 1;
+    for (int s = lane; s < W; s += 32) {
+        R0[s] = kNeg;
+        R1[s] = kNeg;
+    }
+    __syncwarp();
+    int32_t* P1 = R0;       // anti-diagonal d-1
+    int32_t* P2 = R1;       // anti-diagonal d-2, overwritten by d
+    int32_t rb = -W / 2, T = 0, best = 0, L = 0, U = 0;
+    int64_t d = 1, bi = 0, bj = 0, barg = 0;
+    uint32_t flags = 0, base = 0;
+    uint64_t cells = 1;
+    const uint32_t ri = P.rec_of ? __ldcg(P.rec_of + uidx) : 0xffffffffu;
+    if (ri != 0xffffffffu && __ldcg(P.rec + ri) <= W) {
+        band_load_rec(P, ri, R0, R1, rb, d, L, U, T, best, bi, bj, barg, flags, cells, lane);
+    } else if (lane == 0) {
+        P1[W / 2] = 0;      // S(0,0) = 0 at d = 0 (slot W/2)
+    }
+    __syncwarp();
+    const int32_t g = P.gap;
+    for (; d <= m + n; d++) {
+        int64_t lo = L, hi = int64_t(U) + 1;
+        if (d - n > lo) lo = d - n;
+        if (lo < 0) lo = 0;
+        if (hi > m) hi = m;
+        if (hi > d) hi = d;
+        if (P.delta && hi - lo + 1 > int64_t(P.delta)) {
+            flags |= 1u;
+            int64_t start = barg - int64_t(P.delta / 2);
+            const int64_t latest = hi - int64_t(P.delta) + 1;
+            if (latest < start) start = latest;
+            if (start > lo) lo = start;
+            hi = lo + int64_t(P.delta) - 1;
+        }
+        int64_t ib = (d >> 1) + rb;
+        int64_t slo = lo - ib, shi = hi - ib;
+        if (slo < 1 || shi > W - 2) {
+            const int64_t w = hi - lo + 1;
+            if (w > W - 2) return false;
+            const int64_t k = slo - (1 + (W - 2 - w) / 2);
+            // new slot s = old slot s + k: move the ring base, clear the exposed slots
+            base = uint32_t((int64_t(base) + k) & (W - 1));
+            rb += int32_t(k);
+            ib += k;
+            slo -= k;
+            shi -= k;
+            const int64_t ak = k > 0 ? k : -k;
+            const int64_t from = ak >= W ? 0 : (k > 0 ? W - k : 0);
+            const int64_t cnt = ak >= W ? W : ak;
+            for (int64_t t = lane; t < cnt; t += 32) {
+                const uint32_t pos = uint32_t((from + t + base) & (W - 1));
+                P1[pos] = kNeg;
+                P2[pos] = kNeg;
+            }
+            __syncwarp();
+        }
+        const int32_t thr = max(T - P.X, kDeadLine);
+        const bool odd = d & 1;
+        int32_t first = INT32_MAX, last = -1, bmax = kNeg, bslot = INT32_MAX;
+        for (int64_t s0 = slo; s0 <= shi; s0 += 32) {
+            const int64_t s = s0 + lane;
+            if (s <= shi) {
+                const int64_t i = ib + s, j = d - i;
+                const uint32_t ps = uint32_t((s + base) & (W - 1));
+                const uint32_t pa = uint32_t((s - 1 + base) & (W - 1)), pb = uint32_t((s + 1 + base) & (W - 1));
+                const int32_t up = odd ? P1[pa] : P1[ps];
+                const int32_t lf = odd ? P1[ps] : P1[pb];
+                int32_t c = max(up, lf) + g;
+                if (i >= 1 && j >= 1) {
+                    const uint32_t a = residue(P.store, P.alpha, uint64_t(int64_t(u.h0) + dir * (i - 1)));
+                    const uint32_t b = residue(P.store, P.alpha, uint64_t(int64_t(u.v0) + dir * (j - 1)));
+                    c = max(c, P2[ps] + sim[a * P.alpha + b]);
+                }
+                if (c < thr) c = kNeg;
+                P2[ps] = c;
+                if (c != kNeg) {
+                    if (first == INT32_MAX) first = int32_t(s);
+                    last = int32_t(s);
+                    if (c > bmax) {
+                        bmax = c;
+                        bslot = int32_t(s);
+                    }
+                }
+            }
+        }
+        if (lane == 0) {
+            P2[uint32_t((slo - 1 + base) & (W - 1))] = kNeg;
+            P2[uint32_t((shi + 1 + base) & (W - 1))] = kNeg;
+        }
+        cells += uint64_t(hi - lo + 1);
+        first = __reduce_min_sync(0xffffffffu, first);
+        last = __reduce_max_sync(0xffffffffu, last);
+        const int32_t wmax = __reduce_max_sync(0xffffffffu, bmax);
+        bslot = __reduce_min_sync(0xffffffffu, bmax == wmax ? bslot : INT32_MAX);
+        __syncwarp();
+        if (first == INT32_MAX) break;
+        const int64_t arg = ib + bslot;
+        if (wmax > T) {
+            T = wmax;
+            best = wmax;
+            bi = arg;
+            bj = d - arg;
+        }
+        barg = arg;
+        L = int32_t(ib + first);
+        U = int32_t(ib + last);
+        int32_t* tmp = P2;
+        P2 = P1;
+        P1 = tmp;
+    }
+    if (lane == 0) {
+        write_side(P.results, u.pair, u.side, best, uint32_t(bi), uint32_t(bj), flags, cells);
+        atomicAdd(&P.stats[2], 1ull);
+        atomicAdd(&P.stats[6], (unsigned long long)cells);
+    }
+    __syncwarp();
+    return true;
+}
+
+__global__ void __launch_bounds__(32) k_band(Problem P, Queues Q) {
+    extern __shared__ int32_t band_smem[];
+    int32_t* sim = band_smem;
+    int32_t* R0 = band_smem + 416;
+    int32_t* R1 = R0 + kBandW;
+    for (int t = threadIdx.x; t < P.alpha * P.alpha; t += blockDim.x) sim[t] = P.sim[t];
+    __syncwarp();
+    const int lane = threadIdx.x & 31;
+    const uint32_t n_q = *reinterpret_cast<volatile uint32_t*>(&Q.ctr[1 + 2 * kBandQ]);
+    for (;;) {
+        uint32_t k = 0;
+        if (lane == 0) k = atomicAdd(&Q.ctr[2 + 2 * kBandQ], 1u);
+        k = __shfl_sync(0xffffffffu, k, 0);
+        if (k >= n_q) break;
+        const uint32_t uidx = Q.q[kBandQ][k];
+        const Unit u = P.units[uidx];
+        if (!extend_band(P, u, uidx, R0, R1, sim, lane)) {
+            if (lane == 0) {
+                push_unit(Q, kGenericQ, uidx);
+                atomicAdd(&P.stats[3], 1ull);
+            }
+            __syncwarp();
+        }
+    }
+}
+
 // Queue every unit to the generic tier (used when the register tiers are disabled).
 __global__ void k_route_all_generic(Queues Q) {
     uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < Q.n_units) Q.q[kLevels - 1][t] = Q.order[t];
-    if (t == 0) Q.ctr[1 + 2 * (kLevels - 1)] = Q.n_units;
+    if (t < Q.n_units) Q.q[kGenericQ][t] = Q.order[t];
+    if (t == 0) Q.ctr[1 + 2 * kGenericQ] = Q.n_units;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -326,6 +516,18 @@ cudaError_t launch_route_all_generic(const Queues& Q, cudaStream_t st) {
 cudaError_t launch_generic(const Problem& P, const Queues& Q, int32_t* scratch,
                            uint64_t stride, int n_blocks, cudaStream_t st) {
     k_generic<<<n_blocks, 128, 0, st>>>(P, Q, scratch, stride);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_band(const Problem& P, const Queues& Q, int n_sm, cudaStream_t st) {
+    const size_t smem = (416 + 2 * size_t(kBandW)) * sizeof(int32_t);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_band, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_band<<<n_sm * 3, 32, smem, st>>>(P, Q);
     return cudaGetLastError();
 }
 

@@ -5,7 +5,7 @@
 
 namespace xd {
 
-constexpr int kNumCtr = 4 + 2 * kLevels;   // last two: producer warps finished (fused levels)
+constexpr int kNumCtr = 4 + 2 * kLevels;   // then: producer warps finished (two), record counter
 
 cudaError_t launch_pack(int alpha, const uint8_t* codes, uint64_t n_codes, uint32_t* store,
                         uint32_t* err, int n_sm, cudaStream_t st);
@@ -18,6 +18,7 @@ cudaError_t launch_order(uint32_t* hist, uint32_t* ctr, int n_ctr, const uint32_
 cudaError_t launch_route_all_generic(const Queues& Q, cudaStream_t st);
 cudaError_t launch_generic(const Problem& P, const Queues& Q, int32_t* scratch,
                            uint64_t stride, int n_blocks, cudaStream_t st);
+cudaError_t launch_band(const Problem& P, const Queues& Q, int n_sm, cudaStream_t st);
 cudaError_t launch_totals(const xd_pair* pairs, uint32_t n_pairs, const uint64_t* offsets,
                           const uint32_t* lengths, uint32_t n_seqs, const Problem& P,
                           cudaStream_t st);
@@ -25,21 +26,23 @@ cudaError_t launch_totals(const xd_pair* pairs, uint32_t n_pairs, const uint64_t
 cudaError_t launch_accumulate(const unsigned long long* batch, unsigned long long* total, int n,
                               cudaStream_t st);
 
-// Register tiers (xd_tiers.cu): a chain of up to kLevels - 1 register levels, each a
+// Register tiers (xd_tiers.cu): a chain of up to kLevels - 2 register levels, each a
 // group kernel with G lanes per side extension and CG slots per lane (window G * CG),
 // followed by the generic tier.  Variant ids name the compiled (G, CG) pairs.
 enum GroupVariant {
     kG1C16 = 0, kG1C32 = 1, kG4C16 = 2, kG8C16 = 3, kG16C16 = 4, kG32C16 = 5, kG32C32 = 6,
-    kNumGroupVariants = 7
+    kG4C32 = 7, kG8C32 = 8, kG16C32 = 9,
+    kNumGroupVariants = 10
 };
 
 struct TierConfig {
     int n_levels;                       // register levels before the generic tier
-    int variant[kLevels - 1];           // GroupVariant of each level
+    int variant[kLevels - 2];           // GroupVariant of each level
     int blocks_per_sm[kNumGroupVariants];
     int chunk;                          // units pulled per queue access (single-lane groups)
     bool fused;                         // fuse levels 0-2 into one persistent grid
     int every1, every2;                 // fused grid: warps starting in role 1 / role 2
+    int fused_minb;                     // fused grid register budget: resident blocks per SM
 };
 
 // Runs register level `level` of the chain: pulls the cost-ordered list (level 0) or

@@ -150,28 +150,53 @@ __device__ __forceinline__ void band_of(SideState& s, const Problem& P, int32_t 
 }
 
 // The lane's CG cells.  P1 holds d-1, P2 holds d-2 and receives d.  upb / lfb are the
-// neighbours beyond the lane's first / last slot.  Returns the lane's live mask and the
-// maximum key v * 64 + (63 - t) over its cells (dead cells hold kNegR).
+// neighbours beyond the lane's first / last slot.  Similarities come four at a time from a
+// 256-entry shared table indexed by one byte of the xor of the residue slices (four 2-bit
+// fields: zero = match).  Returns the lane's live mask and the maximum key
+// v * 64 + (63 - t) over its cells (dead cells hold kNegR).
 template <int CG, bool ODD>
 __device__ __forceinline__ void cells_of(int32_t (&P1)[CG], int32_t (&P2)[CG], int32_t upb,
                                          int32_t lfb, uint64_t x, uint32_t bm, int32_t thr,
-                                         int32_t gap, int32_t mat, int32_t mis, int32_t& kmax,
+                                         int32_t gap, const int4* lut4, int32_t& kmax,
                                          uint32_t& lm) {
+    static_assert(CG % 4 == 0, "cells come in groups of four");
     kmax = INT32_MIN;
     lm = 0;
 #pragma unroll
-    for (int t = 0; t < CG; t++) {
-        const int32_t up = ODD ? (t > 0 ? P1[t - 1] : upb) : P1[t];
-        const int32_t lf = ODD ? P1[t] : (t < CG - 1 ? P1[t + 1] : lfb);
-        const int32_t sig = ((x >> (2 * t)) & 3ull) ? mis : mat;
-        const int32_t raw = __viaddmax_s32(max(up, lf), gap, P2[t] + sig);
-        const bool live = raw >= thr && ((bm >> t) & 1u);
-        const int32_t v = live ? raw : kNegR;
-        P2[t] = v;
-        lm |= live ? (1u << t) : 0u;
-        kmax = max(kmax, v * 64 + (63 - t));
+    for (int q = 0; q < CG / 4; q++) {
+        const int4 s4 = lut4[uint32_t(x >> (8 * q)) & 0xffu];
+        const int32_t sg[4] = {s4.x, s4.y, s4.z, s4.w};
+        int32_t key[4];
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            const int t = 4 * q + r;
+            const int32_t up = ODD ? (t > 0 ? P1[t - 1] : upb) : P1[t];
+            const int32_t lf = ODD ? P1[t] : (t < CG - 1 ? P1[t + 1] : lfb);
+            const int32_t raw = __viaddmax_s32(max(up, lf), gap, P2[t] + sg[r]);
+            const bool live = raw >= thr && ((bm >> t) & 1u);
+            const int32_t v = live ? raw : kNegR;
+            P2[t] = v;
+            lm |= live ? (1u << t) : 0u;
+            key[r] = v * 64 + (63 - t);
+        }
+        kmax = __vimax3_s32(kmax, key[0], key[1]);
+        kmax = __vimax3_s32(kmax, key[2], key[3]);
     }
 }
+
+// Similarity table for four DNA cells: entry e holds Sim of fields (e >> 2f) & 3, f = 0..3.
+__device__ __forceinline__ void build_lut4(int4* lut4, int32_t mat, int32_t mis) {
+    for (int e = threadIdx.x; e < 256; e += blockDim.x) {
+        int4 v;
+        v.x = (e & 3) ? mis : mat;
+        v.y = ((e >> 2) & 3) ? mis : mat;
+        v.z = ((e >> 4) & 3) ? mis : mat;
+        v.w = ((e >> 6) & 3) ? mis : mat;
+        lut4[e] = v;
+    }
+    __syncthreads();
+}
+constexpr int kLutInts = 1024;
 
 template <int G>
 __device__ __forceinline__ int32_t gmax(int32_t v, uint32_t gm) {
@@ -198,7 +223,7 @@ __device__ __forceinline__ uint32_t slot_mask(int32_t from, int32_t to, int cw) 
 // One anti-diagonal of the group's side extension.
 template <int G, int CG, bool ODD>
 __device__ __forceinline__ int group_step(SideState& s, int32_t (&P1)[CG], int32_t (&P2)[CG],
-                                          const Problem& P, int32_t mat, int32_t mis, int gl,
+                                          const Problem& P, const int4* lut4, int gl,
                                           uint32_t gm, int32_t* gsm) {
     constexpr int W = G * CG;
     const int32_t d = s.d;
@@ -231,6 +256,7 @@ __device__ __forceinline__ int group_step(SideState& s, int32_t (&P1)[CG], int32
         slo -= k;
         shi -= k;
         s.refresh = true;
+        if (gl == 0) atomicAdd(&P.stats[8], 1ull);
     }
     const int32_t sb = gl * CG;
     update_slices<CG, ODD>(s, P, int64_t(ib) - 1 + sb, int64_t(d) - ib - 1 - sb);
@@ -248,7 +274,7 @@ __device__ __forceinline__ int group_step(SideState& s, int32_t (&P1)[CG], int32
     }
     int32_t kmax;
     uint32_t lm;
-    cells_of<CG, ODD>(P1, P2, upb, lfb, s.hs ^ s.vs, bm, thr, P.gap, mat, mis, kmax, lm);
+    cells_of<CG, ODD>(P1, P2, upb, lfb, s.hs ^ s.vs, bm, thr, P.gap, lut4, kmax, lm);
     s.cells += uint64_t(hi - lo + 1);
     const bool any = lm != 0;
     int32_t first = any ? sb + __ffs(lm) - 1 : INT32_MAX;
@@ -343,28 +369,95 @@ __device__ __forceinline__ bool next_unit(const Source& S, int gl, int lane, uin
     return got != 0;
 }
 
+// Record layout: 16 header ints (window, d, rb, L, U, T, best, bi, bj, barg, flags,
+// cells lo/hi), then the window's anti-diagonal d-1 and d-2 in slot order.  Records are
+// bump-allocated from one int pool; rec_of holds a record's offset in the pool.
+constexpr int kRecHeader = 16;
+
+template <int G, int CG>
+__device__ __forceinline__ void save_record(const Problem& P, uint32_t ri, const SideState& s,
+                                            const int32_t (&P1)[CG], const int32_t (&P2)[CG], int gl) {
+    constexpr int W = G * CG;
+    int32_t* r = P.rec + ri;
+#pragma unroll
+    for (int t = 0; t < CG; t++) {
+        __stcg(r + kRecHeader + gl * CG + t, P1[t]);
+        __stcg(r + kRecHeader + W + gl * CG + t, P2[t]);
+    }
+    if (gl == 0) {
+        __stcg(r + 0, W);
+        __stcg(r + 1, s.d);
+        __stcg(r + 2, s.rb);
+        __stcg(r + 3, s.L);
+        __stcg(r + 4, s.U);
+        __stcg(r + 5, s.T);
+        __stcg(r + 6, s.best);
+        __stcg(r + 7, s.bi);
+        __stcg(r + 8, s.bj);
+        __stcg(r + 9, s.barg);
+        __stcg(r + 10, int32_t(s.flags));
+        __stcg(r + 11, int32_t(uint32_t(s.cells)));
+        __stcg(r + 12, int32_t(uint32_t(s.cells >> 32)));
+    }
+}
+
+// Continues a side from its record in a window of W >= the record's window (placed in the
+// middle).  Returns false if the record does not fit (the side then starts from scratch).
+template <int G, int CG>
+__device__ __forceinline__ bool load_record(const Problem& P, uint32_t ri, SideState& s, int32_t (&A)[CG],
+                                            int32_t (&B)[CG], int gl) {
+    constexpr int W = G * CG;
+    const int32_t* r = P.rec + ri;
+    const int32_t w0 = __ldcg(r + 0);
+    if (w0 > W) return false;
+    const int32_t off = (W - w0) / 2;
+    s.d = __ldcg(r + 1);
+    s.rb = __ldcg(r + 2) - off;
+    s.L = __ldcg(r + 3);
+    s.U = __ldcg(r + 4);
+    s.T = __ldcg(r + 5);
+    s.best = __ldcg(r + 6);
+    s.bi = __ldcg(r + 7);
+    s.bj = __ldcg(r + 8);
+    s.barg = __ldcg(r + 9);
+    s.flags = uint32_t(__ldcg(r + 10));
+    s.cells = uint64_t(uint32_t(__ldcg(r + 11))) | (uint64_t(uint32_t(__ldcg(r + 12))) << 32);
+    const bool odd = s.d & 1;   // odd d: A holds d-1; even d: B holds d-1
+#pragma unroll
+    for (int t = 0; t < CG; t++) {
+        const int src = gl * CG + t - off;
+        const bool in = src >= 0 && src < w0;
+        const int32_t v1 = in ? __ldcg(r + kRecHeader + src) : kNegR;
+        const int32_t v2 = in ? __ldcg(r + kRecHeader + w0 + src) : kNegR;
+        A[t] = odd ? v1 : v2;
+        B[t] = odd ? v2 : v1;
+    }
+    return true;
+}
+
 // Runs side extensions from S with groups of G lanes until S is exhausted; overflows go to
-// q[out_q].  gsm_block: the block's shared rows (2W ints per group).
+// q[out_q], carrying an escalation record when the next level is a register level.
+// gsm_block: the block's shared rows (2W ints per group).
 template <int G, int CG>
 __device__ __forceinline__ void group_loop(const Problem& P, const Queues& Q, const Source& S, int out_q,
-                                           int chunk, int32_t* gsm_block) {
+                                           int chunk, int32_t* smem) {
     constexpr int W = G * CG;
     const int lane = threadIdx.x & 31;
     const int gl = lane % G;
     const uint32_t gm = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane - gl));
-    int32_t* gsm = gsm_block + (threadIdx.x / G) * 2 * W;
-    const int32_t mat = P.sim[0], mis = P.sim[1];
+    const int4* lut4 = reinterpret_cast<const int4*>(smem);
+    int32_t* gsm = smem + kLutInts + (threadIdx.x / G) * 2 * W;
     int32_t A[CG], B[CG];
     SideState s{};
     uint32_t uidx = 0, pair = 0, next = 0, end = 0;
-    bool active = false;
+    bool active = false, skip_odd = false;
     for (;;) {
         if (!active) {
             bool got = false;
             while (next_unit<G>(S, gl, lane, gm, chunk, next, end, uidx, P.err)) {
                 const Unit u = P.units[uidx];
                 if ((int64_t(u.m) + u.n) * P.max_abs >= kRegLimit || P.alpha != 4) {
-                    if (gl == 0) push_unit(Q, kLevels - 1, uidx);
+                    if (gl == 0) push_unit(Q, kBandQ, uidx);
                     continue;
                 }
                 init_side(s, u, -W / 2);
@@ -381,30 +474,59 @@ __device__ __forceinline__ void group_loop(const Problem& P, const Queues& Q, co
                 }
                 continue;
             }
-            // S(0,0) = 0 in the middle of the window, every other cell -inf (Sec. 2.2)
+            const uint32_t ri = P.rec_of ? __ldcg(P.rec_of + uidx) : kNoUnit;
+            if (ri == kNoUnit || !load_record<G, CG>(P, ri, s, A, B, gl)) {
+                // S(0,0) = 0 in the middle of the window, every other cell -inf (Sec. 2.2)
 #pragma unroll
-            for (int t = 0; t < CG; t++) {
-                A[t] = kNegR;
-                B[t] = kNegR;
+                for (int t = 0; t < CG; t++) {
+                    A[t] = kNegR;
+                    B[t] = kNegR;
+                }
+                if (gl == (W / 2) / CG) A[(W / 2) % CG] = 0;
             }
-            if (gl == (W / 2) / CG) A[(W / 2) % CG] = 0;
+            skip_odd = (s.d & 1) == 0;   // a side continued on an even anti-diagonal
             active = true;
         }
-        int r = group_step<G, CG, true>(s, A, B, P, mat, mis, gl, gm, gsm);
-        if (r == kCont) r = group_step<G, CG, false>(s, B, A, P, mat, mis, gl, gm, gsm);
+        int r = kCont;
+        if (!skip_odd) r = group_step<G, CG, true>(s, A, B, P, lut4, gl, gm, gsm);
+        skip_odd = false;
+        if (r == kCont) r = group_step<G, CG, false>(s, B, A, P, lut4, gl, gm, gsm);
         if (r == kCont) continue;
         active = false;
-        if (gl == 0) {
-            if (r == kDone) {
+        if (r == kDone) {
+            if (gl == 0) {
                 write_side(P.results, pair, s.side, s.best, uint32_t(s.bi), uint32_t(s.bj), s.flags, s.cells);
                 const int tier = W <= 32 ? 0 : 1;
                 atomicAdd(&P.stats[tier], 1ull);
                 atomicAdd(&P.stats[4 + tier], (unsigned long long)s.cells);
+            }
+            continue;
+        }
+        // overflow: hand the side to the next level, with its state when that level can take it
+        uint32_t ri = kNoUnit;
+        if (out_q <= kBandQ && P.rec) {
+            // bump-allocate kRecHeader + 2W ints of the record pool
+            const uint32_t need = uint32_t(kRecHeader + 2 * W);
+            if (gl == 0) ri = atomicAdd(P.rec_ctr, need);
+            if (G > 1) ri = __shfl_sync(gm, ri, lane - gl);
+            if (ri <= P.rec_cap && P.rec_cap - ri >= need) {
+                if (s.d & 1) save_record<G, CG>(P, ri, s, A, B, gl);
+                else save_record<G, CG>(P, ri, s, B, A, gl);
+                if (G > 1) __syncwarp(gm);
             } else {
-                push_unit(Q, out_q, uidx);
-                atomicAdd(&P.stats[3], 1ull);
+                ri = kNoUnit;
+            }
+        }
+        if (gl == 0) {
+            if (ri != kNoUnit) {
+                __threadfence();
+                __stcg(P.rec_of + uidx, ri);
+                __threadfence();
+            } else {
                 atomicAdd(&P.stats[7], (unsigned long long)s.cells);
             }
+            push_unit(Q, out_q, uidx);
+            atomicAdd(&P.stats[3], 1ull);
         }
     }
 }
@@ -421,7 +543,8 @@ __device__ __forceinline__ Source static_source(const Queues& Q, int in_q) {
 // One register level over a finished list.  in_q < 0: the cost-ordered units, else q[in_q].
 template <int G, int CG, int MINB>
 __global__ void __launch_bounds__(128, MINB) k_group(Problem P, Queues Q, int in_q, int out_q, int chunk) {
-    extern __shared__ int32_t group_smem[];
+    extern __shared__ __align__(16) int32_t group_smem[];
+    build_lut4(reinterpret_cast<int4*>(group_smem), P.sim[0], P.sim[1]);
     group_loop<G, CG>(P, Q, static_source(Q, in_q), out_q, chunk, group_smem);
 }
 
@@ -468,7 +591,8 @@ __device__ __forceinline__ void signal_done(uint32_t* done) {
 
 template <int G0, int C0, int G1, int C1, int G2, int C2, int MINB>
 __global__ void __launch_bounds__(128, MINB) k_fused(Problem P, Queues Q, RolePlan R, int chunk) {
-    extern __shared__ int32_t group_smem[];
+    extern __shared__ __align__(16) int32_t group_smem[];
+    build_lut4(reinterpret_cast<int4*>(group_smem), P.sim[0], P.sim[1]);
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     uint32_t* done0 = &Q.ctr[1 + 2 * kLevels];
     uint32_t* done1 = &Q.ctr[2 + 2 * kLevels];
@@ -487,7 +611,7 @@ __global__ void __launch_bounds__(128, MINB) k_fused(Problem P, Queues Q, RolePl
 template <int G, int CG, int MINB>
 static cudaError_t launch_group(const Problem& P, const Queues& Q, int in_q, int out_q, int blocks,
                                 int chunk, cudaStream_t st) {
-    const size_t smem = size_t(128 / G) * 2 * G * CG * sizeof(int32_t);
+    const size_t smem = (size_t(kLutInts) + size_t(128 / G) * 2 * G * CG) * sizeof(int32_t);
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_group<G, CG, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
@@ -500,7 +624,7 @@ static cudaError_t launch_group(const Problem& P, const Queues& Q, int in_q, int
 
 template <int G, int CG>
 constexpr size_t group_smem_bytes() {
-    return size_t(128 / G) * 2 * G * CG * sizeof(int32_t);
+    return (size_t(kLutInts) + size_t(128 / G) * 2 * G * CG) * sizeof(int32_t);
 }
 
 template <int G0, int C0, int G1, int C1, int G2, int C2, int MINB>
@@ -543,6 +667,9 @@ int variant_window(int v) {
         case kG16C16: return 256;
         case kG32C16: return 512;
         case kG32C32: return 1024;
+        case kG4C32: return 128;
+        case kG8C32: return 256;
+        case kG16C32: return 512;
         default: return 0;
     }
 }
@@ -551,7 +678,7 @@ cudaError_t launch_level(const Problem& P, const Queues& Q, const TierConfig& cf
                          int n_sm, cudaStream_t st) {
     const int v = cfg.variant[level];
     const int in_q = level == 0 ? -1 : level - 1;
-    const int out_q = level == cfg.n_levels - 1 ? kLevels - 1 : level;
+    const int out_q = level == cfg.n_levels - 1 ? kBandQ : level;
     const int blocks = n_sm * cfg.blocks_per_sm[v];
     switch (v) {
         case kG1C16: return launch_group<1, 16, 3>(P, Q, in_q, out_q, blocks, cfg.chunk, st);
@@ -561,6 +688,9 @@ cudaError_t launch_level(const Problem& P, const Queues& Q, const TierConfig& cf
         case kG16C16: return launch_group<16, 16, 3>(P, Q, in_q, out_q, blocks, cfg.chunk, st);
         case kG32C16: return launch_group<32, 16, 3>(P, Q, in_q, out_q, blocks, cfg.chunk, st);
         case kG32C32: return launch_group<32, 32, 2>(P, Q, in_q, out_q, blocks, cfg.chunk, st);
+        case kG4C32: return launch_group<4, 32, 2>(P, Q, in_q, out_q, blocks, cfg.chunk, st);
+        case kG8C32: return launch_group<8, 32, 2>(P, Q, in_q, out_q, blocks, cfg.chunk, st);
+        case kG16C32: return launch_group<16, 32, 2>(P, Q, in_q, out_q, blocks, cfg.chunk, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -568,14 +698,19 @@ cudaError_t launch_level(const Problem& P, const Queues& Q, const TierConfig& cf
 bool fused_supported(const TierConfig& c) {
     if (c.n_levels < 3) return false;
     const int a = c.variant[0], b = c.variant[1], d = c.variant[2];
-    return (a == kG1C32 && b == kG16C16 && d == kG32C16) || (a == kG1C32 && b == kG8C16 && d == kG32C16) ||
+    return (a == kG1C32 && b == kG4C32 && d == kG8C32) || (a == kG1C32 && b == kG8C16 && d == kG16C16) ||
+           (a == kG1C32 && b == kG16C16 && d == kG32C16) || (a == kG1C32 && b == kG8C16 && d == kG32C16) ||
            (a == kG1C16 && b == kG4C16 && d == kG16C16) || (a == kG1C16 && b == kG8C16 && d == kG32C16);
 }
 
 cudaError_t launch_fused_levels(const Problem& P, const Queues& Q, const TierConfig& cfg, int n_sm,
                                 cudaStream_t st) {
     const int a = cfg.variant[0], b = cfg.variant[1], d = cfg.variant[2];
-    if (a == kG1C32 && b == kG16C16 && d == kG32C16) return launch_fused<1, 32, 16, 16, 32, 16, 2>(P, Q, cfg, n_sm, st);
+    if (a == kG1C32 && b == kG4C32 && d == kG8C32) return launch_fused<1, 32, 4, 32, 8, 32, 2>(P, Q, cfg, n_sm, st);
+    if (a == kG1C32 && b == kG8C16 && d == kG16C16) return launch_fused<1, 32, 8, 16, 16, 16, 2>(P, Q, cfg, n_sm, st);
+    if (a == kG1C32 && b == kG16C16 && d == kG32C16)
+        return cfg.fused_minb == 3 ? launch_fused<1, 32, 16, 16, 32, 16, 3>(P, Q, cfg, n_sm, st)
+                                   : launch_fused<1, 32, 16, 16, 32, 16, 2>(P, Q, cfg, n_sm, st);
     if (a == kG1C32 && b == kG8C16 && d == kG32C16) return launch_fused<1, 32, 8, 16, 32, 16, 2>(P, Q, cfg, n_sm, st);
     if (a == kG1C16 && b == kG4C16 && d == kG16C16) return launch_fused<1, 16, 4, 16, 16, 16, 3>(P, Q, cfg, n_sm, st);
     if (a == kG1C16 && b == kG8C16 && d == kG32C16) return launch_fused<1, 16, 8, 16, 32, 16, 3>(P, Q, cfg, n_sm, st);
