@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-pairs", type=int, default=8000, help="oracle sample size")
+    ap.add_argument("--serve", type=float, default=5.0,
+                    help="seconds per offered load of the serving run (0 = skip)")
+    ap.add_argument("--serve-loads", default="0.25,0.5,0.9")
+    ap.add_argument("--serve-inflight", type=int, default=3)
     return ap.parse_args()
 
 
@@ -138,6 +142,161 @@ class Clocks:
                 "sm_max_mhz": max(mx) if mx else None,
                 "power_w_max": max(power) if power else None,
                 "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------- serving
+
+SERVE_MAX_PAIRS = 10_000
+
+
+class RequestMix:
+    """Requests of log-uniform size in [1, 10,000] pairs, half DNA long-read pairs (X drawn
+    from {10, 20, 50}) and half protein pairs (BLOSUM62, X = 49), each a contiguous pair
+    range of a resident pool (zero-copy views; the library copies at submit)."""
+
+    def __init__(self, dna, prot, seed):
+        self.dna, self.prot = dna, prot
+        self.rng = np.random.default_rng(seed)
+
+    def next(self):
+        rng = self.rng
+        pool = self.dna if rng.random() < 0.5 else self.prot
+        size = min(pool.n_pairs, int(np.exp(rng.uniform(0.0, np.log(SERVE_MAX_PAIRS + 1)))))
+        size = max(1, size)
+        a = int(rng.integers(0, pool.n_pairs - size + 1))
+        b = pool.pair_range(a, a + size)
+        if pool is self.dna:
+            b = b.with_params(X=int(rng.choice([10, 20, 50])))
+        return b
+
+
+def serve_run(xdrop, ctx, mix, rate_rps, duration, max_requests=None):
+    """Open-loop Poisson arrivals at rate_rps for `duration` seconds (rate_rps = inf: all
+    at once).  Latency = completion time - scheduled arrival time.  Returns a summary."""
+    import threading
+    rng = np.random.default_rng(99)
+    arrivals, t = [], 0.0
+    while True:
+        if np.isinf(rate_rps):
+            if len(arrivals) >= (max_requests or 200):
+                break
+        else:
+            t += rng.exponential(1.0 / rate_rps)
+            if t > duration or (max_requests and len(arrivals) >= max_requests):
+                break
+        arrivals.append(t if not np.isinf(rate_rps) else 0.0)
+    reqs = [mix.next() for _ in arrivals]
+    outstanding = []          # (ticket, k, out)
+    lock = threading.Lock()
+    done_at = [None] * len(reqs)
+    cells = [0.0] * len(reqs)
+    submitted = threading.Event()
+    errors = []
+
+    def poller():
+        while True:
+            with lock:
+                cur = list(outstanding)
+            if not cur and submitted.is_set():
+                return
+            finished = []
+            for item in cur:
+                tk, k, out = item
+                try:
+                    rc = xdrop.xd_poll(ctx, tk, out, 0)
+                except Exception as e:   # reported below
+                    errors.append(e)
+                    rc = xdrop.XD_OK
+                if rc == xdrop.XD_OK:
+                    done_at[k] = time.perf_counter()
+                    cells[k] = float(out["left"]["cells"].sum() + out["right"]["cells"].sum())
+                    finished.append(item)
+            if finished:
+                with lock:
+                    for item in finished:
+                        outstanding.remove(item)
+            else:
+                time.sleep(50e-6)
+
+    th = threading.Thread(target=poller)
+    th.start()
+    t0 = time.perf_counter()
+    start = [0.0] * len(reqs)
+    sub_begin = [0.0] * len(reqs)
+    sub_end = [0.0] * len(reqs)
+    for k, (at, b) in enumerate(zip(arrivals, reqs)):
+        now = time.perf_counter() - t0
+        if at > now:
+            time.sleep(at - now)
+        start[k] = t0 + at
+        sub_begin[k] = time.perf_counter()
+        args = xdrop.BatchArgs.from_host(b)
+        while True:
+            try:
+                tk = xdrop.xd_submit_batch(ctx, args)
+                break
+            except xdrop.XdError as e:
+                if e.status != xdrop.XD_ENOMEM:
+                    raise
+                time.sleep(200e-6)          # admission refused: retry when memory frees up
+        sub_end[k] = time.perf_counter()
+        out = np.zeros(b.n_pairs, dtype=xdrop.RESULT_DTYPE)
+        with lock:
+            outstanding.append((tk, k, out))
+    submitted.set()
+    th.join()
+    if errors:
+        raise errors[0]
+    t_end = max(done_at)
+    lat = np.array([(d - s) * 1e3 for d, s in zip(done_at, start)])
+    span = t_end - t0
+    pairs = sum(b.n_pairs for b in reqs)
+    wait = np.array([(b_ - s_) * 1e3 for b_, s_ in zip(sub_begin, start)])
+    sub = np.array([(e_ - b_) * 1e3 for e_, b_ in zip(sub_end, sub_begin)])
+    run = np.array([(d - e_) * 1e3 for d, e_ in zip(done_at, sub_end)])
+    pct = lambda a, q: float(np.percentile(a, q))  # noqa: E731
+    return {"requests": len(reqs), "pairs": pairs, "span_s": span,
+            "pairs_per_s": pairs / span, "gcups": sum(cells) / span / 1e9,
+            "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "mean_ms": float(lat.mean()),
+            "breakdown_ms": {"arrival_to_submit_p50": pct(wait, 50), "arrival_to_submit_p99": pct(wait, 99),
+                             "submit_call_p50": pct(sub, 50), "submit_call_p99": pct(sub, 99),
+                             "submitted_to_done_p50": pct(run, 50), "submitted_to_done_p99": pct(run, 99)}}
+
+
+def serving_bench(xdrop, device, dna_pool, seconds, loads, inflight):
+    """Continuous batching against one launch per request, at fractions of the peak."""
+    prot_pool = synth.protein(n_pairs=200_000)
+    mean_pairs = SERVE_MAX_PAIRS / np.log(SERVE_MAX_PAIRS + 1) - 0.5   # E[floor(exp(U(0, ln(N+1))))]
+    res = {"duration_s_per_load": seconds, "request_pairs": f"log-uniform [1, {SERVE_MAX_PAIRS}]",
+           "mix": "50% DNA long-read (X in {10, 20, 50}), 50% protein (BLOSUM62, X = 49)",
+           "arrivals": "Poisson, open loop; latency from scheduled arrival to completion"}
+    modes = {"continuous": dict(max_inflight=inflight, batching=1),
+             "per_batch": dict(max_inflight=1, batching=-1)}
+    for name, kw in modes.items():
+        ctx = xdrop.xd_create(device, **kw)
+        try:
+            # warm-up (pinned buffers, scratch), then the saturated peak
+            serve_run(xdrop, ctx, RequestMix(dna_pool, prot_pool, 1), float("inf"), 0, max_requests=60)
+            peak = serve_run(xdrop, ctx, RequestMix(dna_pool, prot_pool, 2), float("inf"), 0,
+                             max_requests=240)
+            if name == "continuous":
+                res["peak_pairs_per_s"] = peak["pairs_per_s"]
+                res["peak_gcups"] = peak["gcups"]
+            out = {"saturated": peak, "loads": []}
+            for ld in loads:
+                rate_pairs = ld * res["peak_pairs_per_s"]
+                rate_rps = rate_pairs / mean_pairs
+                r = serve_run(xdrop, ctx, RequestMix(dna_pool, prot_pool, 3), rate_rps, seconds)
+                r["load"] = ld
+                r["offered_pairs_per_s"] = rate_pairs
+                out["loads"].append(r)
+            st = xdrop.xd_get_stats(ctx)
+            out["launches"] = st["host_launches"]
+            out["requests_launched"] = st["host_requests"]
+            res[name] = out
+        finally:
+            xdrop.xd_destroy(ctx)
+    return res
 
 
 def run_reference(a, rank, world):
@@ -280,6 +439,11 @@ def main():
             e2e = {"value": cells * world / e2e_s / 1e9, "unit": "GCUPS", "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": int(hout.nbytes), "ms_per_step": e2e_s * 1e3}
 
+        serving = None
+        if rank == 0 and a.serve > 0 and a.workload == "dna_longread":
+            loads = [float(x) for x in a.serve_loads.split(",") if x]
+            serving = serving_bench(xdrop, local, b, a.serve, loads, a.serve_inflight)
+
         cpu = None
         if rank == 0 and not a.no_cpu:
             threads = os.cpu_count() or 1
@@ -305,6 +469,7 @@ def main():
                     "discarded_cells_per_step": tim["discarded_cells"] / nb,
                     "escalations_per_step": tim["escalations"] / nb,
                     "window_shifts_per_step": tim["window_shifts"] / nb,
+                    "serving": serving,
                     "clocks": clk}
             print(json.dumps(line), flush=True)
     finally:

@@ -52,14 +52,21 @@ typedef enum {
 typedef enum { XD_DNA2 = 0, XD_PROT5 = 1 } xd_alphabet;
 
 /* Context configuration.  device: CUDA ordinal.  store_bytes_cap: device bytes the
- * library may hold for in-flight batches (0 = 64 GiB).  max_inflight: concurrently
- * admitted host batches (0 = 8).  tune_table: path of an autotune table written by
- * xd_autotune, or NULL for built-in defaults. */
+ * library may hold for admitted host batches (0 = 64 GiB): their sequences (unpacked and
+ * packed), seed tuples, results and per-side state; each launch slot also keeps band rows
+ * of 3 x (longest side + 1) scores per resident warp of the generic tier.  max_inflight: launches of host
+ * batches in flight at once, each on its own stream (0 = 3).  tune_table: path of a tuning
+ * table written by xd_autotune, or NULL for built-in defaults.  batching: 0 or 1 = continuous
+ * batching (host batches that wait for a free launch slot and share scoring, X and delta_b
+ * are merged into one launch); -1 = one launch per host batch.  max_batch_pairs: cap on the
+ * pairs of one merged launch (0 = 2^20; a single larger batch still runs alone). */
 typedef struct {
     int32_t device;
     uint64_t store_bytes_cap;
     int32_t max_inflight;
     const char* tune_table;
+    int32_t batching;
+    uint32_t max_batch_pairs;
 } xd_config;
 
 /* Scoring (Sec. 2.2): DNA uses match (> 0), mismatch and gap scores; protein uses a
@@ -120,6 +127,8 @@ typedef struct {
     uint64_t units_tier[3];      /* side extensions finished by the narrow, wide, generic tier */
     uint64_t escalations;        /* side extensions restarted in a wider tier */
     uint64_t kernel_launches;    /* kernels launched by the library */
+    uint64_t host_launches;      /* launches of host batches (one per merged group) */
+    uint64_t host_requests;      /* host batches those launches ran */
 } xd_stats;
 
 /* Create a context on cfg->device (NULL cfg = defaults).  Allocates nothing large until
@@ -129,16 +138,24 @@ xd_status xd_create(const xd_config* cfg, xd_ctx** out);
 
 /* Validate and enqueue a host batch (Sec. 4.4 tuples; Sec. 3 method).  Copies every input
  * to pinned staging memory before returning, so the caller may free its buffers at once.
- * On XD_OK *ticket identifies the batch for xd_poll.  Errors: XD_EINVAL (codes out of the
- * alphabet, a seed outside its sequence, X < 0, a protein batch without matrix, scores
- * that could leave the exact integer range), XD_ENOMEM (the batch does not fit the
- * store cap now or no in-flight slot is free: nothing was queued), XD_EDEVICE. */
+ * On XD_OK *ticket identifies the batch for xd_poll.  A dispatcher thread of the context
+ * launches waiting batches whenever one of the max_inflight launch slots is free; with
+ * continuous batching, every waiting batch with the same scoring, X and delta_b joins that
+ * launch (up to max_batch_pairs), so batches that arrive while others run share the next
+ * launch.  Each batch's results are the same whether it ran alone or merged.  Launches
+ * overlap on the device (copies, packing and tails of one with the extension kernel of
+ * another); the fused persistent extension kernels of different launches run one after
+ * another.  Errors: XD_EINVAL (codes out of the alphabet, a seed outside its sequence, X < 0,
+ * a protein batch without matrix, scores that could leave the exact integer range),
+ * XD_ENOMEM (admitted but unfinished batches would exceed store_bytes_cap, or 65536 batches
+ * are outstanding: nothing was queued; retry after polling), XD_EDEVICE. */
 xd_status xd_submit_batch(xd_ctx* ctx, const xd_batch* batch, uint64_t* ticket);
 
 /* Wait up to wait_ms milliseconds (0 = do not wait, < 0 = wait without limit) for the
  * batch of `ticket`; on XD_OK copies n_pairs results to the host array `out` and retires
  * the ticket.  Returns XD_PENDING if not finished and wait_ms == 0, XD_ETIMEDOUT if the
- * wait expired, XD_ENOTFOUND for an unknown ticket, XD_EDEVICE on a CUDA error. */
+ * wait expired, XD_ENOTFOUND for an unknown ticket, XD_EDEVICE if the launch that ran the
+ * batch failed (the ticket is retired).  Thread-safe: several threads may poll at once. */
 xd_status xd_poll(xd_ctx* ctx, uint64_t ticket, xd_result* out, int32_t wait_ms);
 
 /* Run the whole hot path on device-resident inputs, asynchronously on `stream`
@@ -223,7 +240,8 @@ xd_status xd_probe(xd_ctx* ctx, int32_t op, double* rate);
 xd_status xd_run_device_noalloc(const xd_batch* dev_batch, uint32_t max_side_len, xd_result* d_out,
                                 void* stream);
 
-/* Wait (bounded) for all in-flight work, then free every resource of the context. */
+/* Stop the dispatcher, wait (at most 60 s) for launches in flight, fail batches that never
+ * launched, then free every resource of the context.  XD_ETIMEDOUT if the wait expired. */
 xd_status xd_destroy(xd_ctx* ctx);
 
 /* Last error message of the context (never NULL; "" when none).  ctx may be NULL for

@@ -1,16 +1,19 @@
 // Host runtime behind the C ABI of xdrop.h: contexts, validation, memory admission,
-// pinned staging, in-flight slots with their own streams, tickets, and the device
-// pipeline that runs one batch.
+// pinned staging, the request dispatcher (continuous batching over in-flight slots with
+// their own streams), tickets, and the device pipeline that runs one batch.
 #include <algorithm>
 #include <array>
 #include <atomic>
 #include <chrono>
+#include <condition_variable>
 #include <cstdio>
+#include <deque>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
 #include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -89,16 +92,33 @@ struct BatchView {
     uint32_t delta = 0, max_len = 0;
 };
 
+// One submitted host batch (a request).  Its inputs are copied to a pinned buffer at
+// submit, laid out codes | offsets | lengths | pairs; results are copied out of the slot
+// that ran it when that slot finishes.
+struct Request {
+    enum State { kPending, kLaunched, kDone, kFailed };
+    uint64_t ticket = 0;
+    State state = kPending;
+    xd_status status = XD_OK;
+    std::string err;
+    BatchView v;                 // parameters and sizes; pointers unused
+    HostBuf in;
+    size_t o_offs = 0, o_lens = 0, o_pairs = 0, in_bytes = 0;
+    size_t need = 0;             // device bytes admitted for it
+    std::vector<xd_result> out;
+};
+
+// An in-flight launch: one or more requests merged into one batch on the slot's stream.
 struct Slot {
     bool busy = false;
-    uint64_t ticket = 0;
     uint32_t n_pairs = 0;
-    uint64_t bytes = 0;
+    std::vector<Request*> reqs;
+    std::vector<uint32_t> pair_base;   // first result of each request in the merged batch
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
     Scratch s;
     DevBuf d_in, d_results;
-    HostBuf h_in, h_out;
+    HostBuf h_stage, h_out;
 };
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -171,7 +191,7 @@ struct xd_ctx {
     int device = 0;
     int n_sm = 1;
     uint64_t cap = 0;
-    uint64_t in_flight = 0;
+    uint64_t admitted = 0;       // device bytes of requests not yet finished
     std::vector<Slot> slots;
     uint64_t next_ticket = 1;
     Scratch dev;                 // scratch of xd_run_device
@@ -188,6 +208,23 @@ struct xd_ctx {
     uint64_t launches_at_enable = 0;
     std::string err;
     std::mutex mu;
+    // request dispatcher
+    bool merge = true;           // merge waiting requests with identical parameters
+    uint32_t max_batch_pairs = 1u << 20;
+    uint64_t max_batch_codes = uint64_t(8) << 30;
+    std::deque<Request*> pending;
+    std::unordered_map<uint64_t, Request*> requests;
+    std::vector<HostBuf> pinned_cache;
+    uint64_t pinned_cached = 0;
+    std::condition_variable wake;      // dispatcher: new request or stop
+    std::condition_variable finished;  // pollers: a request finished
+    std::thread dispatcher;
+    bool stop = false;
+    bool stop_timed_out = false;
+    uint64_t merged_launches = 0, merged_requests = 0;
+    // the fused persistent kernel's blocks wait on one another, so two of them never run at
+    // the same time: each waits for the previous one through this event
+    cudaEvent_t coop_done = nullptr;
 };
 
 namespace {
@@ -366,7 +403,9 @@ const TierConfig& tiers_for(const xd_ctx* c, const BatchView& b) {
 }
 
 // The hot path of one batch (Sec. 3 method on every side extension), all on stream st.
-xd_status run_pipeline(xd_ctx* c, Scratch& s, const BatchView& b, xd_result* d_out, cudaStream_t st) {
+// chain: an event that orders the fused persistent launches of the context (may be null).
+xd_status run_pipeline(xd_ctx* c, Scratch& s, const BatchView& b, xd_result* d_out, cudaStream_t st,
+                       cudaEvent_t chain) {
     ScratchPlan plan = plan_scratch(c, b.alpha, b.n_codes, b.n_pairs, b.max_len);
     XD_CUDA(c, ensure_scratch(s, plan));
     bool timed = c->timing && c->ev_used < 4096;
@@ -437,7 +476,9 @@ xd_status run_pipeline(xd_ctx* c, Scratch& s, const BatchView& b, xd_result* d_o
                 // the live queues' slots start unpublished
                 XD_CUDA(c, cudaMemsetAsync(Q.q[0], 0xff, sizeof(uint32_t) * size_t(Q.n_units), st));
                 XD_CUDA(c, cudaMemsetAsync(Q.q[1], 0xff, sizeof(uint32_t) * size_t(Q.n_units), st));
+                if (chain) XD_CUDA(c, cudaStreamWaitEvent(st, chain, 0));
                 XD_CUDA(c, launch_fused_levels(P, Q, tc, c->n_sm, st));
+                if (chain) XD_CUDA(c, cudaEventRecord(chain, st));
                 XD_CUDA(c, mark(4));
                 lv = 3;
                 launches += 1;
@@ -471,6 +512,254 @@ xd_status run_pipeline(xd_ctx* c, Scratch& s, const BatchView& b, xd_result* d_o
     return XD_OK;
 }
 
+// ---------------------------------------------------------------- request dispatcher
+
+constexpr size_t kMaxRequests = 1u << 16;
+constexpr uint64_t kPinnedCacheMax = uint64_t(16) << 30;
+constexpr size_t kGatherBelow = size_t(1) << 20;   // smaller code arrays are gathered on the host
+
+// Pinned buffers are cached across requests (page-locking memory is slow), in power-of-two
+// size classes from 64 KiB.
+cudaError_t take_pinned(xd_ctx* c, size_t bytes, HostBuf& out) {
+    size_t cls = size_t(1) << 16;
+    while (cls < bytes) cls <<= 1;
+    for (size_t k = 0; k < c->pinned_cache.size(); k++) {
+        if (c->pinned_cache[k].cap != cls) continue;
+        out = c->pinned_cache[k];
+        c->pinned_cached -= out.cap;
+        c->pinned_cache[k] = c->pinned_cache.back();
+        c->pinned_cache.pop_back();
+        return cudaSuccess;
+    }
+    out = HostBuf{};
+    cudaError_t e = cudaHostAlloc(&out.p, cls, cudaHostAllocDefault);
+    if (e == cudaSuccess) out.cap = cls;
+    else out.p = nullptr;
+    return e;
+}
+
+void give_pinned(xd_ctx* c, HostBuf& b) {
+    if (!b.p) return;
+    c->pinned_cache.push_back(b);
+    c->pinned_cached += b.cap;
+    b = HostBuf{};
+    while (c->pinned_cached > kPinnedCacheMax && !c->pinned_cache.empty()) {
+        auto big = std::max_element(c->pinned_cache.begin(), c->pinned_cache.end(),
+                                    [](const HostBuf& x, const HostBuf& y) { return x.cap < y.cap; });
+        c->pinned_cached -= big->cap;
+        cudaFreeHost(big->p);
+        c->pinned_cache.erase(big);
+    }
+}
+
+// Two requests can share a launch when the kernels see the same parameters.
+bool same_params(const BatchView& a, const BatchView& b) {
+    return a.alpha == b.alpha && a.gap == b.gap && a.X == b.X && a.delta == b.delta &&
+           std::memcmp(a.sim, b.sim, size_t(a.alpha) * a.alpha) == 0;
+}
+
+void finish_request(xd_ctx* c, Request* r, xd_status st, const std::string& msg) {
+    r->state = st == XD_OK ? Request::kDone : Request::kFailed;
+    r->status = st;
+    r->err = msg;
+    give_pinned(c, r->in);
+    c->admitted -= std::min(c->admitted, uint64_t(r->need));
+}
+
+// Launch the oldest waiting request on a free slot, together with every later waiting
+// request of the same parameters while the merged batch stays under the size caps.
+// Called with the context lock held.
+void launch_merged(xd_ctx* c, Slot& slot) {
+    std::vector<Request*> take;
+    const Request* first = c->pending.front();
+    uint64_t n_codes = 0, n_seqs = 0, n_pairs = 0;
+    for (auto it = c->pending.begin(); it != c->pending.end();) {
+        Request* r = *it;
+        const bool fits = take.empty() ||
+                          (c->merge && same_params(r->v, first->v) &&
+                           n_pairs + r->v.n_pairs <= c->max_batch_pairs &&
+                           n_codes + r->v.n_codes <= c->max_batch_codes &&
+                           n_seqs + r->v.n_seqs <= 0xffffffffull);
+        if (fits) {
+            take.push_back(r);
+            n_codes += r->v.n_codes;
+            n_seqs += r->v.n_seqs;
+            n_pairs += r->v.n_pairs;
+            it = c->pending.erase(it);
+        } else {
+            ++it;
+        }
+        if (!c->merge) break;
+    }
+    BatchView v = first->v;
+    v.n_codes = n_codes;
+    v.n_seqs = uint32_t(n_seqs);
+    v.n_pairs = uint32_t(n_pairs);
+    v.max_len = 0;
+    for (Request* r : take) v.max_len = std::max(v.max_len, r->v.max_len);
+    const size_t o_offs = align_up(n_codes, 256);
+    const size_t o_lens = o_offs + align_up(8 * n_seqs, 256);
+    const size_t o_pairs = o_lens + align_up(4 * n_seqs, 256);
+    const size_t in_bytes = o_pairs + align_up(sizeof(xd_pair) * n_pairs, 256);
+    const size_t out_bytes = sizeof(xd_result) * n_pairs + 16;
+    cudaStream_t st = slot.stream;
+    auto fail_all = [&](xd_status code, const std::string& msg) {
+        for (Request* r : take) finish_request(c, r, code, msg);
+        c->finished.notify_all();
+    };
+    auto cuda_err = [&](cudaError_t e, const char* what) {
+        fail_all(XD_EDEVICE, std::string(what) + ": " + cudaGetErrorString(e));
+    };
+    cudaError_t e;
+    if ((e = grow(slot.d_in, in_bytes)) != cudaSuccess) return cuda_err(e, "device input buffer");
+    if ((e = grow(slot.d_results, out_bytes)) != cudaSuccess) return cuda_err(e, "device result buffer");
+    if ((e = grow_pinned(slot.h_out, out_bytes)) != cudaSuccess) return cuda_err(e, "pinned result buffer");
+    char* d = static_cast<char*>(slot.d_in.p);
+    if (take.size() == 1) {
+        // one request: its pinned buffer already has the device layout
+        e = cudaMemcpyAsync(d, take[0]->in.p, take[0]->in_bytes, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_err(e, "cudaMemcpyAsync");
+    } else {
+        // small code arrays and all metadata go through the slot's stage buffer, laid out
+        // like the device buffer; large code arrays are copied from the requests' buffers
+        if ((e = grow_pinned(slot.h_stage, in_bytes)) != cudaSuccess) return cuda_err(e, "pinned stage buffer");
+        char* h = static_cast<char*>(slot.h_stage.p);
+        uint64_t code_base = 0, seq_base = 0, pair_base = 0;
+        size_t run_a = 0, run_b = 0;   // staged code bytes not yet copied
+        auto flush_run = [&]() -> cudaError_t {
+            cudaError_t e2 = cudaSuccess;
+            if (run_b > run_a) e2 = cudaMemcpyAsync(d + run_a, h + run_a, run_b - run_a, cudaMemcpyHostToDevice, st);
+            run_a = run_b;
+            return e2;
+        };
+        for (Request* r : take) {
+            const char* src = static_cast<const char*>(r->in.p);
+            const uint64_t nc = r->v.n_codes;
+            if (nc >= kGatherBelow) {
+                if ((e = flush_run()) != cudaSuccess) return cuda_err(e, "cudaMemcpyAsync");
+                e = cudaMemcpyAsync(d + code_base, src, nc, cudaMemcpyHostToDevice, st);
+                if (e != cudaSuccess) return cuda_err(e, "cudaMemcpyAsync");
+                run_a = run_b = code_base + nc;
+            } else {
+                std::memcpy(h + code_base, src, nc);
+                run_b = code_base + nc;
+            }
+            auto* offs = reinterpret_cast<uint64_t*>(h + o_offs) + seq_base;
+            const auto* r_offs = reinterpret_cast<const uint64_t*>(src + r->o_offs);
+            for (uint32_t q = 0; q < r->v.n_seqs; q++) offs[q] = r_offs[q] + code_base;
+            std::memcpy(reinterpret_cast<uint32_t*>(h + o_lens) + seq_base, src + r->o_lens, 4ull * r->v.n_seqs);
+            auto* prs = reinterpret_cast<xd_pair*>(h + o_pairs) + pair_base;
+            const auto* r_prs = reinterpret_cast<const xd_pair*>(src + r->o_pairs);
+            for (uint32_t q = 0; q < r->v.n_pairs; q++) {
+                prs[q] = r_prs[q];
+                prs[q].h_id += uint32_t(seq_base);
+                prs[q].v_id += uint32_t(seq_base);
+            }
+            code_base += nc;
+            seq_base += r->v.n_seqs;
+            pair_base += r->v.n_pairs;
+        }
+        if ((e = flush_run()) != cudaSuccess) return cuda_err(e, "cudaMemcpyAsync");
+        e = cudaMemcpyAsync(d + o_offs, h + o_offs, in_bytes - o_offs, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_err(e, "cudaMemcpyAsync");
+    }
+    v.codes = reinterpret_cast<const uint8_t*>(d);
+    v.offsets = reinterpret_cast<const uint64_t*>(d + o_offs);
+    v.lengths = reinterpret_cast<const uint32_t*>(d + o_lens);
+    v.pairs = reinterpret_cast<const xd_pair*>(d + o_pairs);
+    auto* d_res = static_cast<xd_result*>(slot.d_results.p);
+    xd_status ps = run_pipeline(c, slot.s, v, d_res, st, c->coop_done);
+    if (ps != XD_OK) return fail_all(ps, c->err);
+    if ((e = cudaMemcpyAsync(slot.h_out.p, d_res, sizeof(xd_result) * n_pairs, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(static_cast<char*>(slot.h_out.p) + out_bytes - 16, slot.s.err.p, 4,
+                             cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaEventRecord(slot.done, st)) != cudaSuccess)
+        return cuda_err(e, "result copy");
+    slot.busy = true;
+    slot.n_pairs = uint32_t(n_pairs);
+    slot.reqs = take;
+    slot.pair_base.clear();
+    uint32_t base = 0;
+    for (Request* r : take) {
+        r->state = Request::kLaunched;
+        slot.pair_base.push_back(base);
+        base += r->v.n_pairs;
+    }
+    c->merged_launches += 1;
+    c->merged_requests += take.size();
+}
+
+// Copy a finished slot's results to its requests.  Context lock held.
+void retire_slot(xd_ctx* c, Slot& slot, cudaError_t status) {
+    const size_t out_bytes = sizeof(xd_result) * size_t(slot.n_pairs) + 16;
+    uint32_t flags = 0;
+    if (status == cudaSuccess) std::memcpy(&flags, static_cast<char*>(slot.h_out.p) + out_bytes - 16, 4);
+    for (size_t k = 0; k < slot.reqs.size(); k++) {
+        Request* r = slot.reqs[k];
+        if (status != cudaSuccess) {
+            finish_request(c, r, XD_EDEVICE, std::string("batch failed: ") + cudaGetErrorString(status));
+        } else if (flags) {
+            finish_request(c, r, XD_EDEVICE, "device validation flags " + std::to_string(flags));
+        } else {
+            r->out.resize(r->v.n_pairs);
+            if (r->v.n_pairs)
+                std::memcpy(r->out.data(), static_cast<const xd_result*>(slot.h_out.p) + slot.pair_base[k],
+                            sizeof(xd_result) * r->v.n_pairs);
+            finish_request(c, r, XD_OK, "");
+        }
+    }
+    slot.reqs.clear();
+    slot.busy = false;
+}
+
+// The dispatcher thread: retires finished slots and launches waiting requests whenever a
+// slot is free, so requests that arrive while others run join the next launch.
+void dispatch_loop(xd_ctx* c) {
+    cudaSetDevice(c->device);
+    std::unique_lock<std::mutex> lk(c->mu);
+    std::chrono::steady_clock::time_point stop_at{};
+    bool stopping = false;
+    for (;;) {
+        if (c->stop && !stopping) {
+            stopping = true;
+            stop_at = std::chrono::steady_clock::now();
+        }
+        bool any_busy = false, retired = false;
+        for (Slot& sl : c->slots) {
+            if (!sl.busy) continue;
+            const cudaError_t q = cudaEventQuery(sl.done);
+            if (q == cudaErrorNotReady) {
+                any_busy = true;
+                continue;
+            }
+            retire_slot(c, sl, q);
+            retired = true;
+        }
+        if (retired) c->finished.notify_all();
+        if (c->stop && !any_busy) break;
+        if (stopping && std::chrono::steady_clock::now() - stop_at > std::chrono::seconds(60)) {
+            for (Slot& sl : c->slots)
+                if (sl.busy) retire_slot(c, sl, cudaErrorLaunchTimeout);
+            c->stop_timed_out = true;
+            break;
+        }
+        if (!c->stop) {
+            for (Slot& sl : c->slots) {
+                if (c->pending.empty()) break;
+                if (sl.busy) continue;
+                launch_merged(c, sl);
+                any_busy = any_busy || sl.busy;
+            }
+        }
+        if (any_busy) c->wake.wait_for(lk, std::chrono::microseconds(40));
+        else if (c->pending.empty() && !c->stop) c->wake.wait_for(lk, std::chrono::milliseconds(50));
+    }
+    // stopping: requests that never launched fail
+    for (Request* r : c->pending) finish_request(c, r, XD_EDEVICE, "context destroyed");
+    c->pending.clear();
+    c->finished.notify_all();
+}
+
 }  // namespace
 
 extern "C" {
@@ -500,12 +789,15 @@ xd_status xd_create(const xd_config* cfg, xd_ctx** out) {
     c->device = dev;
     c->n_sm = prop.multiProcessorCount;
     c->cap = cfg && cfg->store_bytes_cap ? cfg->store_bytes_cap : (uint64_t(64) << 30);
-    int inflight = cfg && cfg->max_inflight > 0 ? cfg->max_inflight : 8;
+    int inflight = cfg && cfg->max_inflight > 0 ? cfg->max_inflight : 3;
     c->slots.resize(inflight);
+    c->merge = !(cfg && cfg->batching < 0);
+    if (cfg && cfg->max_batch_pairs) c->max_batch_pairs = cfg->max_batch_pairs;
     const char* mode = std::getenv("XD_TIERS");
     c->generic_only = mode && std::strcmp(mode, "generic") == 0;
     default_tiers(c);
     if ((e = cudaStreamCreateWithFlags(&c->dev_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&c->coop_done, cudaEventDisableTiming)) != cudaSuccess ||
         (e = grow(c->stats, 128)) != cudaSuccess || (e = cudaMemset(c->stats.p, 0, 128)) != cudaSuccess) {
         delete c;
         return fail(nullptr, XD_EDEVICE, cudaGetErrorString(e));
@@ -517,6 +809,7 @@ xd_status xd_create(const xd_config* cfg, xd_ctx** out) {
             return fail(nullptr, XD_EDEVICE, cudaGetErrorString(e));
         }
     }
+    c->dispatcher = std::thread(dispatch_loop, c);
     *out = c;
     return XD_OK;
 }
@@ -557,7 +850,11 @@ xd_status xd_run_device(xd_ctx* c, const xd_batch* b, xd_result* d_out, void* st
     } else {
         v.max_len = c->reserved_len;
     }
-    return run_pipeline(c, c->dev, v, d_out, st);
+    // order the fused launch after the host batches' ones (not possible inside a capture,
+    // where the caller orders its graphs)
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    XD_CUDA(c, cudaStreamIsCapturing(st, &cs));
+    return run_pipeline(c, c->dev, v, d_out, st, cs == cudaStreamCaptureStatusNone ? c->coop_done : nullptr);
 }
 
 xd_status xd_device_status(xd_ctx* c, uint32_t* flags) {
@@ -572,95 +869,91 @@ xd_status xd_device_status(xd_ctx* c, uint32_t* flags) {
 
 xd_status xd_submit_batch(xd_ctx* c, const xd_batch* b, uint64_t* ticket) {
     if (!c || !b || !ticket) return XD_EINVAL;
-    std::lock_guard<std::mutex> lk(c->mu);
-    XD_CUDA(c, cudaSetDevice(c->device));
+    std::unique_lock<std::mutex> lk(c->mu);
     BatchView v;
     xd_status s = scoring_view(c, b, v);
     if (s != XD_OK) return s;
     uint32_t max_len = 0;
     if ((s = validate_host(c, b, v, &max_len)) != XD_OK) return s;
     v.max_len = max_len;
-    // admission by device memory
-    size_t in_bytes = align_up(b->n_codes, 256) + align_up(8ull * b->n_seqs, 256) +
-                      align_up(4ull * b->n_seqs, 256) + align_up(sizeof(xd_pair) * b->n_pairs, 256);
-    size_t out_bytes = sizeof(xd_result) * size_t(b->n_pairs) + 16;
-    size_t need = in_bytes + out_bytes + plan_bytes(plan_scratch(c, v.alpha, b->n_codes, b->n_pairs, max_len));
-    if (c->in_flight + need > c->cap)
+    // admission by device memory: inputs, results and the scratch of a batch this size
+    const size_t o_offs = align_up(b->n_codes, 256);
+    const size_t o_lens = o_offs + align_up(8ull * b->n_seqs, 256);
+    const size_t o_pairs = o_lens + align_up(4ull * b->n_seqs, 256);
+    const size_t in_bytes = o_pairs + align_up(sizeof(xd_pair) * b->n_pairs, 256);
+    const size_t out_bytes = sizeof(xd_result) * size_t(b->n_pairs) + 16;
+    // (the band rows of the generic tier belong to the launch slot, not to the batch)
+    const ScratchPlan plan = plan_scratch(c, v.alpha, b->n_codes, b->n_pairs, max_len);
+    const size_t need = in_bytes + out_bytes + plan_bytes(plan) - plan.generic;
+    if (c->admitted + need > c->cap)
         return fail(c, XD_ENOMEM, "batch needs " + std::to_string(need) + " device bytes; " +
-                                      std::to_string(c->cap - std::min(c->cap, c->in_flight)) + " available under the cap");
-    Slot* slot = nullptr;
-    for (Slot& q : c->slots)
-        if (!q.busy) { slot = &q; break; }
-    if (!slot) return fail(c, XD_ENOMEM, "no free in-flight slot");
-    // stage inputs in pinned memory (the caller may free its buffers on return)
-    size_t o_codes = 0, o_offs = align_up(b->n_codes, 256);
-    size_t o_lens = o_offs + align_up(8ull * b->n_seqs, 256);
-    size_t o_pairs = o_lens + align_up(4ull * b->n_seqs, 256);
-    XD_CUDA(c, cudaEventSynchronize(slot->done));   // the slot's previous copies are finished
-    XD_CUDA(c, grow_pinned(slot->h_in, in_bytes));
-    XD_CUDA(c, grow_pinned(slot->h_out, out_bytes));
-    char* h = static_cast<char*>(slot->h_in.p);
-    const size_t bad_block = par_copy_check(h + o_codes, b->seq_codes, b->n_codes, v.alpha);
+                                      std::to_string(c->cap - std::min(c->cap, c->admitted)) + " available under the cap");
+    if (c->requests.size() >= kMaxRequests) return fail(c, XD_ENOMEM, "too many requests outstanding");
+    auto* r = new Request();
+    r->v = v;
+    r->o_offs = o_offs;
+    r->o_lens = o_lens;
+    r->o_pairs = o_pairs;
+    r->in_bytes = in_bytes;
+    r->need = need;
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e == cudaSuccess) e = take_pinned(c, in_bytes, r->in);
+    if (e != cudaSuccess) {
+        delete r;
+        return cuda_fail(c, e, "pinned staging buffer");
+    }
+    c->admitted += need;
+    // copy (and check the residue codes) without the lock: the caller may free its arrays
+    // when this returns
+    lk.unlock();
+    char* h = static_cast<char*>(r->in.p);
+    const size_t bad_block = par_copy_check(h, b->seq_codes, b->n_codes, v.alpha);
+    if (bad_block == SIZE_MAX) {
+        std::memcpy(h + o_offs, b->seq_offsets, 8ull * b->n_seqs);
+        std::memcpy(h + o_lens, b->seq_lengths, 4ull * b->n_seqs);
+        std::memcpy(h + o_pairs, b->pairs, sizeof(xd_pair) * b->n_pairs);
+    }
+    lk.lock();
     if (bad_block != SIZE_MAX) {
         size_t t = bad_block;
         while (t < b->n_codes && b->seq_codes[t] < v.alpha) t++;
+        finish_request(c, r, XD_EINVAL, "");
+        delete r;
         return fail(c, XD_EINVAL, "residue code outside the alphabet at byte " + std::to_string(t));
     }
-    std::memcpy(h + o_offs, b->seq_offsets, 8ull * b->n_seqs);
-    std::memcpy(h + o_lens, b->seq_lengths, 4ull * b->n_seqs);
-    std::memcpy(h + o_pairs, b->pairs, sizeof(xd_pair) * b->n_pairs);
-    XD_CUDA(c, grow(slot->d_in, in_bytes));
-    XD_CUDA(c, grow(slot->d_results, out_bytes));
-    cudaStream_t st = slot->stream;
-    XD_CUDA(c, cudaMemcpyAsync(slot->d_in.p, h, in_bytes, cudaMemcpyHostToDevice, st));
-    char* d = static_cast<char*>(slot->d_in.p);
-    v.codes = reinterpret_cast<const uint8_t*>(d + o_codes);
-    v.offsets = reinterpret_cast<const uint64_t*>(d + o_offs);
-    v.lengths = reinterpret_cast<const uint32_t*>(d + o_lens);
-    v.pairs = reinterpret_cast<const xd_pair*>(d + o_pairs);
-    auto* d_res = static_cast<xd_result*>(slot->d_results.p);
-    if ((s = run_pipeline(c, slot->s, v, d_res, st)) != XD_OK) return s;
-    XD_CUDA(c, cudaMemcpyAsync(slot->h_out.p, d_res, sizeof(xd_result) * size_t(b->n_pairs),
-                               cudaMemcpyDeviceToHost, st));
-    XD_CUDA(c, cudaMemcpyAsync(static_cast<char*>(slot->h_out.p) + out_bytes - 16, slot->s.err.p, 4,
-                               cudaMemcpyDeviceToHost, st));
-    XD_CUDA(c, cudaEventRecord(slot->done, st));
-    slot->busy = true;
-    slot->ticket = c->next_ticket++;
-    slot->n_pairs = b->n_pairs;
-    slot->bytes = need;
-    c->in_flight += need;
-    *ticket = slot->ticket;
+    r->ticket = c->next_ticket++;
+    c->requests[r->ticket] = r;
+    c->pending.push_back(r);
+    *ticket = r->ticket;
+    c->wake.notify_one();
     return XD_OK;
 }
 
 xd_status xd_poll(xd_ctx* c, uint64_t ticket, xd_result* out, int32_t wait_ms) {
     if (!c) return XD_EINVAL;
     std::unique_lock<std::mutex> lk(c->mu);
-    XD_CUDA(c, cudaSetDevice(c->device));
-    Slot* slot = nullptr;
-    for (Slot& q : c->slots)
-        if (q.busy && q.ticket == ticket) { slot = &q; break; }
-    if (!slot) return fail(c, XD_ENOTFOUND, "unknown ticket " + std::to_string(ticket));
-    auto t0 = std::chrono::steady_clock::now();
-    for (;;) {
-        cudaError_t e = cudaEventQuery(slot->done);
-        if (e == cudaSuccess) break;
-        if (e != cudaErrorNotReady) return cuda_fail(c, e, "cudaEventQuery");
+    auto it = c->requests.find(ticket);
+    if (it == c->requests.end()) return fail(c, XD_ENOTFOUND, "unknown ticket " + std::to_string(ticket));
+    Request* r = it->second;
+    auto finished = [&]() { return r->state == Request::kDone || r->state == Request::kFailed; };
+    if (!finished()) {
         if (wait_ms == 0) return XD_PENDING;
-        auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
-        if (wait_ms > 0 && ms >= wait_ms) return fail(c, XD_ETIMEDOUT, "batch still running");
-        lk.unlock();
-        std::this_thread::sleep_for(std::chrono::microseconds(ms < 5 ? 20 : 200));
-        lk.lock();
+        if (wait_ms < 0) {
+            c->finished.wait(lk, finished);
+        } else if (!c->finished.wait_for(lk, std::chrono::milliseconds(wait_ms), finished)) {
+            return fail(c, XD_ETIMEDOUT, "batch still running");
+        }
     }
-    size_t out_bytes = sizeof(xd_result) * size_t(slot->n_pairs) + 16;
-    uint32_t flags = 0;
-    std::memcpy(&flags, static_cast<char*>(slot->h_out.p) + out_bytes - 16, 4);
-    if (out && slot->n_pairs) par_memcpy(out, slot->h_out.p, sizeof(xd_result) * size_t(slot->n_pairs));
-    slot->busy = false;
-    c->in_flight -= std::min(c->in_flight, slot->bytes);
-    if (flags) return fail(c, XD_EDEVICE, "device validation flags " + std::to_string(flags));
+    c->requests.erase(it);
+    if (r->state == Request::kFailed) {
+        xd_status st = r->status;
+        std::string msg = r->err;
+        delete r;
+        return fail(c, st, msg);
+    }
+    lk.unlock();
+    if (out && !r->out.empty()) par_memcpy(out, r->out.data(), sizeof(xd_result) * r->out.size());
+    delete r;
     return XD_OK;
 }
 
@@ -671,6 +964,7 @@ xd_status xd_get_stats(const xd_ctx* c, xd_stats* out) {
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
     if (c->stats.p) cudaMemcpy(dev, c->stats.p, 128, cudaMemcpyDeviceToHost);
+    std::lock_guard<std::mutex> lk(const_cast<xd_ctx*>(c)->mu);
     out->batches = c->batches;
     out->pairs = c->pairs;
     out->units_tier[0] = dev[0];
@@ -679,6 +973,8 @@ xd_status xd_get_stats(const xd_ctx* c, xd_stats* out) {
     out->escalations = dev[3];
     out->cells = dev[4] + dev[5] + dev[6];
     out->kernel_launches = c->launches;
+    out->host_launches = c->merged_launches;
+    out->host_requests = c->merged_requests;
     return XD_OK;
 }
 
@@ -744,25 +1040,25 @@ xd_status xd_probe(xd_ctx* c, int32_t op, double* rate) {
 
 xd_status xd_destroy(xd_ctx* c) {
     if (!c) return XD_EINVAL;
-    cudaSetDevice(c->device);
-    xd_status rc = XD_OK;
-    auto t0 = std::chrono::steady_clock::now();
-    for (Slot& s : c->slots) {
-        if (!s.done) continue;
-        while (cudaEventQuery(s.done) == cudaErrorNotReady) {
-            if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(60)) {
-                rc = XD_ETIMEDOUT;
-                break;
-            }
-            std::this_thread::sleep_for(std::chrono::milliseconds(1));
-        }
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        c->stop = true;
     }
+    c->wake.notify_all();
+    if (c->dispatcher.joinable()) c->dispatcher.join();   // waits (bounded) for in-flight slots
+    cudaSetDevice(c->device);
+    const xd_status rc = c->stop_timed_out ? XD_ETIMEDOUT : XD_OK;
     if (rc == XD_OK) cudaDeviceSynchronize();
+    for (auto& kv : c->requests) {
+        if (kv.second->in.p) cudaFreeHost(kv.second->in.p);
+        delete kv.second;
+    }
+    for (HostBuf& b : c->pinned_cache) cudaFreeHost(b.p);
     for (Slot& s : c->slots) {
         release(s.s);
         release(s.d_in);
         release(s.d_results);
-        if (s.h_in.p) cudaFreeHost(s.h_in.p);
+        if (s.h_stage.p) cudaFreeHost(s.h_stage.p);
         if (s.h_out.p) cudaFreeHost(s.h_out.p);
         if (s.stream) cudaStreamDestroy(s.stream);
         if (s.done) cudaEventDestroy(s.done);
@@ -772,6 +1068,7 @@ xd_status xd_destroy(xd_ctx* c) {
     for (auto& set : c->ev_sets)
         for (cudaEvent_t ev : set) cudaEventDestroy(ev);
     if (c->dev_stream) cudaStreamDestroy(c->dev_stream);
+    if (c->coop_done) cudaEventDestroy(c->coop_done);
     delete c;
     return rc;
 }

@@ -25,7 +25,8 @@ PAIR_DTYPE = np.dtype([("h_id", np.uint32), ("v_id", np.uint32), ("h_seed", np.u
 
 class xd_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("store_bytes_cap", ctypes.c_uint64),
-                ("max_inflight", ctypes.c_int32), ("tune_table", ctypes.c_char_p)]
+                ("max_inflight", ctypes.c_int32), ("tune_table", ctypes.c_char_p),
+                ("batching", ctypes.c_int32), ("max_batch_pairs", ctypes.c_uint32)]
 
 
 class xd_scoring(ctypes.Structure):
@@ -44,7 +45,8 @@ class xd_batch(ctypes.Structure):
 class xd_stats(ctypes.Structure):
     _fields_ = [("batches", ctypes.c_uint64), ("pairs", ctypes.c_uint64), ("cells", ctypes.c_uint64),
                 ("units_tier", ctypes.c_uint64 * 3), ("escalations", ctypes.c_uint64),
-                ("kernel_launches", ctypes.c_uint64)]
+                ("kernel_launches", ctypes.c_uint64), ("host_launches", ctypes.c_uint64),
+                ("host_requests", ctypes.c_uint64)]
 
 
 class xd_timing(ctypes.Structure):
@@ -56,7 +58,7 @@ class xd_timing(ctypes.Structure):
                 ("launches", ctypes.c_uint64), ("window_shifts", ctypes.c_uint64)]
 
 
-assert ctypes.sizeof(xd_batch) == 88 and RESULT_DTYPE.itemsize == 56
+assert ctypes.sizeof(xd_batch) == 88 and RESULT_DTYPE.itemsize == 56 and ctypes.sizeof(xd_config) == 40
 
 _LIB = None
 
@@ -114,9 +116,10 @@ def xd_last_error(ctx=None):
     return lib().xd_last_error(ctx).decode()
 
 
-def xd_create(device=0, store_bytes_cap=0, max_inflight=0, tune_table=None):
+def xd_create(device=0, store_bytes_cap=0, max_inflight=0, tune_table=None, batching=0,
+              max_batch_pairs=0):
     cfg = xd_config(device, store_bytes_cap, max_inflight,
-                    None if tune_table is None else tune_table.encode())
+                    None if tune_table is None else tune_table.encode(), batching, max_batch_pairs)
     out = ctypes.c_void_p()
     rc = lib().xd_create(ctypes.byref(cfg), ctypes.byref(out))
     if rc != XD_OK:
@@ -199,7 +202,8 @@ def xd_get_stats(ctx):
         raise XdError(rc, xd_last_error(ctx))
     return {"batches": s.batches, "pairs": s.pairs, "cells": s.cells,
             "units_tier": list(s.units_tier), "escalations": s.escalations,
-            "kernel_launches": s.kernel_launches}
+            "kernel_launches": s.kernel_launches, "host_launches": s.host_launches,
+            "host_requests": s.host_requests}
 
 
 def xd_set_timing(ctx, enable=True):

@@ -97,6 +97,28 @@ class Batch:
                      self.match, self.mismatch, self.gap, self.matrix, self.X, self.delta,
                      self.name + "[subset]", dict(self.meta))
 
+    def pair_range(self, a, b):
+        """Batch of the pairs [a, b) sharing this batch's arrays where possible.
+
+        Needs the generator layout (pair p uses sequences 2p and 2p+1, stored in order), so
+        the codes of the range are one contiguous view; offsets and ids are rebased."""
+        a, b = int(a), int(b)
+        if not (0 <= a <= b <= self.n_pairs):
+            raise ValueError("pair range out of bounds")
+        ids = self.pairs[a:b, :2]
+        if b > a and not (np.array_equal(ids[:, 0], np.arange(2 * a, 2 * b, 2)) and
+                          np.array_equal(ids[:, 1], np.arange(2 * a + 1, 2 * b, 2))):
+            raise ValueError("pair_range needs the generator's sequence layout")
+        lens = self.lengths[2 * a:2 * b]
+        base = int(self.offsets[2 * a]) if b > a else 0
+        end = base + int(lens.astype(np.int64).sum())
+        offs = self.offsets[2 * a:2 * b] - np.uint64(base)
+        pairs = self.pairs[a:b].copy()
+        pairs[:, :2] -= np.uint32(2 * a)
+        return Batch(self.alphabet, self.codes[base:end], offs, lens, pairs,
+                     self.match, self.mismatch, self.gap, self.matrix, self.X, self.delta,
+                     f"{self.name}[{a}:{b}]", dict(self.meta))
+
     def with_params(self, X=None, delta=None):
         b = Batch(self.alphabet, self.codes, self.offsets, self.lengths, self.pairs,
                   self.match, self.mismatch, self.gap, self.matrix,

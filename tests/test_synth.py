@@ -1,5 +1,6 @@
 """Synthetic workloads: seeded, valid seed tuples, and the documented shapes."""
 import numpy as np
+import pytest
 
 import synth
 
@@ -58,3 +59,26 @@ def test_subset_roundtrip():
             n_ = s.pairs[new, side]
             assert np.array_equal(b.codes[b.offsets[o]:b.offsets[o] + b.lengths[o]],
                                   s.codes[s.offsets[n_]:s.offsets[n_] + s.lengths[n_]])
+
+
+def test_pair_range_matches_subset():
+    b = synth.dna_longread(n_pairs=200)
+    for a, e in ((0, 0), (0, 1), (17, 90), (150, 200)):
+        r = b.pair_range(a, e)
+        s = b.subset(np.arange(a, e))
+        assert np.array_equal(r.codes, s.codes)
+        assert np.array_equal(r.offsets, s.offsets)
+        assert np.array_equal(r.lengths, s.lengths)
+        assert np.array_equal(r.pairs, s.pairs)
+    with pytest.raises(ValueError):
+        b.pair_range(5, 201)
+    with pytest.raises(ValueError):
+        b.pair_range(-1, 2)
+    with pytest.raises(ValueError):
+        _swap(b).pair_range(0, 2)      # not the generator's layout
+
+
+def _swap(b):
+    p = b.pairs.copy()
+    p[:, [0, 1]] = p[:, [1, 0]]
+    return synth.Batch(b.alphabet, b.codes, b.offsets, b.lengths, p)
