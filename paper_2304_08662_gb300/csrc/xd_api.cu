@@ -187,6 +187,14 @@ void par_memcpy(void* dst, const void* src, size_t n) { par_copy_check(dst, src,
 
 }  // namespace
 
+// One tuned configuration: the register-level chain and its launch parameters for batches of
+// one alphabet, X bucket and length bucket.
+struct TuneEntry {
+    int alpha = 4, xb = 0, lb = 0;
+    TierConfig cfg{};
+    float ms = 0;
+};
+
 struct xd_ctx {
     int device = 0;
     int n_sm = 1;
@@ -198,7 +206,9 @@ struct xd_ctx {
     uint32_t reserved_len = 0;
     cudaStream_t dev_stream = nullptr;
     bool generic_only = false;
-    TierConfig tiers{}, tiers_small_x{}, tiers_large_x{};
+    TierConfig tiers{}, tiers_small_x{}, tiers_large_x{}, tiers_protein{};
+    std::vector<TuneEntry> tuned;      // autotuned configurations by (alphabet, X, length) bucket
+    const TierConfig* force_tiers = nullptr;   // set while the autotuner times a candidate
     DevBuf stats;                // uint64 [16]: cumulative per-batch counters (see Problem::stats)
     uint64_t batches = 0, pairs = 0, launches = 0;
     bool timing = false;
@@ -383,6 +393,17 @@ void default_tiers(xd_ctx* c) {
     set_chain(c->tiers_small_x, {kG1C32, kG16C16, kG32C16, kG32C32});
     c->tiers_large_x = t;
     set_chain(c->tiers_large_x, {kG4C16, kG16C16, kG32C32});
+    c->tiers_protein = t;
+    set_chain(c->tiers_protein, {kG4C16, kG16C16, kG32C32});
+    c->tiers_protein.fused = env_int("XD_FUSED_PROT", 0) != 0;   // separate launches measured faster
+    if (const char* ch = std::getenv("XD_CHAIN_PROT")) {
+        c->tiers_protein.n_levels = 0;
+        for (const char* q = ch; *q && c->tiers_protein.n_levels < kLevels - 2;) {
+            c->tiers_protein.variant[c->tiers_protein.n_levels++] = std::atoi(q);
+            while (*q && *q != ',') q++;
+            if (*q == ',') q++;
+        }
+    }
     if (const char* ch = std::getenv("XD_CHAIN")) {
         // comma-separated variant ids, used for every X
         TierConfig forced = t;
@@ -396,7 +417,15 @@ void default_tiers(xd_ctx* c) {
     }
 }
 
+int x_bucket(int32_t X) { return X <= 15 ? 0 : X <= 30 ? 1 : 2; }
+int len_bucket(uint32_t max_len) { return max_len <= 2048 ? 0 : max_len <= 20000 ? 1 : 2; }
+
 const TierConfig& tiers_for(const xd_ctx* c, const BatchView& b) {
+    if (c->force_tiers) return *c->force_tiers;
+    const int xb = x_bucket(b.X), lb = len_bucket(b.max_len);
+    for (const TuneEntry& t : c->tuned)
+        if (t.alpha == b.alpha && t.xb == xb && t.lb == lb) return t.cfg;
+    if (b.alpha == 20) return c->tiers_protein;
     if (b.X <= 15) return c->tiers_small_x;
     if (b.X <= 30) return c->tiers;
     return c->tiers_large_x;
@@ -472,7 +501,7 @@ xd_status run_pipeline(xd_ctx* c, Scratch& s, const BatchView& b, xd_result* d_o
         } else {
             const TierConfig& tc = tiers_for(c, b);
             int lv = 0;
-            if (tc.fused && fused_supported(tc)) {
+            if (tc.fused && fused_supported(tc, b.alpha)) {
                 // the live queues' slots start unpublished
                 XD_CUDA(c, cudaMemsetAsync(Q.q[0], 0xff, sizeof(uint32_t) * size_t(Q.n_units), st));
                 XD_CUDA(c, cudaMemsetAsync(Q.q[1], 0xff, sizeof(uint32_t) * size_t(Q.n_units), st));
@@ -760,6 +789,144 @@ void dispatch_loop(xd_ctx* c) {
     c->finished.notify_all();
 }
 
+// ---------------------------------------------------------------- tuning table
+
+// One line per entry:  alpha=4 xb=1 lb=1 chain=1,4,5,6 chunk=1 fused=1 every1=4 every2=16 minb=2 ms=63.2
+std::string format_entry(const TuneEntry& t) {
+    std::string chain;
+    for (int k = 0; k < t.cfg.n_levels; k++) chain += (k ? "," : "") + std::to_string(t.cfg.variant[k]);
+    char buf[256];
+    std::snprintf(buf, sizeof(buf), "alpha=%d xb=%d lb=%d chain=%s chunk=%d fused=%d every1=%d every2=%d minb=%d ms=%.4f",
+                  t.alpha, t.xb, t.lb, chain.c_str(), t.cfg.chunk, t.cfg.fused ? 1 : 0, t.cfg.every1,
+                  t.cfg.every2, t.cfg.fused_minb, double(t.ms));
+    return buf;
+}
+
+// Parses one entry over the defaults `base`; false (with a reason) on a malformed line.
+bool parse_entry(const std::string& line, const TierConfig& base, TuneEntry& out, std::string& why) {
+    out = TuneEntry{};
+    out.cfg = base;
+    bool have_chain = false;
+    size_t p = 0;
+    while (p < line.size()) {
+        while (p < line.size() && line[p] == ' ') p++;
+        size_t e = line.find(' ', p);
+        if (e == std::string::npos) e = line.size();
+        const std::string tok = line.substr(p, e - p);
+        p = e;
+        if (tok.empty()) continue;
+        const size_t eq = tok.find('=');
+        if (eq == std::string::npos) { why = "token without '=': " + tok; return false; }
+        const std::string k = tok.substr(0, eq), v = tok.substr(eq + 1);
+        if (k == "chain") {
+            out.cfg.n_levels = 0;
+            for (size_t q = 0; q < v.size();) {
+                if (out.cfg.n_levels >= kLevels - 2) { why = "chain too long"; return false; }
+                const int id = std::atoi(v.c_str() + q);
+                if (id < 0 || id >= kNumGroupVariants) { why = "unknown variant " + std::to_string(id); return false; }
+                out.cfg.variant[out.cfg.n_levels++] = id;
+                while (q < v.size() && v[q] != ',') q++;
+                if (q < v.size()) q++;
+            }
+            have_chain = out.cfg.n_levels > 0;
+        } else {
+            const int x = std::atoi(v.c_str());
+            if (k == "alpha") out.alpha = x;
+            else if (k == "xb") out.xb = x;
+            else if (k == "lb") out.lb = x;
+            else if (k == "chunk") out.cfg.chunk = std::max(1, std::min(x, 64));
+            else if (k == "fused") out.cfg.fused = x != 0;
+            else if (k == "every1") out.cfg.every1 = std::max(0, x);
+            else if (k == "every2") out.cfg.every2 = std::max(0, x);
+            else if (k == "minb") out.cfg.fused_minb = x;
+            else if (k == "ms") out.ms = float(std::atof(v.c_str()));
+        }
+    }
+    if (!have_chain) { why = "entry without chain"; return false; }
+    if (out.alpha != 4 && out.alpha != 20) { why = "alpha must be 4 or 20"; return false; }
+    if (out.xb < 0 || out.xb > 2 || out.lb < 0 || out.lb > 2) { why = "bucket out of range"; return false; }
+    if (out.alpha == 20)
+        for (int k = 0; k < out.cfg.n_levels; k++) {
+            const int v = out.cfg.variant[k];
+            if (!(v == kG1C16 || v == kG4C16 || v == kG8C16 || v == kG16C16 || v == kG32C16 || v == kG32C32)) {
+                why = "variant " + std::to_string(v) + " is not compiled for protein";
+                return false;
+            }
+        }
+    if (out.cfg.fused && !fused_supported(out.cfg, out.alpha)) out.cfg.fused = false;
+    return true;
+}
+
+xd_status load_table(xd_ctx* c, const char* path, std::vector<TuneEntry>& out) {
+    out.clear();
+    FILE* f = std::fopen(path, "r");
+    if (!f) return fail(c, XD_EINVAL, std::string("cannot open tuning table ") + path);
+    char buf[1024];
+    int ln = 0;
+    xd_status st = XD_OK;
+    while (std::fgets(buf, sizeof(buf), f)) {
+        ln++;
+        std::string line(buf);
+        while (!line.empty() && (line.back() == '\n' || line.back() == '\r')) line.pop_back();
+        if (line.empty() || line[0] == '#') continue;
+        TuneEntry t;
+        std::string why;
+        if (!parse_entry(line, c->tiers, t, why)) {
+            st = fail(c, XD_EINVAL, std::string(path) + ":" + std::to_string(ln) + ": " + why);
+            break;
+        }
+        out.push_back(t);
+    }
+    std::fclose(f);
+    return st;
+}
+
+void put_entry(std::vector<TuneEntry>& v, const TuneEntry& t) {
+    for (TuneEntry& e : v)
+        if (e.alpha == t.alpha && e.xb == t.xb && e.lb == t.lb) {
+            e = t;
+            return;
+        }
+    v.push_back(t);
+}
+
+// Lanes per side extension of a variant (the threads per alignment of its level).
+int tier_group_of(int v) {
+    switch (v) {
+        case kG1C16: case kG1C32: return 1;
+        case kG4C16: case kG4C32: return 4;
+        case kG8C16: case kG8C32: return 8;
+        case kG16C16: case kG16C32: return 16;
+        default: return 32;
+    }
+}
+
+// Candidate configurations of the autotuner, in stages: the register chain (lanes per side
+// and window of every level: the threads per alignment and band tile width), then the
+// queue chunk of single-lane levels, then the fused grid's role mix.
+std::vector<TierConfig> chain_candidates(const TierConfig& base, int alpha) {
+    std::vector<std::vector<int>> chains;
+    if (alpha == 4)
+        chains = {{kG1C32, kG16C16, kG32C16, kG32C32}, {kG1C16, kG4C16, kG16C16, kG32C32},
+                  {kG1C32, kG8C16, kG32C16, kG32C32}, {kG1C32, kG4C32, kG8C32, kG32C32},
+                  {kG4C16, kG16C16, kG32C32},         {kG1C16, kG8C16, kG32C16, kG32C32},
+                  {kG1C32, kG8C16, kG16C16, kG32C32}};
+    else
+        chains = {{kG4C16, kG16C16, kG32C32}, {kG1C16, kG4C16, kG16C16, kG32C32},
+                  {kG8C16, kG32C16, kG32C32}, {kG4C16, kG8C16, kG32C16, kG32C32}};
+    std::vector<TierConfig> out;
+    for (const auto& ch : chains)
+        for (int fused = 1; fused >= 0; fused--) {
+            TierConfig t = base;
+            t.n_levels = 0;
+            for (int v : ch) t.variant[t.n_levels++] = v;
+            t.fused = fused != 0;
+            if (t.fused && !fused_supported(t, alpha)) continue;
+            out.push_back(t);
+        }
+    return out;
+}
+
 }  // namespace
 
 extern "C" {
@@ -808,6 +975,15 @@ xd_status xd_create(const xd_config* cfg, xd_ctx** out) {
             delete c;
             return fail(nullptr, XD_EDEVICE, cudaGetErrorString(e));
         }
+    }
+    if (cfg && cfg->tune_table) {
+        std::vector<TuneEntry> t;
+        if (load_table(c, cfg->tune_table, t) != XD_OK) {
+            const std::string msg = c->err;
+            xd_destroy(c);
+            return fail(nullptr, XD_EINVAL, msg);
+        }
+        c->tuned = t;
     }
     c->dispatcher = std::thread(dispatch_loop, c);
     *out = c;
@@ -1035,6 +1211,149 @@ xd_status xd_probe(xd_ctx* c, int32_t op, double* rate) {
     XD_CUDA(c, cudaDeviceSynchronize());
     float ms = 0;
     XD_CUDA(c, probe_rate(op, c->n_sm, rate, &ms));
+    return XD_OK;
+}
+
+xd_status xd_autotune(xd_ctx* c, const xd_batch* b, const char* path, float* best_ms) {
+    if (!c || !b) return XD_EINVAL;
+    std::unique_lock<std::mutex> lk(c->mu);
+    XD_CUDA(c, cudaSetDevice(c->device));
+    BatchView v;
+    xd_status s = scoring_view(c, b, v);
+    if (s != XD_OK) return s;
+    uint32_t max_len = 0;
+    if ((s = validate_host(c, b, v, &max_len)) != XD_OK) return s;
+    if (b->n_pairs == 0) return fail(c, XD_EINVAL, "empty tuning sample");
+    for (uint64_t t = 0; t < b->n_codes; t++)
+        if (b->seq_codes[t] >= v.alpha) return fail(c, XD_EINVAL, "residue code outside the alphabet");
+    v.max_len = max_len;
+    // the sample on the device, with its own scratch and stream
+    const size_t o_offs = align_up(b->n_codes, 256);
+    const size_t o_lens = o_offs + align_up(8ull * b->n_seqs, 256);
+    const size_t o_pairs = o_lens + align_up(4ull * b->n_seqs, 256);
+    const size_t in_bytes = o_pairs + align_up(sizeof(xd_pair) * b->n_pairs, 256);
+    const size_t out_bytes = sizeof(xd_result) * size_t(b->n_pairs);
+    DevBuf d_in, d_out;
+    Scratch sc;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    std::vector<char> h(in_bytes);
+    std::vector<xd_result> ref(b->n_pairs), got(b->n_pairs);
+    std::memcpy(h.data(), b->seq_codes, b->n_codes);
+    std::memcpy(h.data() + o_offs, b->seq_offsets, 8ull * b->n_seqs);
+    std::memcpy(h.data() + o_lens, b->seq_lengths, 4ull * b->n_seqs);
+    std::memcpy(h.data() + o_pairs, b->pairs, sizeof(xd_pair) * b->n_pairs);
+    auto cleanup = [&]() {
+        c->force_tiers = nullptr;
+        if (st) cudaStreamSynchronize(st);
+        release(d_in);
+        release(d_out);
+        release(sc);
+        if (st) cudaStreamDestroy(st);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    auto cuda_bail = [&](cudaError_t e, const char* what) {
+        cleanup();
+        return cuda_fail(c, e, what);
+    };
+    cudaError_t e;
+    if ((e = grow(d_in, in_bytes)) != cudaSuccess || (e = grow(d_out, out_bytes)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(d_in.p, h.data(), in_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_bail(e, "autotune setup");
+    char* d = static_cast<char*>(d_in.p);
+    v.codes = reinterpret_cast<const uint8_t*>(d);
+    v.offsets = reinterpret_cast<const uint64_t*>(d + o_offs);
+    v.lengths = reinterpret_cast<const uint32_t*>(d + o_lens);
+    v.pairs = reinterpret_cast<const xd_pair*>(d + o_pairs);
+    auto* res = static_cast<xd_result*>(d_out.p);
+    const bool timing = c->timing;
+    c->timing = false;
+    bool have_ref = false;
+    // time one candidate: a warm-up run, then the best of two; results must not change
+    auto run = [&](const TierConfig& cand, float& ms) -> xd_status {
+        c->force_tiers = &cand;
+        ms = 1e30f;
+        for (int rep = 0; rep < 3; rep++) {
+            cudaError_t ee = cudaEventRecord(e0, st);
+            if (ee != cudaSuccess) return cuda_fail(c, ee, "cudaEventRecord");
+            xd_status ps = run_pipeline(c, sc, v, res, st, c->coop_done);
+            if (ps != XD_OK) return ps;
+            if ((ee = cudaEventRecord(e1, st)) != cudaSuccess || (ee = cudaEventSynchronize(e1)) != cudaSuccess)
+                return cuda_fail(c, ee, "autotune run");
+            float t = 0;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (rep > 0) ms = std::min(ms, t);
+        }
+        uint32_t flags = 0;
+        cudaError_t ee = cudaMemcpy(&flags, sc.err.p, 4, cudaMemcpyDeviceToHost);
+        if (ee == cudaSuccess)
+            ee = cudaMemcpy(have_ref ? got.data() : ref.data(), res, out_bytes, cudaMemcpyDeviceToHost);
+        if (ee != cudaSuccess) return cuda_fail(c, ee, "autotune copy");
+        if (flags) return fail(c, XD_EDEVICE, "device flags " + std::to_string(flags) + " while tuning");
+        if (have_ref && std::memcmp(got.data(), ref.data(), out_bytes) != 0)
+            return fail(c, XD_EDEVICE, "a tuning candidate changed the results");
+        have_ref = true;
+        return XD_OK;
+    };
+    const TierConfig base = tiers_for(c, v);
+    TuneEntry best;
+    best.alpha = v.alpha;
+    best.xb = x_bucket(v.X);
+    best.lb = len_bucket(v.max_len);
+    best.cfg = base;
+    best.ms = 1e30f;
+    auto consider = [&](const TierConfig& cand) -> xd_status {
+        float ms = 0;
+        xd_status r = run(cand, ms);
+        if (r == XD_OK && ms < best.ms) {
+            best.ms = ms;
+            best.cfg = cand;
+        }
+        return r;
+    };
+    xd_status r = consider(base);
+    for (const TierConfig& cand : chain_candidates(base, v.alpha))
+        if (r == XD_OK) r = consider(cand);
+    if (r == XD_OK && tier_group_of(best.cfg.variant[0]) == 1)
+        for (int ch : {2, 4, 8, 16, 32, 64}) {
+            TierConfig cand = best.cfg;
+            cand.chunk = ch;
+            if (r == XD_OK) r = consider(cand);
+        }
+    if (r == XD_OK && best.cfg.fused)
+        for (auto mix : {std::pair<int, int>{2, 8}, {8, 32}, {4, 8}, {8, 16}, {0, 16}, {4, 0}, {4, 32}}) {
+            TierConfig cand = best.cfg;
+            cand.every1 = mix.first;
+            cand.every2 = mix.second;
+            if (r == XD_OK) r = consider(cand);
+        }
+    c->timing = timing;
+    if (r != XD_OK) {
+        const std::string msg = c->err;
+        cleanup();
+        return fail(c, r, msg);
+    }
+    cleanup();
+    put_entry(c->tuned, best);
+    if (best_ms) *best_ms = best.ms;
+    if (path && *path) {
+        std::vector<TuneEntry> table;
+        if (FILE* f = std::fopen(path, "r")) {
+            std::fclose(f);
+            if (load_table(c, path, table) != XD_OK) return XD_EINVAL;
+        }
+        put_entry(table, best);
+        FILE* f = std::fopen(path, "w");
+        if (!f) return fail(c, XD_EINVAL, std::string("cannot write tuning table ") + path);
+        std::fprintf(f, "# xdrop-gb300 tuning table: alpha (4 DNA, 20 protein), X bucket (0: X <= 15, 1: <= 30,\n"
+                        "# 2: more), length bucket (0: longest side <= 2048, 1: <= 20000, 2: more), chain of\n"
+                        "# register-level variants, queue chunk, fused grid and its role mix, measured ms\n");
+        for (const TuneEntry& t : table) std::fprintf(f, "%s\n", format_entry(t).c_str());
+        std::fclose(f);
+    }
     return XD_OK;
 }
 

@@ -1,0 +1,790 @@
+// Register tiers of the X-Drop library: one templated group kernel.
+//
+// A side extension is owned by a group of G lanes (G = 1 .. 32); lane l of the group holds
+// slots [l*CG, (l+1)*CG) of a window of W = G*CG slots per anti-diagonal.  Slot s of
+// anti-diagonal d holds cell i = floor(d/2) + rb + s.  In these coordinates the diagonal
+// predecessor S(i-1, j-1) sits in the same slot two anti-diagonals back and the two gap
+// predecessors sit in slots (s-1, s) on odd d and (s, s+1) on even d, so a band that
+// follows the main diagonal does not move in the window; it drifts only with the indels of
+// the alignment.  The window is re-centred through shared memory when the band nears its
+// edge (one guard slot on each side holds the gap predecessors of the band's end cells).
+// A side whose band outgrows the window is appended to the next level's queue and
+// restarted there with a wider window.  The two anti-diagonals are the paper's
+// memory-restricted pair (Gotoh's two-diagonal scheme, Sec. 3): the new anti-diagonal
+// overwrites d-2 slot by slot.
+//
+// Per anti-diagonal (Sec. 3, Algorithm 1): band [first live, last live + 1] of d-1 clipped
+// to the matrix and, when restricted, to delta_b cells centred on d-1's best cell; per cell
+// the recurrence of Sec. 2.2 as max(S(i-1,j-1) + Sim, max(S(i-1,j), S(i,j-1)) + gap) with
+// the DPX add-max, the X-Drop test against T of the completed anti-diagonals; then group
+// reductions of the live range and of the best cell (lowest i on ties).
+//
+// Residues: each lane keeps slices of H and V for its slots (2-bit fields for DNA; for
+// protein, 16-bit table offsets, two slots per register).  On odd d the V slice gains one
+// residue, on even d the H slice does; residues come from two oriented streams per lane
+// whose next store word is always prefetched.
+//
+// This header holds the templates; xd_tiers.cu instantiates the DNA kernels (A = 4) and
+// xd_tiers_prot.cu the protein ones (A = 20).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "xd_device.cuh"
+#include "xd_launch.h"
+
+namespace xd {
+
+// Register levels keep scores in a narrower range so that a (score, slot) key fits 32 bits.
+constexpr int32_t kNegR = -(1 << 24);
+constexpr int32_t kDeadR = -(1 << 23);
+constexpr int64_t kRegLimit = int64_t(1) << 23;
+
+enum { kCont = 0, kDone = 1, kOverflow = 2 };
+
+__device__ __forceinline__ uint32_t ld_word(const uint32_t* store, uint64_t n_words, int64_t w) {
+    w = w < 0 ? 0 : w;
+    w = w >= int64_t(n_words) ? int64_t(n_words) - 1 : w;
+    return __ldg(store + w);
+}
+
+// 32 residues from position p: field f (bits 2f, 2f+1) = residue p + f, or p + 31 - f
+// when rev.  Positions outside the store read clamped words (only cells outside the band
+// ever use them).
+__device__ __forceinline__ uint64_t slice_at(const uint32_t* store, uint64_t nw, int64_t p, bool rev) {
+    const int64_t w = p >> 4;
+    const uint32_t sh = uint32_t(p & 15) * 2u;
+    const uint64_t lo = (uint64_t(ld_word(store, nw, w + 1)) << 32) | ld_word(store, nw, w);
+    const uint64_t hi = ld_word(store, nw, w + 2);
+    uint64_t x = sh ? (lo >> sh) | (hi << (64 - sh)) : lo;
+    if (rev) {
+        x = __brevll(x);
+        x = ((x >> 1) & 0x5555555555555555ull) | ((x & 0x5555555555555555ull) << 1);
+    }
+    return x;
+}
+
+// Oriented residue stream: next() returns store[p], store[p + dir], store[p + 2 dir], ...
+struct Stream {
+    int64_t word;      // index of cur
+    uint32_t cur, nxt; // current word and the following one (prefetched)
+    int32_t off;       // bit offset of the next residue in cur
+    int32_t dir;       // +1 or -1
+};
+
+__device__ __forceinline__ void stream_init(Stream& s, const uint32_t* store, uint64_t nw, int64_t p, int32_t dir) {
+    s.word = p >> 4;
+    s.off = int32_t(p & 15) * 2;
+    s.dir = dir;
+    s.cur = ld_word(store, nw, s.word);
+    s.nxt = ld_word(store, nw, s.word + dir);
+}
+
+__device__ __forceinline__ uint32_t stream_next(Stream& s, const uint32_t* store, uint64_t nw) {
+    const uint32_t c = (s.cur >> s.off) & 3u;
+    s.off += 2 * s.dir;
+    if (s.off < 0 || s.off > 30) {
+        s.word += s.dir;
+        s.cur = s.nxt;
+        s.nxt = ld_word(store, nw, s.word + s.dir);
+        s.off &= 31;
+    }
+    return c;
+}
+
+// Protein residue stream over the 5-bit store (six residues per word, residue k of a word
+// in bits 5k .. 5k+4).
+struct Stream5 {
+    int64_t word;
+    uint32_t cur, nxt;
+    int32_t off;
+    int32_t dir;
+};
+
+__device__ __forceinline__ void stream5_init(Stream5& s, const uint32_t* store, uint64_t nw, int64_t p, int32_t dir) {
+    const int64_t w = p >= 0 ? p / 6 : -((-p + 5) / 6);   // floor(p / 6)
+    s.word = w;
+    s.off = int32_t(p - 6 * w) * 5;
+    s.dir = dir;
+    s.cur = ld_word(store, nw, w);
+    s.nxt = ld_word(store, nw, w + dir);
+}
+
+__device__ __forceinline__ uint32_t stream5_next(Stream5& s, const uint32_t* store, uint64_t nw) {
+    const uint32_t c = (s.cur >> s.off) & 31u;
+    s.off += 5 * s.dir;
+    if (s.off < 0 || s.off > 25) {
+        s.word += s.dir;
+        s.cur = s.nxt;
+        s.nxt = ld_word(store, nw, s.word + s.dir);
+        s.off = s.dir > 0 ? 0 : 25;
+    }
+    return c;
+}
+
+// Per-side state, replicated across the lanes of a group (the residue slices live in Res).
+struct SideState {
+    int64_t h0, v0;
+    uint64_t cells;
+    int32_t m, n, d, rb, dir;
+    int32_t L, U, T, best, bi, bj, barg;
+    uint32_t flags, side;
+    bool refresh;
+};
+
+__device__ __forceinline__ void init_side(SideState& s, const Unit& u, int32_t rb) {
+    s.h0 = int64_t(u.h0);
+    s.v0 = int64_t(u.v0);
+    s.m = int32_t(u.m);
+    s.n = int32_t(u.n);
+    s.side = u.side;
+    s.dir = u.side ? -1 : 1;
+    s.rb = rb;
+    s.d = 1;
+    s.L = s.U = 0;
+    s.T = s.best = s.bi = s.bj = s.barg = 0;
+    s.flags = 0;
+    s.cells = 1;
+    s.refresh = true;
+}
+
+// Residue slices of a lane's CG slots: slot t pairs H_side[hb + t] with V_side[vb - t],
+// where H_side[k] = store[h0 + dir k] (likewise V).
+template <int CG, int A>
+struct Res;
+
+// DNA: 2-bit fields of one 64-bit word per sequence.
+template <int CG>
+struct Res<CG, 4> {
+    uint64_t hs, vs;
+    Stream sh, sv;              // next residue entering the H / V slice
+
+    __device__ __forceinline__ void load(const Problem& P, const SideState& s, int64_t hb, int64_t vb) {
+        hs = s.dir > 0 ? slice_at(P.store, P.n_words, s.h0 + hb, false)
+                       : slice_at(P.store, P.n_words, s.h0 - hb - 31, true);
+        if constexpr (CG < 32) hs &= (1ull << (2 * CG)) - 1ull;   // fields >= CG stay zero while shifting
+        vs = s.dir > 0 ? slice_at(P.store, P.n_words, s.v0 + vb - 31, true)
+                       : slice_at(P.store, P.n_words, s.v0 - vb, false);
+        stream_init(sh, P.store, P.n_words, s.h0 + s.dir * (hb + CG), s.dir);
+        stream_init(sv, P.store, P.n_words, s.v0 + s.dir * (vb + 1), s.dir);
+    }
+    __device__ __forceinline__ void push_h(const Problem& P) {
+        const uint64_t c = stream_next(sh, P.store, P.n_words);
+        hs = (hs >> 2) | (c << (2 * (CG - 1)));
+    }
+    __device__ __forceinline__ void push_v(const Problem& P) {
+        const uint64_t c = stream_next(sv, P.store, P.n_words);
+        vs = (vs << 2) | c;
+    }
+};
+
+// Protein: byte offsets into the 20 x 20 int32 similarity table in shared memory, H codes
+// scaled by 80 and V codes by 4, two slots per register (slot 2k in the low half).  The
+// sum of an H and a V register is the table offset of both slots' cells at once (no carry
+// crosses the halves: 31 * 80 + 31 * 4 < 2^16).
+template <int CG>
+struct Res<CG, 20> {
+    uint32_t hx[CG / 2], vx[CG / 2];
+    Stream5 sh, sv;
+
+    __device__ __forceinline__ void load(const Problem& P, const SideState& s, int64_t hb, int64_t vb) {
+        Stream5 t;
+        stream5_init(t, P.store, P.n_words, s.h0 + s.dir * hb, s.dir);
+#pragma unroll
+        for (int k = 0; k < CG / 2; k++) {
+            const uint32_t lo = stream5_next(t, P.store, P.n_words) * 80u;
+            const uint32_t hi = stream5_next(t, P.store, P.n_words) * 80u;
+            hx[k] = lo | (hi << 16);
+        }
+        // V_side[vb - CG + 1 .. vb] in side order fills the slots from CG - 1 down to 0
+        stream5_init(t, P.store, P.n_words, s.v0 + s.dir * (vb - CG + 1), s.dir);
+#pragma unroll
+        for (int k = CG / 2 - 1; k >= 0; k--) {
+            const uint32_t hi = stream5_next(t, P.store, P.n_words) * 4u;
+            const uint32_t lo = stream5_next(t, P.store, P.n_words) * 4u;
+            vx[k] = lo | (hi << 16);
+        }
+        stream5_init(sh, P.store, P.n_words, s.h0 + s.dir * (hb + CG), s.dir);
+        stream5_init(sv, P.store, P.n_words, s.v0 + s.dir * (vb + 1), s.dir);
+    }
+    __device__ __forceinline__ void push_h(const Problem& P) {
+        const uint32_t c = stream5_next(sh, P.store, P.n_words) * 80u;
+#pragma unroll
+        for (int k = 0; k < CG / 2 - 1; k++) hx[k] = __funnelshift_r(hx[k], hx[k + 1], 16);
+        hx[CG / 2 - 1] = (hx[CG / 2 - 1] >> 16) | (c << 16);
+    }
+    __device__ __forceinline__ void push_v(const Problem& P) {
+        const uint32_t c = stream5_next(sv, P.store, P.n_words) * 4u;
+#pragma unroll
+        for (int k = CG / 2 - 1; k > 0; k--) vx[k] = __funnelshift_l(vx[k - 1], vx[k], 16);
+        vx[0] = (vx[0] << 16) | c;
+    }
+};
+
+template <int CG, bool ODD, int A>
+__device__ __forceinline__ void update_slices(SideState& s, Res<CG, A>& r, const Problem& P, int64_t hb,
+                                              int64_t vb) {
+    if (s.refresh) {
+        r.load(P, s, hb, vb);
+        s.refresh = false;
+    } else if (!ODD) {
+        r.push_h(P);
+    } else {
+        r.push_v(P);
+    }
+}
+
+// Band [lo, hi] of anti-diagonal d: [first live, last live + 1] of d-1 clipped to the
+// matrix, then to delta_b cells centred on d-1's best cell when restricted.
+__device__ __forceinline__ void band_of(SideState& s, const Problem& P, int32_t d, int32_t& lo, int32_t& hi) {
+    lo = max(max(s.L, d - s.n), 0);
+    hi = min(min(s.U + 1, s.m), d);
+    if (P.delta && hi - lo + 1 > int32_t(P.delta)) {
+        s.flags |= 1u;
+        const int32_t start = min(s.barg - int32_t(P.delta >> 1), hi - int32_t(P.delta) + 1);
+        lo = max(lo, start);
+        hi = lo + int32_t(P.delta) - 1;
+    }
+}
+
+// The lane's CG cells.  P1 holds d-1, P2 holds d-2 and receives d.  upb / lfb are the
+// neighbours beyond the lane's first / last slot.  tab is the block's similarity table:
+// for DNA 256 int4 entries indexed by one byte of the xor of the residue slices (four
+// 2-bit fields, zero = match), giving four cells' Sim per load; for protein the 20 x 20
+// int32 matrix addressed by the slices' summed byte offsets.  Returns the lane's live mask
+// and the maximum key v * 64 + (63 - t) over its cells (dead cells hold kNegR).
+template <int CG, bool ODD, int A>
+__device__ __forceinline__ void cells_of(int32_t (&P1)[CG], int32_t (&P2)[CG], int32_t upb,
+                                         int32_t lfb, const Res<CG, A>& res, uint32_t bm, int32_t thr,
+                                         int32_t gap, const int32_t* tab, int32_t& kmax,
+                                         uint32_t& lm) {
+    static_assert(CG % 4 == 0, "cells come in groups of four");
+    kmax = INT32_MIN;
+    lm = 0;
+#pragma unroll
+    for (int q = 0; q < CG / 4; q++) {
+        int32_t sg[4];
+        if constexpr (A == 4) {
+            const uint64_t x = res.hs ^ res.vs;
+            const int4 s4 = reinterpret_cast<const int4*>(tab)[uint32_t(x >> (8 * q)) & 0xffu];
+            sg[0] = s4.x;
+            sg[1] = s4.y;
+            sg[2] = s4.z;
+            sg[3] = s4.w;
+        } else {
+            const char* tb = reinterpret_cast<const char*>(tab);
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const uint32_t ix = res.hx[2 * q + h] + res.vx[2 * q + h];
+                sg[2 * h] = *reinterpret_cast<const int32_t*>(tb + (ix & 0xffffu));
+                sg[2 * h + 1] = *reinterpret_cast<const int32_t*>(tb + (ix >> 16));
+            }
+        }
+        int32_t key[4];
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            const int t = 4 * q + r;
+            const int32_t up = ODD ? (t > 0 ? P1[t - 1] : upb) : P1[t];
+            const int32_t lf = ODD ? P1[t] : (t < CG - 1 ? P1[t + 1] : lfb);
+            const int32_t raw = __viaddmax_s32(max(up, lf), gap, P2[t] + sg[r]);
+            const bool live = raw >= thr && ((bm >> t) & 1u);
+            const int32_t v = live ? raw : kNegR;
+            P2[t] = v;
+            lm |= live ? (1u << t) : 0u;
+            key[r] = v * 64 + (63 - t);
+        }
+        kmax = __vimax3_s32(kmax, key[0], key[1]);
+        kmax = __vimax3_s32(kmax, key[2], key[3]);
+    }
+}
+
+// The block's similarity table at the start of its shared memory.  DNA: entry e holds Sim of
+// the four fields (e >> 2f) & 3, f = 0..3 (zero = match).  Protein: Sim row-major, H code
+// major.  Entries past the 20 x 20 matrix are zero (offsets of codes >= 20 land there; only
+// cells outside the band can carry such codes).
+template <int A>
+__device__ __forceinline__ void build_table(int32_t* tab, const Problem& P) {
+    if constexpr (A == 4) {
+        const int32_t mat = P.sim[0], mis = P.sim[1];
+        for (int e = threadIdx.x; e < 256; e += blockDim.x) {
+            int4 v;
+            v.x = (e & 3) ? mis : mat;
+            v.y = ((e >> 2) & 3) ? mis : mat;
+            v.z = ((e >> 4) & 3) ? mis : mat;
+            v.w = ((e >> 6) & 3) ? mis : mat;
+            reinterpret_cast<int4*>(tab)[e] = v;
+        }
+    } else {
+        for (int e = threadIdx.x; e < 1024; e += blockDim.x) tab[e] = e < 400 ? int32_t(P.sim[e]) : 0;
+    }
+    __syncthreads();
+}
+constexpr int kLutInts = 1024;
+
+template <int G>
+__device__ __forceinline__ int32_t gmax(int32_t v, uint32_t gm) {
+    if constexpr (G == 32) {
+        return __reduce_max_sync(0xffffffffu, v);
+    } else {
+#pragma unroll
+        for (int k = G / 2; k >= 1; k >>= 1) v = max(v, __shfl_xor_sync(gm, v, k));
+        return v;
+    }
+}
+
+template <int G>
+__device__ __forceinline__ int32_t gmin(int32_t v, uint32_t gm) {
+    if constexpr (G == 32) {
+        return __reduce_min_sync(0xffffffffu, v);
+    } else {
+#pragma unroll
+        for (int k = G / 2; k >= 1; k >>= 1) v = min(v, __shfl_xor_sync(gm, v, k));
+        return v;
+    }
+}
+
+__device__ __forceinline__ uint32_t slot_mask(int32_t from, int32_t to, int cw) {
+    const int32_t a = max(from, 0), b = min(to + 1, cw);
+    if (a >= b) return 0u;
+    return uint32_t(((1ull << b) - 1ull) & ~((1ull << a) - 1ull));
+}
+
+// One anti-diagonal of the group's side extension.
+template <int G, int CG, bool ODD, int A>
+__device__ __forceinline__ int group_step(SideState& s, Res<CG, A>& res, int32_t (&P1)[CG], int32_t (&P2)[CG],
+                                          const Problem& P, const int32_t* tab, int gl,
+                                          uint32_t gm, int32_t* gsm) {
+    constexpr int W = G * CG;
+    const int32_t d = s.d;
+    int32_t ib = (d >> 1) + s.rb;
+    int32_t lo, hi;
+    band_of(s, P, d, lo, hi);
+    int32_t slo = lo - ib, shi = hi - ib;
+    if (slo < 1 || shi > W - 2) {
+        const int32_t w = hi - lo + 1;
+        if (w > W - 2) return kOverflow;
+        const int32_t k = slo - (1 + (W - 2 - w) / 2);
+        // re-centre: every lane parks its slots in the group's shared row and reads back
+        // the slots k positions further
+#pragma unroll
+        for (int t = 0; t < CG; t++) {
+            gsm[gl * CG + t] = P1[t];
+            gsm[W + gl * CG + t] = P2[t];
+        }
+        if (G > 1) __syncwarp(gm);
+#pragma unroll
+        for (int t = 0; t < CG; t++) {
+            const int src = gl * CG + t + k;
+            const bool in = src >= 0 && src < W;
+            P1[t] = in ? gsm[src] : kNegR;
+            P2[t] = in ? gsm[W + src] : kNegR;
+        }
+        if (G > 1) __syncwarp(gm);
+        s.rb += k;
+        ib += k;
+        slo -= k;
+        shi -= k;
+        s.refresh = true;
+        if (gl == 0) atomicAdd(&P.stats[8], 1ull);
+    }
+    const int32_t sb = gl * CG;
+    update_slices<CG, ODD, A>(s, res, P, int64_t(ib) - 1 + sb, int64_t(d) - ib - 1 - sb);
+    const uint32_t bm = slot_mask(slo - sb, shi - sb, CG);
+    const int32_t thr = max(s.T - P.X, kDeadR);
+    int32_t upb = kNegR, lfb = kNegR;
+    if (G > 1) {
+        if (ODD) {
+            upb = __shfl_up_sync(gm, P1[CG - 1], 1, G);
+            if (gl == 0) upb = kNegR;
+        } else {
+            lfb = __shfl_down_sync(gm, P1[0], 1, G);
+            if (gl == G - 1) lfb = kNegR;
+        }
+    }
+    int32_t kmax;
+    uint32_t lm;
+    cells_of<CG, ODD, A>(P1, P2, upb, lfb, res, bm, thr, P.gap, tab, kmax, lm);
+    s.cells += uint64_t(hi - lo + 1);
+    const bool any = lm != 0;
+    int32_t first = any ? sb + __ffs(lm) - 1 : INT32_MAX;
+    int32_t last = any ? sb + 31 - __clz(lm) : -1;
+    first = gmin<G>(first, gm);
+    if (first == INT32_MAX) return kDone;
+    last = gmax<G>(last, gm);
+    s.L = ib + first;
+    s.U = ib + last;
+    const int32_t lv = kmax >> 6;
+    const int32_t wmax = gmax<G>(lv, gm);
+    const int32_t arg = ib + gmin<G>(lv == wmax ? sb + (63 - (kmax & 63)) : INT32_MAX, gm);
+    if (wmax > s.T) {
+        s.T = wmax;
+        s.best = wmax;
+        s.bi = arg;
+        s.bj = d - arg;
+    }
+    s.barg = arg;
+    s.d = d + 1;
+    return d == s.m + s.n ? kDone : kCont;
+}
+
+// Where a group takes its next side extension from.  A static source is a finished list
+// (the cost-ordered units, or a queue filled by an earlier launch).  A live source is a
+// queue that producers of the same launch may still append to: slots are reserved with an
+// atomic counter and published by storing the unit index over the kNoUnit sentinel.
+constexpr uint32_t kNoUnit = 0xffffffffu;
+constexpr uint32_t kMaxSpin = 1u << 24;
+
+struct Source {
+    const uint32_t* list;
+    uint32_t* pull;             // pull counter
+    uint32_t n;                 // length of a static source
+    bool live;
+    uint32_t* reserve;          // live: length counter
+    uint32_t* producers_done;   // live: producer warps that have finished
+    uint32_t n_producers;
+};
+
+// Next unit for the group (group-uniform result).  Returns false when the source is
+// exhausted.  Waits on a live source are bounded; a wait that gives up raises kErrWait.
+template <int G>
+__device__ __forceinline__ bool next_unit(const Source& S, int gl, int lane, uint32_t gm, int chunk,
+                                          uint32_t& next, uint32_t& end, uint32_t& uidx, uint32_t* err) {
+    if (!S.live) {
+        if (next >= end) {
+            uint32_t base = 0;
+            const uint32_t take = G == 1 ? uint32_t(chunk) : 1u;
+            if (gl == 0) base = atomicAdd(S.pull, take);
+            if (G > 1) base = __shfl_sync(gm, base, lane - gl);
+            if (base >= S.n) return false;
+            next = base;
+            end = min(base + take, S.n);
+        }
+        uidx = S.list[next++];
+        return true;
+    }
+    uint32_t u = kNoUnit;
+    int got = 0;
+    if (gl == 0) {
+        const uint32_t ticket = atomicAdd(S.pull, 1u);
+        for (uint32_t it = 0;; it++) {
+            if (ticket < atomicAdd(S.reserve, 0u)) {
+                const volatile uint32_t* slot = S.list + ticket;
+                uint32_t v = *slot;
+                for (uint32_t w = 0; v == kNoUnit && w < kMaxSpin; w++) {
+                    __nanosleep(64);
+                    v = *slot;
+                }
+                if (v == kNoUnit) atomicOr(err, kErrWait);
+                else { u = v; got = 1; }
+                break;
+            }
+            if (atomicAdd(S.producers_done, 0u) >= S.n_producers) {
+                __threadfence();
+                if (ticket < atomicAdd(S.reserve, 0u)) continue;   // a final push landed meanwhile
+                break;
+            }
+            if (it >= kMaxSpin) {
+                atomicOr(err, kErrWait);
+                break;
+            }
+            __nanosleep(256);
+        }
+    }
+    if (G > 1) {
+        got = __shfl_sync(gm, got, lane - gl);
+        u = __shfl_sync(gm, u, lane - gl);
+    }
+    uidx = u;
+    return got != 0;
+}
+
+// Record layout: 16 header ints (window, d, rb, L, U, T, best, bi, bj, barg, flags,
+// cells lo/hi), then the window's anti-diagonal d-1 and d-2 in slot order.  Records are
+// bump-allocated from one int pool; rec_of holds a record's offset in the pool.
+constexpr int kRecHeader = 16;
+
+template <int G, int CG>
+__device__ __forceinline__ void save_record(const Problem& P, uint32_t ri, const SideState& s,
+                                            const int32_t (&P1)[CG], const int32_t (&P2)[CG], int gl) {
+    constexpr int W = G * CG;
+    int32_t* r = P.rec + ri;
+#pragma unroll
+    for (int t = 0; t < CG; t++) {
+        __stcg(r + kRecHeader + gl * CG + t, P1[t]);
+        __stcg(r + kRecHeader + W + gl * CG + t, P2[t]);
+    }
+    if (gl == 0) {
+        __stcg(r + 0, W);
+        __stcg(r + 1, s.d);
+        __stcg(r + 2, s.rb);
+        __stcg(r + 3, s.L);
+        __stcg(r + 4, s.U);
+        __stcg(r + 5, s.T);
+        __stcg(r + 6, s.best);
+        __stcg(r + 7, s.bi);
+        __stcg(r + 8, s.bj);
+        __stcg(r + 9, s.barg);
+        __stcg(r + 10, int32_t(s.flags));
+        __stcg(r + 11, int32_t(uint32_t(s.cells)));
+        __stcg(r + 12, int32_t(uint32_t(s.cells >> 32)));
+    }
+}
+
+// Continues a side from its record in a window of W >= the record's window (placed in the
+// middle).  Returns false if the record does not fit (the side then starts from scratch).
+template <int G, int CG>
+__device__ __forceinline__ bool load_record(const Problem& P, uint32_t ri, SideState& s, int32_t (&A)[CG],
+                                            int32_t (&B)[CG], int gl) {
+    constexpr int W = G * CG;
+    const int32_t* r = P.rec + ri;
+    const int32_t w0 = __ldcg(r + 0);
+    if (w0 > W) return false;
+    const int32_t off = (W - w0) / 2;
+    s.d = __ldcg(r + 1);
+    s.rb = __ldcg(r + 2) - off;
+    s.L = __ldcg(r + 3);
+    s.U = __ldcg(r + 4);
+    s.T = __ldcg(r + 5);
+    s.best = __ldcg(r + 6);
+    s.bi = __ldcg(r + 7);
+    s.bj = __ldcg(r + 8);
+    s.barg = __ldcg(r + 9);
+    s.flags = uint32_t(__ldcg(r + 10));
+    s.cells = uint64_t(uint32_t(__ldcg(r + 11))) | (uint64_t(uint32_t(__ldcg(r + 12))) << 32);
+    const bool odd = s.d & 1;   // odd d: A holds d-1; even d: B holds d-1
+#pragma unroll
+    for (int t = 0; t < CG; t++) {
+        const int src = gl * CG + t - off;
+        const bool in = src >= 0 && src < w0;
+        const int32_t v1 = in ? __ldcg(r + kRecHeader + src) : kNegR;
+        const int32_t v2 = in ? __ldcg(r + kRecHeader + w0 + src) : kNegR;
+        A[t] = odd ? v1 : v2;
+        B[t] = odd ? v2 : v1;
+    }
+    return true;
+}
+
+// Runs side extensions from S with groups of G lanes until S is exhausted; overflows go to
+// q[out_q], carrying an escalation record when the next level is a register level.
+// gsm_block: the block's shared rows (2W ints per group).
+template <int G, int CG, int A>
+__device__ __forceinline__ void group_loop(const Problem& P, const Queues& Q, const Source& S, int out_q,
+                                           int chunk, int32_t* smem) {
+    constexpr int W = G * CG;
+    const int lane = threadIdx.x & 31;
+    const int gl = lane % G;
+    const uint32_t gm = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane - gl));
+    const int32_t* tab = smem;
+    int32_t* gsm = smem + kLutInts + (threadIdx.x / G) * 2 * W;
+    int32_t R0[CG], R1[CG];
+    SideState s{};
+    Res<CG, A> res;
+    uint32_t uidx = 0, pair = 0, next = 0, end = 0;
+    bool active = false, skip_odd = false;
+    for (;;) {
+        if (!active) {
+            bool got = false;
+            while (next_unit<G>(S, gl, lane, gm, chunk, next, end, uidx, P.err)) {
+                const Unit u = P.units[uidx];
+                if ((int64_t(u.m) + u.n) * P.max_abs >= kRegLimit || P.alpha != A) {
+                    if (gl == 0) push_unit(Q, kBandQ, uidx);
+                    continue;
+                }
+                init_side(s, u, -W / 2);
+                pair = u.pair;
+                got = true;
+                break;
+            }
+            if (!got) break;
+            if (s.m + s.n == 0) {
+                if (gl == 0) {
+                    write_side(P.results, pair, s.side, 0, 0, 0, 0, 1);
+                    atomicAdd(&P.stats[0], 1ull);
+                    atomicAdd(&P.stats[4], 1ull);
+                }
+                continue;
+            }
+            const uint32_t ri = P.rec_of ? __ldcg(P.rec_of + uidx) : kNoUnit;
+            if (ri == kNoUnit || !load_record<G, CG>(P, ri, s, R0, R1, gl)) {
+                // S(0,0) = 0 in the middle of the window, every other cell -inf (Sec. 2.2)
+#pragma unroll
+                for (int t = 0; t < CG; t++) {
+                    R0[t] = kNegR;
+                    R1[t] = kNegR;
+                }
+                if (gl == (W / 2) / CG) R0[(W / 2) % CG] = 0;
+            }
+            skip_odd = (s.d & 1) == 0;   // a side continued on an even anti-diagonal
+            active = true;
+        }
+        int r = kCont;
+        if (!skip_odd) r = group_step<G, CG, true, A>(s, res, R0, R1, P, tab, gl, gm, gsm);
+        skip_odd = false;
+        if (r == kCont) r = group_step<G, CG, false, A>(s, res, R1, R0, P, tab, gl, gm, gsm);
+        if (r == kCont) continue;
+        active = false;
+        if (r == kDone) {
+            if (gl == 0) {
+                write_side(P.results, pair, s.side, s.best, uint32_t(s.bi), uint32_t(s.bj), s.flags, s.cells);
+                const int tier = W <= 32 ? 0 : 1;
+                atomicAdd(&P.stats[tier], 1ull);
+                atomicAdd(&P.stats[4 + tier], (unsigned long long)s.cells);
+            }
+            continue;
+        }
+        // overflow: hand the side to the next level, with its state when that level can take it
+        uint32_t ri = kNoUnit;
+        if (out_q <= kBandQ && P.rec) {
+            // bump-allocate kRecHeader + 2W ints of the record pool
+            const uint32_t need = uint32_t(kRecHeader + 2 * W);
+            if (gl == 0) ri = atomicAdd(P.rec_ctr, need);
+            if (G > 1) ri = __shfl_sync(gm, ri, lane - gl);
+            if (ri <= P.rec_cap && P.rec_cap - ri >= need) {
+                if (s.d & 1) save_record<G, CG>(P, ri, s, R0, R1, gl);
+                else save_record<G, CG>(P, ri, s, R1, R0, gl);
+                if (G > 1) __syncwarp(gm);
+            } else {
+                ri = kNoUnit;
+            }
+        }
+        if (gl == 0) {
+            if (ri != kNoUnit) {
+                __threadfence();
+                __stcg(P.rec_of + uidx, ri);
+                __threadfence();
+            } else {
+                atomicAdd(&P.stats[7], (unsigned long long)s.cells);
+            }
+            push_unit(Q, out_q, uidx);
+            atomicAdd(&P.stats[3], 1ull);
+        }
+    }
+}
+
+__device__ __forceinline__ Source static_source(const Queues& Q, int in_q) {
+    Source S{};
+    S.list = in_q < 0 ? Q.order : Q.q[in_q];
+    S.pull = in_q < 0 ? &Q.ctr[0] : &Q.ctr[2 + 2 * in_q];
+    S.n = in_q < 0 ? Q.n_units : *reinterpret_cast<volatile uint32_t*>(&Q.ctr[1 + 2 * in_q]);
+    S.live = false;
+    return S;
+}
+
+// One register level over a finished list.  in_q < 0: the cost-ordered units, else q[in_q].
+template <int G, int CG, int MINB, int A>
+__global__ void __launch_bounds__(128, MINB) k_group(Problem P, Queues Q, int in_q, int out_q, int chunk) {
+    extern __shared__ __align__(16) int32_t group_smem[];
+    build_table<A>(group_smem, P);
+    group_loop<G, CG, A>(P, Q, static_source(Q, in_q), out_q, chunk, group_smem);
+}
+
+// The first register levels fused into one persistent, cooperatively launched grid.
+// Each warp walks the role sequence 0 -> 1 -> 2: role 0 runs the cost-ordered units with
+// groups of G0 lanes and appends overflows to the live queue q[0]; role 1 consumes q[0]
+// with groups of G1 lanes and appends its overflows to the live queue q[1]; role 2
+// consumes q[1] with groups of G2 lanes, overflows go to q[2] for the later launches.
+// Some warps start directly in role 1 or 2, so wider sides begin while narrower levels
+// still run.  A warp that leaves role 0 (1) counts itself in done[0] (done[1]); consumers
+// stop once their queue is drained and all its producers have counted themselves.
+struct RolePlan {
+    int every1, every2;         // warp gw starts in role 2 if gw % every2 == every2 - 1,
+                                // else in role 1 if gw % every1 == 0, else in role 0
+    uint32_t producers0;        // warps that start in role 0
+    uint32_t producers1;        // warps that start in role 0 or 1
+};
+
+__host__ __device__ __forceinline__ int start_role(uint32_t gw, int every1, int every2) {
+    if (every2 > 0 && gw % uint32_t(every2) == uint32_t(every2 - 1)) return 2;
+    if (every1 > 0 && gw % uint32_t(every1) == 0) return 1;
+    return 0;
+}
+
+__device__ __forceinline__ Source live_source(const Queues& Q, int k, uint32_t* done, uint32_t producers) {
+    Source S{};
+    S.list = Q.q[k];
+    S.pull = &Q.ctr[2 + 2 * k];
+    S.live = true;
+    S.reserve = &Q.ctr[1 + 2 * k];
+    S.producers_done = done;
+    S.n_producers = producers;
+    return S;
+}
+
+__device__ __forceinline__ void signal_done(uint32_t* done) {
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) {
+        __threadfence();
+        atomicAdd(done, 1u);
+    }
+    __syncwarp();
+}
+
+template <int G0, int C0, int G1, int C1, int G2, int C2, int MINB, int A>
+__global__ void __launch_bounds__(128, MINB) k_fused(Problem P, Queues Q, RolePlan R, int chunk) {
+    extern __shared__ __align__(16) int32_t group_smem[];
+    build_table<A>(group_smem, P);
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    uint32_t* done0 = &Q.ctr[1 + 2 * kLevels];
+    uint32_t* done1 = &Q.ctr[2 + 2 * kLevels];
+    const int role = start_role(gw, R.every1, R.every2);
+    if (role == 0) {
+        group_loop<G0, C0, A>(P, Q, static_source(Q, -1), 0, chunk, group_smem);
+        signal_done(done0);
+    }
+    if (role <= 1) {
+        group_loop<G1, C1, A>(P, Q, live_source(Q, 0, done0, R.producers0), 1, 1, group_smem);
+        signal_done(done1);
+    }
+    group_loop<G2, C2, A>(P, Q, live_source(Q, 1, done1, R.producers1), 2, 1, group_smem);
+}
+
+template <int G, int CG, int MINB, int A>
+static cudaError_t launch_group(const Problem& P, const Queues& Q, int in_q, int out_q, int blocks,
+                                int chunk, cudaStream_t st) {
+    const size_t smem = (size_t(kLutInts) + size_t(128 / G) * 2 * G * CG) * sizeof(int32_t);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_group<G, CG, MINB, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_group<G, CG, MINB, A><<<blocks, 128, smem, st>>>(P, Q, in_q, out_q, chunk);
+    return cudaGetLastError();
+}
+
+template <int G, int CG>
+constexpr size_t group_smem_bytes() {
+    return (size_t(kLutInts) + size_t(128 / G) * 2 * G * CG) * sizeof(int32_t);
+}
+
+template <int G0, int C0, int G1, int C1, int G2, int C2, int MINB, int A>
+static cudaError_t launch_fused(const Problem& P, const Queues& Q, const TierConfig& cfg, int n_sm,
+                                cudaStream_t st) {
+    size_t smem = group_smem_bytes<G0, C0>();
+    if (group_smem_bytes<G1, C1>() > smem) smem = group_smem_bytes<G1, C1>();
+    if (group_smem_bytes<G2, C2>() > smem) smem = group_smem_bytes<G2, C2>();
+    auto fn = k_fused<G0, C0, G1, C1, G2, C2, MINB, A>;
+    static int occ = 0;
+    if (occ == 0) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 128, smem);
+        if (e != cudaSuccess) return e;
+        if (occ < 1) return cudaErrorInvalidConfiguration;
+    }
+    // every block must be resident at once: consumers wait for producers of the same grid
+    const int blocks = n_sm * occ;
+    const uint32_t n_warps = uint32_t(blocks) * 4;
+    RolePlan R{cfg.every1, cfg.every2, 0, 0};
+    for (uint32_t w = 0; w < n_warps; w++) {
+        const int r = start_role(w, R.every1, R.every2);
+        R.producers0 += r == 0;
+        R.producers1 += r <= 1;
+    }
+    Problem p = P;
+    Queues q = Q;
+    int ch = cfg.chunk;
+    void* args[] = {&p, &q, &R, &ch};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(fn), dim3(blocks), dim3(128), args, smem, st);
+}
+
+}  // namespace xd

@@ -53,10 +53,17 @@ int variant_window(int variant);
 
 // Levels 0-2 fused into one cooperatively launched persistent grid (consumers of the
 // escalation queues start while the narrower levels still run).  Only some variant
-// triples are compiled.
-bool fused_supported(const TierConfig& cfg);
+// triples are compiled (per alphabet: 4 = DNA, 20 = protein).
+bool fused_supported(const TierConfig& cfg, int alpha);
 cudaError_t launch_fused_levels(const Problem& P, const Queues& Q, const TierConfig& cfg, int n_sm,
                                 cudaStream_t st);
+
+// Protein instantiations (xd_tiers_prot.cu), reached through the two launchers above.
+cudaError_t launch_level_prot(const Problem& P, const Queues& Q, int variant, int in_q, int out_q,
+                              int blocks, int chunk, cudaStream_t st);
+bool fused_supported_prot(int a, int b, int d);
+cudaError_t launch_fused_levels_prot(const Problem& P, const Queues& Q, const TierConfig& cfg, int n_sm,
+                                     cudaStream_t st);
 
 // Throughput probes (xd_roof.cu).
 cudaError_t probe_rate(int op, int n_sm, double* rate, float* ms);

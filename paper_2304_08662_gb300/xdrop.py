@@ -81,12 +81,13 @@ def lib():
         L.xd_get_timing.argtypes = [P, ctypes.POINTER(xd_timing)]
         L.xd_probe.argtypes = [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
         L.xd_run_device_noalloc.argtypes = [ctypes.POINTER(xd_batch), ctypes.c_uint32, V, V]
+        L.xd_autotune.argtypes = [P, ctypes.POINTER(xd_batch), ctypes.c_char_p, ctypes.POINTER(ctypes.c_float)]
         L.xd_destroy.argtypes = [P]
         L.xd_last_error.argtypes = [P]
         L.xd_last_error.restype = ctypes.c_char_p
         L.xd_version.restype = ctypes.c_char_p
         for name in ("xd_create", "xd_submit_batch", "xd_poll", "xd_run_device", "xd_reserve",
-                     "xd_device_status", "xd_get_stats", "xd_destroy", "xd_set_timing", "xd_get_timing", "xd_probe", "xd_run_device_noalloc"):
+                     "xd_device_status", "xd_get_stats", "xd_destroy", "xd_set_timing", "xd_get_timing", "xd_probe", "xd_run_device_noalloc", "xd_autotune"):
             getattr(L, name).restype = ctypes.c_int
         _LIB = L
     return _LIB
@@ -235,6 +236,16 @@ def xd_probe(ctx, op):
     if rc != XD_OK:
         raise XdError(rc, xd_last_error(ctx))
     return r.value
+
+
+def xd_autotune(ctx, args, path=None):
+    """Tune on a host sample (BatchArgs); returns the winner's milliseconds."""
+    ms = ctypes.c_float()
+    rc = lib().xd_autotune(ctx, ctypes.byref(args.c), None if path is None else str(path).encode(),
+                           ctypes.byref(ms))
+    if rc != XD_OK:
+        raise XdError(rc, xd_last_error(ctx))
+    return ms.value
 
 
 # ----------------------------------------------------------------------------- helpers
