@@ -34,7 +34,10 @@ import synth  # noqa: E402
 # conditional assignment, and the running maximum T'.
 ALG_OPS_PER_CELL = 9
 SM_COUNT_GB300 = 152
-INT32_LANES_PER_SM = 128
+# Integer ALU-pipe lanes per SM per clock: max, DPX, logic, select and byte-permute
+# instructions all issue there (measured: 60-61 per clock at 1.99 GHz for each of them);
+# plain adds and multiply-adds can also use the FMA pipe.
+ALU_LANES_PER_SM = 64
 
 
 def parse():
@@ -403,15 +406,21 @@ def main():
         except (OSError, ValueError):
             pass
         sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-        peak = props.multi_processor_count * INT32_LANES_PER_SM * sm_max * 1e6 / 1e12
-        tier_names = ["narrow (thread per side)", "wide (warp per side)", "generic (warp per side, global ring)"]
+        peak = props.multi_processor_count * ALU_LANES_PER_SM * sm_max * 1e6 / 1e12
+        # measured in this run: the ALU pipe's issue rate (max) and the tiers' own cell update
+        alu_meas = xdrop.xd_probe(ctx, "max") / 1e12
+        cell_probe = xdrop.xd_probe(ctx, "cell_dna" if b.alphabet == "dna" else "cell_prot")
+        tier_names = ["first register launch (fused persistent grid of levels 0-2, or level 0)",
+                      "later register levels and band tier", "generic tier"]
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                     "frac": achieved / peak if peak else None, "traffic": None,
-                    "kernel": tier_names[top],
-                    "ops_per_cell": ALG_OPS_PER_CELL,
-                    "peak_basis": f"{props.multi_processor_count} SMs x {INT32_LANES_PER_SM} INT32 lanes x "
-                                  f"{sm_max:.0f} MHz (max SM clock)",
-                    "kernel_ms": tier_ms[top]}
+                    "kernel": tier_names[top], "ops_per_cell": ALG_OPS_PER_CELL,
+                    "peak_basis": f"{props.multi_processor_count} SMs x {ALU_LANES_PER_SM} integer ALU-pipe "
+                                  f"lanes x {sm_max:.0f} MHz (max SM clock)",
+                    "kernel_ms": tier_ms[top],
+                    "measured_alu_peak": alu_meas, "frac_of_measured_alu": achieved / alu_meas,
+                    "cell_probe_gcups": cell_probe / 1e9,
+                    "frac_of_cell_probe": top_cells / (tier_ms[top] * 1e-3) / cell_probe}
         if clk.get("sm_mhz"):
             roofline["frac_at_sampled_clock"] = achieved / (peak * clk["sm_mhz"] / sm_max)
 

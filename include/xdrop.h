@@ -124,7 +124,7 @@ typedef struct {
     uint64_t batches;            /* batches run (host and device entry points) */
     uint64_t pairs;
     uint64_t cells;              /* sum of xd_side.cells over all sides */
-    uint64_t units_tier[3];      /* side extensions finished by the narrow, wide, generic tier */
+    uint64_t units_tier[3];      /* side extensions finished per stage (see xd_timing) */
     uint64_t escalations;        /* side extensions restarted in a wider tier */
     uint64_t kernel_launches;    /* kernels launched by the library */
     uint64_t host_launches;      /* launches of host batches (one per merged group) */
@@ -180,10 +180,13 @@ xd_status xd_get_stats(const xd_ctx* ctx, xd_stats* out);
 
 /* Timing of the device pipeline, summed over every batch run since timing was enabled,
  * recorded with CUDA events on the stream the kernels are launched on.  Stage times are
- * in milliseconds; tier 0 = one thread per side extension (narrow bands), tier 1 = one
- * warp per side extension (wide bands), tier 2 = generic (any band width).  tier_cells
- * are the DP cells of the side extensions each tier finished; discarded_cells were
- * evaluated by a tier before a side was escalated to a wider one. */
+ * in milliseconds.  The side extensions run in three stages: tier 0 = the first register
+ * launch (the fused persistent grid of the first three register levels, or the first
+ * level alone), tier 1 = the later register levels and the band tier (one warp per side
+ * with a shared-memory ring), tier 2 = the generic tier (any band width, rows in global
+ * memory).  tier_units / tier_cells are the side extensions each stage finished and their
+ * DP cells; discarded_cells were evaluated by a level before a side was escalated without
+ * an escalation record. */
 typedef struct {
     uint64_t batches;            /* batches summed below */
     float pack_ms, units_ms, order_ms;
@@ -213,8 +216,9 @@ xd_status xd_get_timing(xd_ctx* ctx, xd_timing* out);
  *   0 add, 1 max, 2 DPX add-max, 3 DPX 3-way max, 4 3-input logic, 5 multiply-add,
  *   6 compare + select (two instructions), 7 byte permute, 8 DPX add-max on 16x2,
  *   9 DPX 3-way max on 16x2, 10 max on 16x2,
- * or op 100: the register tiers' complete DNA cell update on 32 in-register slots.
- * *rate receives operations (op 100: cells) per second for the whole GPU.  Synchronous;
+ * or op 100 / 101: the register tiers' own cell update on 32 in-register slots for DNA /
+ * protein scoring (every slot in the band, no band bookkeeping).
+ * *rate receives operations (ops 100, 101: cells) per second for the whole GPU.  Synchronous;
  * runs for a few tens of milliseconds.  Errors: XD_EINVAL (unknown op), XD_EDEVICE. */
 xd_status xd_probe(xd_ctx* ctx, int32_t op, double* rate);
 

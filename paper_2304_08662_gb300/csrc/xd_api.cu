@@ -1205,7 +1205,7 @@ xd_status xd_get_timing(xd_ctx* c, xd_timing* out) {
 
 xd_status xd_probe(xd_ctx* c, int32_t op, double* rate) {
     if (!c || !rate) return XD_EINVAL;
-    if (!((op >= 0 && op <= 10) || op == 100)) return fail(c, XD_EINVAL, "unknown probe op");
+    if (!((op >= 0 && op <= 10) || op == 100 || op == 101)) return fail(c, XD_EINVAL, "unknown probe op");
     std::lock_guard<std::mutex> lk(c->mu);
     XD_CUDA(c, cudaSetDevice(c->device));
     XD_CUDA(c, cudaDeviceSynchronize());

@@ -37,8 +37,11 @@ struct Problem {
     const Unit* units;
     xd_result* results;         // per pair
     uint32_t* err;              // validation / wait error word
-    unsigned long long* stats;  // per batch: [0..2] units finished per tier, [3] escalations,
-                                // [4..6] cells per tier, [7] cells discarded by escalation
+    unsigned long long* stats;  // per batch: [0..2] units finished per stage, [3] escalations,
+                                // [4..6] cells per stage, [7] cells discarded by escalation,
+                                // [8] window re-centrings.  Stage 0: the first register
+                                // launch (fused grid or level 0); 1: later register levels
+                                // and the band tier; 2: the generic tier
     int32_t alpha;              // 4 or 20
     int32_t gap;
     int32_t X;

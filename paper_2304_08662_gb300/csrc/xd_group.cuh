@@ -568,7 +568,7 @@ __device__ __forceinline__ bool load_record(const Problem& P, uint32_t ri, SideS
 // gsm_block: the block's shared rows (2W ints per group).
 template <int G, int CG, int A>
 __device__ __forceinline__ void group_loop(const Problem& P, const Queues& Q, const Source& S, int out_q,
-                                           int chunk, int32_t* smem) {
+                                           int chunk, int32_t* smem, int stage) {
     constexpr int W = G * CG;
     const int lane = threadIdx.x & 31;
     const int gl = lane % G;
@@ -598,8 +598,8 @@ __device__ __forceinline__ void group_loop(const Problem& P, const Queues& Q, co
             if (s.m + s.n == 0) {
                 if (gl == 0) {
                     write_side(P.results, pair, s.side, 0, 0, 0, 0, 1);
-                    atomicAdd(&P.stats[0], 1ull);
-                    atomicAdd(&P.stats[4], 1ull);
+                    atomicAdd(&P.stats[stage], 1ull);
+                    atomicAdd(&P.stats[4 + stage], 1ull);
                 }
                 continue;
             }
@@ -625,9 +625,8 @@ __device__ __forceinline__ void group_loop(const Problem& P, const Queues& Q, co
         if (r == kDone) {
             if (gl == 0) {
                 write_side(P.results, pair, s.side, s.best, uint32_t(s.bi), uint32_t(s.bj), s.flags, s.cells);
-                const int tier = W <= 32 ? 0 : 1;
-                atomicAdd(&P.stats[tier], 1ull);
-                atomicAdd(&P.stats[4 + tier], (unsigned long long)s.cells);
+                atomicAdd(&P.stats[stage], 1ull);
+                atomicAdd(&P.stats[4 + stage], (unsigned long long)s.cells);
             }
             continue;
         }
@@ -674,7 +673,7 @@ template <int G, int CG, int MINB, int A>
 __global__ void __launch_bounds__(128, MINB) k_group(Problem P, Queues Q, int in_q, int out_q, int chunk) {
     extern __shared__ __align__(16) int32_t group_smem[];
     build_table<A>(group_smem, P);
-    group_loop<G, CG, A>(P, Q, static_source(Q, in_q), out_q, chunk, group_smem);
+    group_loop<G, CG, A>(P, Q, static_source(Q, in_q), out_q, chunk, group_smem, in_q < 0 ? 0 : 1);
 }
 
 // The first register levels fused into one persistent, cooperatively launched grid.
@@ -727,14 +726,14 @@ __global__ void __launch_bounds__(128, MINB) k_fused(Problem P, Queues Q, RolePl
     uint32_t* done1 = &Q.ctr[2 + 2 * kLevels];
     const int role = start_role(gw, R.every1, R.every2);
     if (role == 0) {
-        group_loop<G0, C0, A>(P, Q, static_source(Q, -1), 0, chunk, group_smem);
+        group_loop<G0, C0, A>(P, Q, static_source(Q, -1), 0, chunk, group_smem, 0);
         signal_done(done0);
     }
     if (role <= 1) {
-        group_loop<G1, C1, A>(P, Q, live_source(Q, 0, done0, R.producers0), 1, 1, group_smem);
+        group_loop<G1, C1, A>(P, Q, live_source(Q, 0, done0, R.producers0), 1, 1, group_smem, 0);
         signal_done(done1);
     }
-    group_loop<G2, C2, A>(P, Q, live_source(Q, 1, done1, R.producers1), 2, 1, group_smem);
+    group_loop<G2, C2, A>(P, Q, live_source(Q, 1, done1, R.producers1), 2, 1, group_smem, 0);
 }
 
 template <int G, int CG, int MINB, int A>

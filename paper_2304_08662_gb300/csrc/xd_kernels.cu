@@ -400,8 +400,8 @@ __device__ bool extend_band(const Problem& P, const Unit& u, uint32_t uidx, int3
     }
     if (lane == 0) {
         write_side(P.results, u.pair, u.side, best, uint32_t(bi), uint32_t(bj), flags, cells);
-        atomicAdd(&P.stats[2], 1ull);
-        atomicAdd(&P.stats[6], (unsigned long long)cells);
+        atomicAdd(&P.stats[1], 1ull);
+        atomicAdd(&P.stats[5], (unsigned long long)cells);
     }
     __syncwarp();
     return true;

@@ -8,8 +8,7 @@
 // (or cells) per second for the whole GPU.
 #include <cstdint>
 #include <cuda_runtime.h>
-#include "xd_device.cuh"
-#include "xd_launch.h"
+#include "xd_group.cuh"
 
 namespace xd {
 
@@ -25,7 +24,8 @@ enum ProbeOp {
     kProbeViaddmax16 = 8,  // 16x2: x = max(x + c, y) per half   (DPX)
     kProbeVimax3_16 = 9,   // 16x2: x = max(x, y, z) per half    (DPX)
     kProbeVmax16 = 10,     // 16x2: x = max(x, y) per half
-    kProbeCellDna = 100,   // full per-cell update of the register tiers, 32 slots
+    kProbeCellDna = 100,   // the register tiers' cell update (cells_of), DNA, 32 slots
+    kProbeCellProt = 101,  // the same, protein (similarity-table offsets), 32 slots
 };
 
 template <int OP>
@@ -63,47 +63,55 @@ __global__ void __launch_bounds__(256) k_probe(int32_t* out, int iters, int32_t 
     if (acc == seed) out[blockIdx.x] = acc;   // practically never true; keeps the chains live
 }
 
-// The register tiers' cell update on 32 in-register slots, alternating odd / even
-// anti-diagonals, every slot inside the band.
-template <bool ODD>
-__device__ __forceinline__ void probe_cells(int32_t (&P1)[32], int32_t (&P2)[32], uint64_t x,
-                                            int32_t thr, int32_t gap, int32_t mat, int32_t mis,
-                                            int32_t& kmax, uint32_t& lm) {
-    kmax = INT32_MIN;
-    lm = 0;
-#pragma unroll
-    for (int t = 0; t < 32; t++) {
-        const int32_t up = ODD ? (t > 0 ? P1[t - 1] : -(1 << 24)) : P1[t];
-        const int32_t lf = ODD ? P1[t] : (t < 31 ? P1[t + 1] : -(1 << 24));
-        const int32_t sig = ((x >> (2 * t)) & 3ull) ? mis : mat;
-        const int32_t raw = __viaddmax_s32(max(up, lf), gap, P2[t] + sig);
-        const bool live = raw >= thr;
-        const int32_t v = live ? raw : -(1 << 24);
-        P2[t] = v;
-        lm |= live ? (1u << t) : 0u;
-        kmax = max(kmax, v * 64 + (63 - t));
-    }
-}
-
+// The register tiers' own cell update (cells_of of the group kernels) on 32 in-register
+// slots, alternating odd / even anti-diagonals, every slot inside the band; the residue
+// slices rotate so that the similarities vary.
+template <int A>
 __global__ void __launch_bounds__(128, 2) k_probe_cells(int32_t* out, int iters, int32_t seed) {
-    int32_t A[32], B[32];
+    __shared__ __align__(16) int32_t tab[kLutInts];
+    Problem P{};
+    if (A == 4) {
+        P.sim[0] = 1;
+        P.sim[1] = -1;
+    } else {
+        for (int t = 0; t < 400; t++) P.sim[t] = int8_t((t * 7 + 3) % 15 - 7);
+    }
+    build_table<A>(tab, P);
+    int32_t R0[32], R1[32];
 #pragma unroll
     for (int t = 0; t < 32; t++) {
-        A[t] = (t * 7 + seed) & 15;
-        B[t] = (t * 3 + seed) & 15;
+        R0[t] = (t * 7 + seed) & 15;
+        R1[t] = (t * 3 + seed) & 15;
     }
+    Res<32, A> res;
     uint64_t x = 0x9E3779B97F4A7C15ull ^ uint64_t(threadIdx.x) * 0xBF58476D1CE4E5B9ull;
+    if constexpr (A == 4) {
+        res.hs = x;
+        res.vs = x * 0x94D049BB133111EBull;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+            res.hx[k] = uint32_t((x >> (k & 7)) % 20) * 80u | (uint32_t((x >> (k + 9)) % 20) * 80u << 16);
+            res.vx[k] = uint32_t((x >> (k + 3)) % 20) * 4u | (uint32_t((x >> (k + 17)) % 20) * 4u << 16);
+        }
+    }
     int32_t thr = -100, kmax = 0;
     uint32_t lm = 0, acc = 0;
     for (int k = 0; k < iters; k++) {
-        probe_cells<true>(A, B, x, thr, -1, 1, -1, kmax, lm);
+        cells_of<32, true, A>(R0, R1, kNegR, kNegR, res, 0xffffffffu, thr, -1, tab, kmax, lm);
         acc ^= lm;
         thr = (kmax >> 6) - 40;
-        x = (x << 2) | (x >> 62);
-        probe_cells<false>(B, A, x, thr, -1, 1, -1, kmax, lm);
+        cells_of<32, false, A>(R1, R0, kNegR, kNegR, res, 0xffffffffu, thr, -1, tab, kmax, lm);
         acc ^= lm;
         thr = (kmax >> 6) - 40;
-        x = (x << 2) | (x >> 62);
+        if constexpr (A == 4) {
+            res.hs = (res.hs << 2) | (res.hs >> 62);
+        } else {
+            const uint32_t t0 = res.hx[0];
+#pragma unroll
+            for (int q = 0; q < 15; q++) res.hx[q] = res.hx[q + 1];
+            res.hx[15] = t0;
+        }
     }
     if (acc == uint32_t(seed) && kmax == seed) out[blockIdx.x] = int32_t(acc);
 }
@@ -123,7 +131,8 @@ cudaError_t probe_rate(int op, int n_sm, double* rate, float* ms_out) {
     cudaEventCreate(&a);
     cudaEventCreate(&b);
     const int blocks = n_sm * 8;
-    int iters = op == kProbeCellDna ? 4000 : 20000;
+    const bool cells = op == kProbeCellDna || op == kProbeCellProt;
+    int iters = cells ? 4000 : 20000;
     double per_thread = 0;
     int threads = 256;
     auto launch = [&]() -> cudaError_t {
@@ -140,18 +149,21 @@ cudaError_t probe_rate(int op, int n_sm, double* rate, float* ms_out) {
             case kProbeVimax3_16: return run_probe<kProbeVimax3_16>(blocks, iters, 0, out);
             case kProbeVmax16: return run_probe<kProbeVmax16>(blocks, iters, 0, out);
             case kProbeCellDna:
-                k_probe_cells<<<n_sm * 2, 128, 0, 0>>>(out, iters, 12345);
+                k_probe_cells<4><<<n_sm * 2, 128, 0, 0>>>(out, iters, 12345);
+                return cudaGetLastError();
+            case kProbeCellProt:
+                k_probe_cells<20><<<n_sm * 2, 128, 0, 0>>>(out, iters, 12345);
                 return cudaGetLastError();
             default: return cudaErrorInvalidValue;
         }
     };
-    if (op == kProbeCellDna) {
+    if (cells) {
         threads = 128;
         per_thread = double(iters) * 64.0;            // cells
     } else {
         per_thread = double(iters) * 64.0;            // 8 rounds x 8 chains
     }
-    const int total_blocks = op == kProbeCellDna ? n_sm * 2 : blocks;
+    const int total_blocks = cells ? n_sm * 2 : blocks;
     e = launch();                                      // warm-up
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     float ms = 0;
