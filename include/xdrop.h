@@ -129,6 +129,8 @@ typedef struct {
     uint64_t kernel_launches;    /* kernels launched by the library */
     uint64_t host_launches;      /* launches of host batches (one per merged group) */
     uint64_t host_requests;      /* host batches those launches ran */
+    uint64_t graph_captures;     /* device-entry pipelines captured as CUDA graphs */
+    uint64_t graph_replays;      /* device-entry batches run by replaying a graph */
 } xd_stats;
 
 /* Create a context on cfg->device (NULL cfg = defaults).  Allocates nothing large until
@@ -164,6 +166,10 @@ xd_status xd_poll(xd_ctx* ctx, uint64_t ticket, xd_result* out, int32_t wait_ms)
  * comes from the context and is grown on demand (call xd_reserve first to keep
  * allocations out of a timed region).  Input validation happens on the device; read it
  * with xd_device_status after the stream has finished.  Not reentrant per context.
+ * A call whose arguments (device pointers, sizes, scoring, X, delta_b, stream) repeat the
+ * previous call's exactly is captured as a CUDA graph and later such calls replay it (the
+ * buffers' contents may change between calls; on a non-default stream, when timing is
+ * off).  The call may itself be captured into the caller's graph.
  * Errors: XD_EINVAL (null pointers, X < 0, protein without matrix), XD_ENOMEM, XD_EDEVICE. */
 xd_status xd_run_device(xd_ctx* ctx, const xd_batch* dev_batch, xd_result* d_out, void* stream);
 

@@ -187,6 +187,18 @@ void par_memcpy(void* dst, const void* src, size_t n) { par_copy_check(dst, src,
 
 }  // namespace
 
+// Everything a captured pipeline bakes in: device pointers, sizes, parameters, scratch.
+struct GraphKey {
+    int alpha;
+    uint32_t n_seqs, n_pairs, max_len, delta;
+    uint64_t n_codes;
+    const void *codes, *offsets, *lengths, *pairs, *out, *stream;
+    int32_t gap, X;
+    int8_t sim[400];
+    const void* scratch[11 + kLevels];
+    const void* tiers;
+};
+
 // One tuned configuration: the register-level chain and its launch parameters for batches of
 // one alphabet, X bucket and length bucket.
 struct TuneEntry {
@@ -235,6 +247,14 @@ struct xd_ctx {
     // the fused persistent kernel's blocks wait on one another, so two of them never run at
     // the same time: each waits for the previous one through this event
     cudaEvent_t coop_done = nullptr;
+    // CUDA graph of the device entry point: a batch that repeats the previous call's
+    // arguments exactly is captured once and then replayed
+    bool graphs = true;
+    GraphKey last_key{}, graph_key{};
+    bool have_last = false;
+    cudaGraphExec_t graph_exec = nullptr;
+    uint64_t graph_launches = 0;       // kernels per replay
+    uint64_t graph_replays = 0, graph_captures = 0;
 };
 
 namespace {
@@ -383,6 +403,7 @@ void default_tiers(xd_ctx* c) {
     TierConfig& t = c->tiers;
     for (int v = 0; v < kNumGroupVariants; v++) t.blocks_per_sm[v] = 3;
     for (int v : {kG1C32, kG32C32, kG4C32, kG8C32, kG16C32}) t.blocks_per_sm[v] = 2;
+    for (int v : {kG4C8, kG8C8, kG16C8, kG32C8}) t.blocks_per_sm[v] = 4;
     t.chunk = std::max(1, env_int("XD_CHUNK", 1));
     t.fused = env_int("XD_FUSED", 1) != 0;
     t.every1 = std::max(0, env_int("XD_EVERY1", 4));
@@ -848,7 +869,8 @@ bool parse_entry(const std::string& line, const TierConfig& base, TuneEntry& out
     if (out.alpha == 20)
         for (int k = 0; k < out.cfg.n_levels; k++) {
             const int v = out.cfg.variant[k];
-            if (!(v == kG1C16 || v == kG4C16 || v == kG8C16 || v == kG16C16 || v == kG32C16 || v == kG32C32)) {
+            if (!(v == kG1C16 || v == kG4C16 || v == kG8C16 || v == kG16C16 || v == kG32C16 || v == kG32C32 ||
+                  v == kG8C8 || v == kG32C8)) {
                 why = "variant " + std::to_string(v) + " is not compiled for protein";
                 return false;
             }
@@ -894,9 +916,9 @@ void put_entry(std::vector<TuneEntry>& v, const TuneEntry& t) {
 int tier_group_of(int v) {
     switch (v) {
         case kG1C16: case kG1C32: return 1;
-        case kG4C16: case kG4C32: return 4;
-        case kG8C16: case kG8C32: return 8;
-        case kG16C16: case kG16C32: return 16;
+        case kG4C16: case kG4C32: case kG4C8: return 4;
+        case kG8C16: case kG8C32: case kG8C8: return 8;
+        case kG16C16: case kG16C32: case kG16C8: return 16;
         default: return 32;
     }
 }
@@ -959,6 +981,7 @@ xd_status xd_create(const xd_config* cfg, xd_ctx** out) {
     int inflight = cfg && cfg->max_inflight > 0 ? cfg->max_inflight : 3;
     c->slots.resize(inflight);
     c->merge = !(cfg && cfg->batching < 0);
+    c->graphs = env_int("XD_GRAPHS", 1) != 0;
     if (cfg && cfg->max_batch_pairs) c->max_batch_pairs = cfg->max_batch_pairs;
     const char* mode = std::getenv("XD_TIERS");
     c->generic_only = mode && std::strcmp(mode, "generic") == 0;
@@ -1030,7 +1053,79 @@ xd_status xd_run_device(xd_ctx* c, const xd_batch* b, xd_result* d_out, void* st
     // where the caller orders its graphs)
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     XD_CUDA(c, cudaStreamIsCapturing(st, &cs));
-    return run_pipeline(c, c->dev, v, d_out, st, cs == cudaStreamCaptureStatusNone ? c->coop_done : nullptr);
+    if (cs != cudaStreamCaptureStatusNone) return run_pipeline(c, c->dev, v, d_out, st, nullptr);
+    if (!c->graphs || c->timing || st == nullptr) return run_pipeline(c, c->dev, v, d_out, st, c->coop_done);
+    // the scratch must be in place before a capture (no allocation inside one)
+    const ScratchPlan plan = plan_scratch(c, v.alpha, v.n_codes, v.n_pairs, v.max_len);
+    XD_CUDA(c, ensure_scratch(c->dev, plan));
+    GraphKey k;
+    std::memset(&k, 0, sizeof(k));
+    k.alpha = v.alpha;
+    k.n_seqs = v.n_seqs;
+    k.n_pairs = v.n_pairs;
+    k.max_len = v.max_len;
+    k.delta = v.delta;
+    k.n_codes = v.n_codes;
+    k.codes = v.codes;
+    k.offsets = v.offsets;
+    k.lengths = v.lengths;
+    k.pairs = v.pairs;
+    k.out = d_out;
+    k.stream = st;
+    k.gap = v.gap;
+    k.X = v.X;
+    std::memcpy(k.sim, v.sim, sizeof(k.sim));
+    const Scratch& sc = c->dev;
+    const void* bufs[11] = {sc.store.p, sc.units.p, sc.bucket.p, sc.order.p, sc.ctr.p, sc.hist.p,
+                            sc.err.p, sc.generic.p, sc.bstats.p, sc.rec.p, sc.rec_of.p};
+    std::memcpy(k.scratch, bufs, sizeof(bufs));
+    for (int q = 0; q < kLevels; q++) k.scratch[11 + q] = sc.q[q].p;
+    k.tiers = &tiers_for(c, v);
+    if (c->graph_exec && std::memcmp(&k, &c->graph_key, sizeof(k)) == 0) {
+        XD_CUDA(c, cudaStreamWaitEvent(st, c->coop_done, 0));
+        XD_CUDA(c, cudaGraphLaunch(c->graph_exec, st));
+        XD_CUDA(c, cudaEventRecord(c->coop_done, st));
+        c->graph_replays += 1;
+        c->launches += c->graph_launches;
+        c->batches += 1;
+        c->pairs += v.n_pairs;
+        return XD_OK;
+    }
+    const bool repeat = c->have_last && std::memcmp(&k, &c->last_key, sizeof(k)) == 0;
+    c->last_key = k;
+    c->have_last = true;
+    if (!repeat) return run_pipeline(c, c->dev, v, d_out, st, c->coop_done);
+    // the second identical call: capture the pipeline, then launch the graph
+    const uint64_t launches0 = c->launches, batches0 = c->batches, pairs0 = c->pairs;
+    XD_CUDA(c, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    const xd_status ps = run_pipeline(c, c->dev, v, d_out, st, nullptr);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(st, &g);
+    cudaGraphExec_t exec = nullptr;
+    if (ps == XD_OK && e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    c->batches = batches0;
+    c->pairs = pairs0;
+    const uint64_t per = c->launches - launches0;
+    c->launches = launches0;
+    if (ps != XD_OK || e != cudaSuccess) {
+        // this pipeline cannot be captured here: keep launching it directly
+        cudaGetLastError();
+        c->graphs = false;
+        return run_pipeline(c, c->dev, v, d_out, st, c->coop_done);
+    }
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    c->graph_exec = exec;
+    c->graph_key = k;
+    c->graph_launches = per;
+    c->graph_captures += 1;
+    XD_CUDA(c, cudaStreamWaitEvent(st, c->coop_done, 0));
+    XD_CUDA(c, cudaGraphLaunch(exec, st));
+    XD_CUDA(c, cudaEventRecord(c->coop_done, st));
+    c->launches += per;
+    c->batches += 1;
+    c->pairs += v.n_pairs;
+    return XD_OK;
 }
 
 xd_status xd_device_status(xd_ctx* c, uint32_t* flags) {
@@ -1151,6 +1246,8 @@ xd_status xd_get_stats(const xd_ctx* c, xd_stats* out) {
     out->kernel_launches = c->launches;
     out->host_launches = c->merged_launches;
     out->host_requests = c->merged_requests;
+    out->graph_captures = c->graph_captures;
+    out->graph_replays = c->graph_replays;
     return XD_OK;
 }
 
@@ -1388,6 +1485,7 @@ xd_status xd_destroy(xd_ctx* c) {
         for (cudaEvent_t ev : set) cudaEventDestroy(ev);
     if (c->dev_stream) cudaStreamDestroy(c->dev_stream);
     if (c->coop_done) cudaEventDestroy(c->coop_done);
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     delete c;
     return rc;
 }

@@ -404,17 +404,31 @@ __device__ __forceinline__ int group_step(SideState& s, Res<CG, A>& res, int32_t
     uint32_t lm;
     cells_of<CG, ODD, A>(P1, P2, upb, lfb, res, bm, thr, P.gap, tab, kmax, lm);
     s.cells += uint64_t(hi - lo + 1);
-    const bool any = lm != 0;
-    int32_t first = any ? sb + __ffs(lm) - 1 : INT32_MAX;
-    int32_t last = any ? sb + 31 - __clz(lm) : -1;
-    first = gmin<G>(first, gm);
-    if (first == INT32_MAX) return kDone;
-    last = gmax<G>(last, gm);
+    const int32_t lv = kmax >> 6;
+    int32_t first, last, wmax, arg;
+    if constexpr (G == 1) {
+        if (lm == 0) return kDone;
+        first = __ffs(lm) - 1;
+        last = 31 - __clz(lm);
+        wmax = lv;
+        arg = ib + 63 - (kmax & 63);
+    } else {
+        // live range: the first / last lane with a live cell (one vote) gives the group's
+        // first / last live slot; best cell: the group maximum, then the lowest lane that
+        // holds it (one vote) gives its lowest slot
+        const int base = (threadIdx.x & 31) - gl;
+        uint32_t live_lanes = __ballot_sync(gm, lm != 0);
+        if constexpr (G < 32) live_lanes = (live_lanes >> base) & ((1u << G) - 1u);
+        if (live_lanes == 0) return kDone;
+        first = __shfl_sync(gm, sb + __ffs(lm) - 1, base + __ffs(live_lanes) - 1);
+        last = __shfl_sync(gm, sb + 31 - __clz(lm), base + 31 - __clz(live_lanes));
+        wmax = gmax<G>(lv, gm);
+        uint32_t best_lanes = __ballot_sync(gm, lv == wmax);
+        if constexpr (G < 32) best_lanes = (best_lanes >> base) & ((1u << G) - 1u);
+        arg = ib + __shfl_sync(gm, sb + (63 - (kmax & 63)), base + __ffs(best_lanes) - 1);
+    }
     s.L = ib + first;
     s.U = ib + last;
-    const int32_t lv = kmax >> 6;
-    const int32_t wmax = gmax<G>(lv, gm);
-    const int32_t arg = ib + gmin<G>(lv == wmax ? sb + (63 - (kmax & 63)) : INT32_MAX, gm);
     if (wmax > s.T) {
         s.T = wmax;
         s.best = wmax;

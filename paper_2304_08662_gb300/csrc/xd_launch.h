@@ -31,8 +31,8 @@ cudaError_t launch_accumulate(const unsigned long long* batch, unsigned long lon
 // followed by the generic tier.  Variant ids name the compiled (G, CG) pairs.
 enum GroupVariant {
     kG1C16 = 0, kG1C32 = 1, kG4C16 = 2, kG8C16 = 3, kG16C16 = 4, kG32C16 = 5, kG32C32 = 6,
-    kG4C32 = 7, kG8C32 = 8, kG16C32 = 9,
-    kNumGroupVariants = 10
+    kG4C32 = 7, kG8C32 = 8, kG16C32 = 9, kG4C8 = 10, kG8C8 = 11, kG16C8 = 12, kG32C8 = 13,
+    kNumGroupVariants = 14
 };
 
 struct TierConfig {
@@ -58,7 +58,10 @@ bool fused_supported(const TierConfig& cfg, int alpha);
 cudaError_t launch_fused_levels(const Problem& P, const Queues& Q, const TierConfig& cfg, int n_sm,
                                 cudaStream_t st);
 
-// Protein instantiations (xd_tiers_prot.cu), reached through the two launchers above.
+// DNA levels (xd_tiers_dna.cu) and protein instantiations (xd_tiers_prot.cu), reached
+// through the launchers above.
+cudaError_t launch_level_dna(const Problem& P, const Queues& Q, int variant, int in_q, int out_q,
+                             int blocks, int chunk, cudaStream_t st);
 cudaError_t launch_level_prot(const Problem& P, const Queues& Q, int variant, int in_q, int out_q,
                               int blocks, int chunk, cudaStream_t st);
 bool fused_supported_prot(int a, int b, int d);

@@ -1,4 +1,4 @@
-// Register tiers, DNA instantiations (A = 4), and the dispatch of register levels to the
+// Register tiers: the fused DNA grids (A = 4) and the dispatch of register levels to the
 // DNA or protein kernels.  The kernels themselves are the templates of xd_group.cuh.
 #include "xd_group.cuh"
 
@@ -16,6 +16,10 @@ int variant_window(int v) {
         case kG4C32: return 128;
         case kG8C32: return 256;
         case kG16C32: return 512;
+        case kG4C8: return 32;
+        case kG8C8: return 64;
+        case kG16C8: return 128;
+        case kG32C8: return 256;
         default: return 0;
     }
 }
@@ -27,19 +31,7 @@ cudaError_t launch_level(const Problem& P, const Queues& Q, const TierConfig& cf
     const int out_q = level == cfg.n_levels - 1 ? kBandQ : level;
     const int blocks = n_sm * cfg.blocks_per_sm[v];
     if (P.alpha == 20) return launch_level_prot(P, Q, v, in_q, out_q, blocks, cfg.chunk, st);
-    switch (v) {
-        case kG1C16: return launch_group<1, 16, 3, 4>(P, Q, in_q, out_q, blocks, cfg.chunk, st);
-        case kG1C32: return launch_group<1, 32, 2, 4>(P, Q, in_q, out_q, blocks, cfg.chunk, st);
-        case kG4C16: return launch_group<4, 16, 3, 4>(P, Q, in_q, out_q, blocks, cfg.chunk, st);
-        case kG8C16: return launch_group<8, 16, 3, 4>(P, Q, in_q, out_q, blocks, cfg.chunk, st);
-        case kG16C16: return launch_group<16, 16, 3, 4>(P, Q, in_q, out_q, blocks, cfg.chunk, st);
-        case kG32C16: return launch_group<32, 16, 3, 4>(P, Q, in_q, out_q, blocks, cfg.chunk, st);
-        case kG32C32: return launch_group<32, 32, 2, 4>(P, Q, in_q, out_q, blocks, cfg.chunk, st);
-        case kG4C32: return launch_group<4, 32, 2, 4>(P, Q, in_q, out_q, blocks, cfg.chunk, st);
-        case kG8C32: return launch_group<8, 32, 2, 4>(P, Q, in_q, out_q, blocks, cfg.chunk, st);
-        case kG16C32: return launch_group<16, 32, 2, 4>(P, Q, in_q, out_q, blocks, cfg.chunk, st);
-        default: return cudaErrorInvalidValue;
-    }
+    return launch_level_dna(P, Q, v, in_q, out_q, blocks, cfg.chunk, st);
 }
 
 bool fused_supported(const TierConfig& c, int alpha) {

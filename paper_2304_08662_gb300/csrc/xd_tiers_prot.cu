@@ -13,6 +13,8 @@ cudaError_t launch_level_prot(const Problem& P, const Queues& Q, int variant, in
         case kG16C16: return launch_group<16, 16, 3, 20>(P, Q, in_q, out_q, blocks, chunk, st);
         case kG32C16: return launch_group<32, 16, 3, 20>(P, Q, in_q, out_q, blocks, chunk, st);
         case kG32C32: return launch_group<32, 32, 2, 20>(P, Q, in_q, out_q, blocks, chunk, st);
+        case kG8C8: return launch_group<8, 8, 4, 20>(P, Q, in_q, out_q, blocks, chunk, st);
+        case kG32C8: return launch_group<32, 8, 4, 20>(P, Q, in_q, out_q, blocks, chunk, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -46,7 +46,8 @@ class xd_stats(ctypes.Structure):
     _fields_ = [("batches", ctypes.c_uint64), ("pairs", ctypes.c_uint64), ("cells", ctypes.c_uint64),
                 ("units_tier", ctypes.c_uint64 * 3), ("escalations", ctypes.c_uint64),
                 ("kernel_launches", ctypes.c_uint64), ("host_launches", ctypes.c_uint64),
-                ("host_requests", ctypes.c_uint64)]
+                ("host_requests", ctypes.c_uint64), ("graph_captures", ctypes.c_uint64),
+                ("graph_replays", ctypes.c_uint64)]
 
 
 class xd_timing(ctypes.Structure):
@@ -204,7 +205,8 @@ def xd_get_stats(ctx):
     return {"batches": s.batches, "pairs": s.pairs, "cells": s.cells,
             "units_tier": list(s.units_tier), "escalations": s.escalations,
             "kernel_launches": s.kernel_launches, "host_launches": s.host_launches,
-            "host_requests": s.host_requests}
+            "host_requests": s.host_requests, "graph_captures": s.graph_captures,
+            "graph_replays": s.graph_replays}
 
 
 def xd_set_timing(ctx, enable=True):
