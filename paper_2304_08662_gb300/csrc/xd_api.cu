@@ -202,7 +202,7 @@ struct GraphKey {
 // One tuned configuration: the register-level chain and its launch parameters for batches of
 // one alphabet, X bucket and length bucket.
 struct TuneEntry {
-    int alpha = 4, xb = 0, lb = 0;
+    int alpha = 4, xb = 0, lb = 0, sb = 2;
     TierConfig cfg{};
     float ms = 0;
 };
@@ -218,7 +218,8 @@ struct xd_ctx {
     uint32_t reserved_len = 0;
     cudaStream_t dev_stream = nullptr;
     bool generic_only = false;
-    TierConfig tiers{}, tiers_small_x{}, tiers_large_x{}, tiers_protein{};
+    TierConfig tiers{}, tiers_small_x{}, tiers_large_x{}, tiers_protein{}, tiers_latency{};
+    uint32_t latency_units = 0;        // batches with fewer side extensions use tiers_latency
     std::vector<TuneEntry> tuned;      // autotuned configurations by (alphabet, X, length) bucket
     const TierConfig* force_tiers = nullptr;   // set while the autotuner times a candidate
     DevBuf stats;                // uint64 [16]: cumulative per-batch counters (see Problem::stats)
@@ -399,6 +400,26 @@ void set_chain(TierConfig& t, std::initializer_list<int> vs) {
     for (int v : vs) t.variant[t.n_levels++] = v;
 }
 
+// Comma-separated variant ids into a chain; false if the list is empty.
+bool parse_chain(const char* ch, TierConfig& t) {
+    int n = 0;
+    for (const char* q = ch; *q && n < kLevels - 2;) {
+        const int v = std::atoi(q);
+        if (v < 0 || v >= kNumGroupVariants) return false;
+        t.variant[n++] = v;
+        while (*q && *q != ',') q++;
+        if (*q == ',') q++;
+    }
+    if (n == 0) return false;
+    t.n_levels = n;
+    return true;
+}
+
+// Batches with fewer side extensions than this cannot fill the GPU with one lane per side:
+// their time is the serial anti-diagonal chain of their longest sides, so they run with a
+// full warp per side from the first level (lower latency per anti-diagonal).
+constexpr uint32_t kLatencyUnits = 65536;
+
 void default_tiers(xd_ctx* c) {
     TierConfig& t = c->tiers;
     for (int v = 0; v < kNumGroupVariants; v++) t.blocks_per_sm[v] = 3;
@@ -417,35 +438,32 @@ void default_tiers(xd_ctx* c) {
     c->tiers_protein = t;
     set_chain(c->tiers_protein, {kG4C16, kG16C16, kG32C32});
     c->tiers_protein.fused = env_int("XD_FUSED_PROT", 0) != 0;   // separate launches measured faster
-    if (const char* ch = std::getenv("XD_CHAIN_PROT")) {
-        c->tiers_protein.n_levels = 0;
-        for (const char* q = ch; *q && c->tiers_protein.n_levels < kLevels - 2;) {
-            c->tiers_protein.variant[c->tiers_protein.n_levels++] = std::atoi(q);
-            while (*q && *q != ',') q++;
-            if (*q == ',') q++;
-        }
-    }
+    c->tiers_latency = t;
+    set_chain(c->tiers_latency, {kG32C16, kG32C32});
+    c->tiers_latency.fused = false;
+    c->latency_units = uint32_t(std::max(0, env_int("XD_LATENCY_UNITS", int(kLatencyUnits))));
+    // overrides for experiments: comma-separated variant ids
+    if (const char* ch = std::getenv("XD_CHAIN_PROT")) parse_chain(ch, c->tiers_protein);
+    if (const char* ch = std::getenv("XD_CHAIN_SMALL")) parse_chain(ch, c->tiers_latency);
     if (const char* ch = std::getenv("XD_CHAIN")) {
-        // comma-separated variant ids, used for every X
         TierConfig forced = t;
-        forced.n_levels = 0;
-        for (const char* q = ch; *q && forced.n_levels < kLevels - 2;) {
-            forced.variant[forced.n_levels++] = std::atoi(q);
-            while (*q && *q != ',') q++;
-            if (*q == ',') q++;
-        }
-        c->tiers = c->tiers_small_x = c->tiers_large_x = forced;
+        if (parse_chain(ch, forced)) c->tiers = c->tiers_small_x = c->tiers_large_x = forced;
     }
 }
 
 int x_bucket(int32_t X) { return X <= 15 ? 0 : X <= 30 ? 1 : 2; }
 int len_bucket(uint32_t max_len) { return max_len <= 2048 ? 0 : max_len <= 20000 ? 1 : 2; }
+int size_bucket(uint32_t n_pairs) {
+    const uint64_t u = uint64_t(n_pairs) * 2;
+    return u < 8192 ? 0 : u < kLatencyUnits ? 1 : 2;
+}
 
 const TierConfig& tiers_for(const xd_ctx* c, const BatchView& b) {
     if (c->force_tiers) return *c->force_tiers;
-    const int xb = x_bucket(b.X), lb = len_bucket(b.max_len);
+    const int xb = x_bucket(b.X), lb = len_bucket(b.max_len), sb = size_bucket(b.n_pairs);
     for (const TuneEntry& t : c->tuned)
-        if (t.alpha == b.alpha && t.xb == xb && t.lb == lb) return t.cfg;
+        if (t.alpha == b.alpha && t.xb == xb && t.lb == lb && t.sb == sb) return t.cfg;
+    if (uint64_t(b.n_pairs) * 2 < c->latency_units) return c->tiers_latency;
     if (b.alpha == 20) return c->tiers_protein;
     if (b.X <= 15) return c->tiers_small_x;
     if (b.X <= 30) return c->tiers;
@@ -817,8 +835,9 @@ std::string format_entry(const TuneEntry& t) {
     std::string chain;
     for (int k = 0; k < t.cfg.n_levels; k++) chain += (k ? "," : "") + std::to_string(t.cfg.variant[k]);
     char buf[256];
-    std::snprintf(buf, sizeof(buf), "alpha=%d xb=%d lb=%d chain=%s chunk=%d fused=%d every1=%d every2=%d minb=%d ms=%.4f",
-                  t.alpha, t.xb, t.lb, chain.c_str(), t.cfg.chunk, t.cfg.fused ? 1 : 0, t.cfg.every1,
+    std::snprintf(buf, sizeof(buf),
+                  "alpha=%d xb=%d lb=%d sb=%d chain=%s chunk=%d fused=%d every1=%d every2=%d minb=%d ms=%.4f",
+                  t.alpha, t.xb, t.lb, t.sb, chain.c_str(), t.cfg.chunk, t.cfg.fused ? 1 : 0, t.cfg.every1,
                   t.cfg.every2, t.cfg.fused_minb, double(t.ms));
     return buf;
 }
@@ -855,6 +874,7 @@ bool parse_entry(const std::string& line, const TierConfig& base, TuneEntry& out
             if (k == "alpha") out.alpha = x;
             else if (k == "xb") out.xb = x;
             else if (k == "lb") out.lb = x;
+            else if (k == "sb") out.sb = x;
             else if (k == "chunk") out.cfg.chunk = std::max(1, std::min(x, 64));
             else if (k == "fused") out.cfg.fused = x != 0;
             else if (k == "every1") out.cfg.every1 = std::max(0, x);
@@ -865,7 +885,10 @@ bool parse_entry(const std::string& line, const TierConfig& base, TuneEntry& out
     }
     if (!have_chain) { why = "entry without chain"; return false; }
     if (out.alpha != 4 && out.alpha != 20) { why = "alpha must be 4 or 20"; return false; }
-    if (out.xb < 0 || out.xb > 2 || out.lb < 0 || out.lb > 2) { why = "bucket out of range"; return false; }
+    if (out.xb < 0 || out.xb > 2 || out.lb < 0 || out.lb > 2 || out.sb < 0 || out.sb > 2) {
+        why = "bucket out of range";
+        return false;
+    }
     if (out.alpha == 20)
         for (int k = 0; k < out.cfg.n_levels; k++) {
             const int v = out.cfg.variant[k];
@@ -905,7 +928,7 @@ xd_status load_table(xd_ctx* c, const char* path, std::vector<TuneEntry>& out) {
 
 void put_entry(std::vector<TuneEntry>& v, const TuneEntry& t) {
     for (TuneEntry& e : v)
-        if (e.alpha == t.alpha && e.xb == t.xb && e.lb == t.lb) {
+        if (e.alpha == t.alpha && e.xb == t.xb && e.lb == t.lb && e.sb == t.sb) {
             e = t;
             return;
         }
@@ -932,10 +955,14 @@ std::vector<TierConfig> chain_candidates(const TierConfig& base, int alpha) {
         chains = {{kG1C32, kG16C16, kG32C16, kG32C32}, {kG1C16, kG4C16, kG16C16, kG32C32},
                   {kG1C32, kG8C16, kG32C16, kG32C32}, {kG1C32, kG4C32, kG8C32, kG32C32},
                   {kG4C16, kG16C16, kG32C32},         {kG1C16, kG8C16, kG32C16, kG32C32},
-                  {kG1C32, kG8C16, kG16C16, kG32C32}};
+                  {kG1C32, kG8C16, kG16C16, kG32C32}, {kG32C16, kG32C32},
+                  {kG32C8, kG32C32},                  {kG16C8, kG32C16, kG32C32},
+                  {kG8C16, kG32C32}};
     else
         chains = {{kG4C16, kG16C16, kG32C32}, {kG1C16, kG4C16, kG16C16, kG32C32},
-                  {kG8C16, kG32C16, kG32C32}, {kG4C16, kG8C16, kG32C16, kG32C32}};
+                  {kG8C16, kG32C16, kG32C32}, {kG4C16, kG8C16, kG32C16, kG32C32},
+                  {kG32C16, kG32C32},         {kG32C8, kG32C32},
+                  {kG8C8, kG32C32}};
     std::vector<TierConfig> out;
     for (const auto& ch : chains)
         for (int fused = 1; fused >= 0; fused--) {
@@ -1400,6 +1427,7 @@ xd_status xd_autotune(xd_ctx* c, const xd_batch* b, const char* path, float* bes
     best.alpha = v.alpha;
     best.xb = x_bucket(v.X);
     best.lb = len_bucket(v.max_len);
+    best.sb = size_bucket(v.n_pairs);
     best.cfg = base;
     best.ms = 1e30f;
     auto consider = [&](const TierConfig& cand) -> xd_status {
@@ -1446,8 +1474,9 @@ xd_status xd_autotune(xd_ctx* c, const xd_batch* b, const char* path, float* bes
         FILE* f = std::fopen(path, "w");
         if (!f) return fail(c, XD_EINVAL, std::string("cannot write tuning table ") + path);
         std::fprintf(f, "# xdrop-gb300 tuning table: alpha (4 DNA, 20 protein), X bucket (0: X <= 15, 1: <= 30,\n"
-                        "# 2: more), length bucket (0: longest side <= 2048, 1: <= 20000, 2: more), chain of\n"
-                        "# register-level variants, queue chunk, fused grid and its role mix, measured ms\n");
+                        "# 2: more), length bucket (0: longest side <= 2048, 1: <= 20000, 2: more), size bucket\n"
+                        "# (0: < 8192 side extensions, 1: < 65536, 2: more), chain of register-level variants,\n"
+                        "# queue chunk, fused grid and its role mix, measured ms\n");
         for (const TuneEntry& t : table) std::fprintf(f, "%s\n", format_entry(t).c_str());
         std::fclose(f);
     }

@@ -24,15 +24,22 @@ THREADS = max(1, os.cpu_count() or 1)
 FIELDS = ("score", "h_ext", "v_ext", "flags", "cells")
 
 
-MODES = {"tiered": {}, "generic": {"XD_TIERS": "generic"}, "split": {"XD_FUSED": "0"}}
+# tiered: the default choice (batches this small take the latency chain, a warp per side);
+# throughput / split: the X-based chains of large batches, fused or one launch per level;
+# generic: every side in the generic tier
+MODES = {"tiered": {}, "generic": {"XD_TIERS": "generic"},
+         "throughput": {"XD_LATENCY_UNITS": "0"},
+         "split": {"XD_LATENCY_UNITS": "0", "XD_FUSED": "0"}}
+ENV_KEYS = ("XD_TIERS", "XD_FUSED", "XD_FUSED_PROT", "XD_LATENCY_UNITS", "XD_CHAIN", "XD_CHAIN_PROT",
+            "XD_CHAIN_SMALL")
 
 
-def _ctx(mode):
-    keys = ("XD_TIERS", "XD_FUSED")
+def _ctx(mode, env=None):
+    keys = ENV_KEYS
     old = {k: os.environ.get(k) for k in keys}
     for k in keys:
         os.environ.pop(k, None)
-    os.environ.update(MODES[mode])
+    os.environ.update(MODES[mode] if env is None else env)
     try:
         return xdrop.xd_create(0)
     finally:
@@ -43,7 +50,7 @@ def _ctx(mode):
                 os.environ[k] = v
 
 
-@pytest.fixture(scope="module", params=["tiered", "split", "generic"])
+@pytest.fixture(scope="module", params=["tiered", "throughput", "split", "generic"])
 def ctx(request):
     c = _ctx(request.param)
     yield c
@@ -167,6 +174,38 @@ def test_protein_shape(ctx):
 def test_uneven_restricted_shape(ctx, delta):
     b = synth.uneven(n_pairs=150, delta=delta)
     assert_parity(xdrop.extend_host(ctx, b), b)
+
+
+# Every compiled (lanes per side, slots per lane) variant, as a level of some chain, fused
+# and as separate launches, on a mix of narrow and wide bands (DNA ids: 0 G1C16, 1 G1C32,
+# 2 G4C16, 3 G8C16, 4 G16C16, 5 G32C16, 6 G32C32, 7 G4C32, 8 G8C32, 9 G16C32, 10 G4C8,
+# 11 G8C8, 12 G16C8, 13 G32C8).
+CHAINS_DNA = ["1,4,5,6", "0,2,4,6", "1,7,8,6", "1,3,5,6", "10,11,12,13,6", "0,3,9,6", "13,6", "2,4,6"]
+CHAINS_PROT = ["2,4,6", "0,2,4,6", "3,5,6", "11,13,6", "13,6"]
+
+
+@pytest.fixture(scope="module")
+def chain_batches():
+    rng = np.random.default_rng(808)
+    dna = [synth.dna_longread(n_pairs=200).with_params(X=X) for X in (10, 50)]
+    dna.append(synth.from_strings(random_pairs(rng, 150, "dna", 400), X=30))
+    prot = [synth.protein(n_pairs=500),
+            synth.from_strings(random_pairs(rng, 150, "protein", 300), alphabet="protein", gap=-2, X=80)]
+    return dna, prot
+
+
+@pytest.mark.parametrize("fused", ["1", "0"])
+@pytest.mark.parametrize("chain", CHAINS_DNA + ["p" + c for c in CHAINS_PROT])
+def test_every_variant_chain(chain_batches, chain, fused):
+    prot = chain.startswith("p")
+    env = {"XD_LATENCY_UNITS": "0", "XD_FUSED": fused, "XD_FUSED_PROT": fused}
+    env["XD_CHAIN_PROT" if prot else "XD_CHAIN"] = chain.lstrip("p")
+    c = _ctx("tiered", env)
+    try:
+        for b in chain_batches[1 if prot else 0]:
+            assert_parity(xdrop.extend_host(c, b), b)
+    finally:
+        xdrop.xd_destroy(c)
 
 
 def test_uneven_small_window_overflows(tiered):
