@@ -218,7 +218,8 @@ struct xd_ctx {
     uint32_t reserved_len = 0;
     cudaStream_t dev_stream = nullptr;
     bool generic_only = false;
-    TierConfig tiers{}, tiers_small_x{}, tiers_large_x{}, tiers_protein{}, tiers_latency{};
+    TierConfig tiers{}, tiers_small_x{}, tiers_large_x{}, tiers_protein{};
+    TierConfig tiers_latency{}, tiers_latency_mid{}, tiers_latency_prot{};
     uint32_t latency_units = 0;        // batches with fewer side extensions use tiers_latency
     std::vector<TuneEntry> tuned;      // autotuned configurations by (alphabet, X, length) bucket
     const TierConfig* force_tiers = nullptr;   // set while the autotuner times a candidate
@@ -438,13 +439,23 @@ void default_tiers(xd_ctx* c) {
     c->tiers_protein = t;
     set_chain(c->tiers_protein, {kG4C16, kG16C16, kG32C32});
     c->tiers_protein.fused = env_int("XD_FUSED_PROT", 0) != 0;   // separate launches measured faster
+    // small batches (measured on long-read and protein batches of 1,000 - 30,000 pairs):
+    // DNA below half the threshold 32 lanes x 16 slots, above it 16 x 8 first; protein 32 x 8
     c->tiers_latency = t;
     set_chain(c->tiers_latency, {kG32C16, kG32C32});
     c->tiers_latency.fused = false;
+    c->tiers_latency_mid = c->tiers_latency;
+    set_chain(c->tiers_latency_mid, {kG16C8, kG32C16, kG32C32});
+    c->tiers_latency_prot = c->tiers_latency;
+    set_chain(c->tiers_latency_prot, {kG32C8, kG32C32});
     c->latency_units = uint32_t(std::max(0, env_int("XD_LATENCY_UNITS", int(kLatencyUnits))));
     // overrides for experiments: comma-separated variant ids
     if (const char* ch = std::getenv("XD_CHAIN_PROT")) parse_chain(ch, c->tiers_protein);
-    if (const char* ch = std::getenv("XD_CHAIN_SMALL")) parse_chain(ch, c->tiers_latency);
+    if (const char* ch = std::getenv("XD_CHAIN_SMALL")) {
+        parse_chain(ch, c->tiers_latency);
+        parse_chain(ch, c->tiers_latency_mid);
+        parse_chain(ch, c->tiers_latency_prot);
+    }
     if (const char* ch = std::getenv("XD_CHAIN")) {
         TierConfig forced = t;
         if (parse_chain(ch, forced)) c->tiers = c->tiers_small_x = c->tiers_large_x = forced;
@@ -463,7 +474,11 @@ const TierConfig& tiers_for(const xd_ctx* c, const BatchView& b) {
     const int xb = x_bucket(b.X), lb = len_bucket(b.max_len), sb = size_bucket(b.n_pairs);
     for (const TuneEntry& t : c->tuned)
         if (t.alpha == b.alpha && t.xb == xb && t.lb == lb && t.sb == sb) return t.cfg;
-    if (uint64_t(b.n_pairs) * 2 < c->latency_units) return c->tiers_latency;
+    const uint64_t units = uint64_t(b.n_pairs) * 2;
+    if (units < c->latency_units) {
+        if (b.alpha == 20) return c->tiers_latency_prot;
+        return units < c->latency_units / 2 ? c->tiers_latency : c->tiers_latency_mid;
+    }
     if (b.alpha == 20) return c->tiers_protein;
     if (b.X <= 15) return c->tiers_small_x;
     if (b.X <= 30) return c->tiers;

@@ -79,15 +79,18 @@ __device__ __forceinline__ void stream_init(Stream& s, const uint32_t* store, ui
     s.nxt = ld_word(store, nw, s.word + dir);
 }
 
+// The next word is re-read on every call, by every lane at once: a load issued only by the
+// lanes that cross a word boundary would leave the register pending for the whole warp, and
+// the next lane to cross (usually a step later) would wait for it.  Re-read words hit L1.
 __device__ __forceinline__ uint32_t stream_next(Stream& s, const uint32_t* store, uint64_t nw) {
     const uint32_t c = (s.cur >> s.off) & 3u;
     s.off += 2 * s.dir;
     if (s.off < 0 || s.off > 30) {
         s.word += s.dir;
         s.cur = s.nxt;
-        s.nxt = ld_word(store, nw, s.word + s.dir);
         s.off &= 31;
     }
+    s.nxt = ld_word(store, nw, s.word + s.dir);
     return c;
 }
 
@@ -115,9 +118,9 @@ __device__ __forceinline__ uint32_t stream5_next(Stream5& s, const uint32_t* sto
     if (s.off < 0 || s.off > 25) {
         s.word += s.dir;
         s.cur = s.nxt;
-        s.nxt = ld_word(store, nw, s.word + s.dir);
         s.off = s.dir > 0 ? 0 : 25;
     }
+    s.nxt = ld_word(store, nw, s.word + s.dir);   // every call, as stream_next
     return c;
 }
 
@@ -404,29 +407,15 @@ __device__ __forceinline__ int group_step(SideState& s, Res<CG, A>& res, int32_t
     uint32_t lm;
     cells_of<CG, ODD, A>(P1, P2, upb, lfb, res, bm, thr, P.gap, tab, kmax, lm);
     s.cells += uint64_t(hi - lo + 1);
+    const bool any = lm != 0;
+    int32_t first = any ? sb + __ffs(lm) - 1 : INT32_MAX;
+    int32_t last = any ? sb + 31 - __clz(lm) : -1;
+    first = gmin<G>(first, gm);
+    if (first == INT32_MAX) return kDone;
+    last = gmax<G>(last, gm);
     const int32_t lv = kmax >> 6;
-    int32_t first, last, wmax, arg;
-    if constexpr (G == 1) {
-        if (lm == 0) return kDone;
-        first = __ffs(lm) - 1;
-        last = 31 - __clz(lm);
-        wmax = lv;
-        arg = ib + 63 - (kmax & 63);
-    } else {
-        // live range: the first / last lane with a live cell (one vote) gives the group's
-        // first / last live slot; best cell: the group maximum, then the lowest lane that
-        // holds it (one vote) gives its lowest slot
-        const int base = (threadIdx.x & 31) - gl;
-        uint32_t live_lanes = __ballot_sync(gm, lm != 0);
-        if constexpr (G < 32) live_lanes = (live_lanes >> base) & ((1u << G) - 1u);
-        if (live_lanes == 0) return kDone;
-        first = __shfl_sync(gm, sb + __ffs(lm) - 1, base + __ffs(live_lanes) - 1);
-        last = __shfl_sync(gm, sb + 31 - __clz(lm), base + 31 - __clz(live_lanes));
-        wmax = gmax<G>(lv, gm);
-        uint32_t best_lanes = __ballot_sync(gm, lv == wmax);
-        if constexpr (G < 32) best_lanes = (best_lanes >> base) & ((1u << G) - 1u);
-        arg = ib + __shfl_sync(gm, sb + (63 - (kmax & 63)), base + __ffs(best_lanes) - 1);
-    }
+    const int32_t wmax = gmax<G>(lv, gm);
+    const int32_t arg = ib + gmin<G>(lv == wmax ? sb + (63 - (kmax & 63)) : INT32_MAX, gm);
     s.L = ib + first;
     s.U = ib + last;
     if (wmax > s.T) {
