@@ -478,6 +478,8 @@ def main():
                     "discarded_cells_per_step": tim["discarded_cells"] / nb,
                     "escalations_per_step": tim["escalations"] / nb,
                     "window_shifts_per_step": tim["window_shifts"] / nb,
+                    "register_window_fill": (tim["register_band_cells"] / tim["register_slot_cells"]
+                                             if tim["register_slot_cells"] else None),
                     "serving": serving,
                     "clocks": clk}
             print(json.dumps(line), flush=True)

@@ -205,6 +205,8 @@ typedef struct {
     uint64_t discarded_cells;
     uint64_t launches;           /* kernels the library launched */
     uint64_t window_shifts;      /* register-window re-centrings */
+    uint64_t register_band_cells;   /* cells inside the band evaluated by the register levels */
+    uint64_t register_slot_cells;   /* window slots those levels evaluated (anti-diagonals x window) */
 } xd_timing;
 
 /* enable != 0 synchronises the context, clears the timing sums and records stage events

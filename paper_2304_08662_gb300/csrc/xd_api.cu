@@ -428,14 +428,21 @@ void default_tiers(xd_ctx* c) {
     for (int v : {kG4C8, kG8C8, kG16C8, kG32C8}) t.blocks_per_sm[v] = 4;
     t.chunk = std::max(1, env_int("XD_CHUNK", 1));
     t.fused = env_int("XD_FUSED", 1) != 0;
-    t.every1 = std::max(0, env_int("XD_EVERY1", 4));
-    t.every2 = std::max(0, env_int("XD_EVERY2", 16));
+    t.every1 = std::max(0, env_int("XD_EVERY1", 2));
+    t.every2 = std::max(0, env_int("XD_EVERY2", 8));
+    if (t.every1 == 1) t.every1 = 2;   // every warp in role 1 would leave the ordered units to nobody
+    if (t.every2 == 1) t.every2 = 2;
     t.fused_minb = env_int("XD_FUSED_MINB", 2);
+    t.long_permille = std::max(0, std::min(250, env_int("XD_LONG_PERMILLE", 5)));
     set_chain(t, {kG1C32, kG16C16, kG32C16, kG32C32});
     c->tiers_small_x = t;
     set_chain(c->tiers_small_x, {kG1C32, kG16C16, kG32C16, kG32C32});
     c->tiers_large_x = t;
     set_chain(c->tiers_large_x, {kG4C16, kG16C16, kG32C32});
+    c->tiers_large_x.every1 = std::max(0, env_int("XD_EVERY1", 4));   // measured: 4 / 16 for this chain
+    c->tiers_large_x.every2 = std::max(0, env_int("XD_EVERY2", 16));
+    if (c->tiers_large_x.every1 == 1) c->tiers_large_x.every1 = 2;
+    if (c->tiers_large_x.every2 == 1) c->tiers_large_x.every2 = 2;
     c->tiers_protein = t;
     set_chain(c->tiers_protein, {kG4C16, kG16C16, kG32C32});
     c->tiers_protein.fused = env_int("XD_FUSED_PROT", 0) != 0;   // separate launches measured faster
@@ -892,8 +899,8 @@ bool parse_entry(const std::string& line, const TierConfig& base, TuneEntry& out
             else if (k == "sb") out.sb = x;
             else if (k == "chunk") out.cfg.chunk = std::max(1, std::min(x, 64));
             else if (k == "fused") out.cfg.fused = x != 0;
-            else if (k == "every1") out.cfg.every1 = std::max(0, x);
-            else if (k == "every2") out.cfg.every2 = std::max(0, x);
+            else if (k == "every1") out.cfg.every1 = x == 1 ? 2 : std::max(0, x);   // 1: no warp in role 0
+            else if (k == "every2") out.cfg.every2 = x == 1 ? 2 : std::max(0, x);
             else if (k == "minb") out.cfg.fused_minb = x;
             else if (k == "ms") out.ms = float(std::atof(v.c_str()));
         }
@@ -1338,6 +1345,8 @@ xd_status xd_get_timing(xd_ctx* c, xd_timing* out) {
     out->escalations = d[3];
     out->discarded_cells = d[7];
     out->window_shifts = d[8];
+    out->register_band_cells = d[9];
+    out->register_slot_cells = d[10];
     out->launches = c->launches - c->launches_at_enable;
     return XD_OK;
 }

@@ -39,7 +39,8 @@ struct Problem {
     uint32_t* err;              // validation / wait error word
     unsigned long long* stats;  // per batch: [0..2] units finished per stage, [3] escalations,
                                 // [4..6] cells per stage, [7] cells discarded by escalation,
-                                // [8] window re-centrings.  Stage 0: the first register
+                                // [8] window re-centrings, [9] / [10] in-band cells and
+                                // slots evaluated by the register levels.  Stage 0: the first register
                                 // launch (fused grid or level 0); 1: later register levels
                                 // and the band tier; 2: the generic tier
     int32_t alpha;              // 4 or 20

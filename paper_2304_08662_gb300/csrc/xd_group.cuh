@@ -27,6 +27,7 @@
 // This header holds the templates; xd_tiers.cu instantiates the DNA kernels (A = 4) and
 // xd_tiers_prot.cu the protein ones (A = 20).
 #pragma once
+#include <algorithm>
 #include <cstdint>
 #include <cuda_runtime.h>
 #include "xd_device.cuh"
@@ -79,18 +80,15 @@ __device__ __forceinline__ void stream_init(Stream& s, const uint32_t* store, ui
     s.nxt = ld_word(store, nw, s.word + dir);
 }
 
-// The next word is re-read on every call, by every lane at once: a load issued only by the
-// lanes that cross a word boundary would leave the register pending for the whole warp, and
-// the next lane to cross (usually a step later) would wait for it.  Re-read words hit L1.
 __device__ __forceinline__ uint32_t stream_next(Stream& s, const uint32_t* store, uint64_t nw) {
     const uint32_t c = (s.cur >> s.off) & 3u;
     s.off += 2 * s.dir;
     if (s.off < 0 || s.off > 30) {
         s.word += s.dir;
         s.cur = s.nxt;
+        s.nxt = ld_word(store, nw, s.word + s.dir);
         s.off &= 31;
     }
-    s.nxt = ld_word(store, nw, s.word + s.dir);
     return c;
 }
 
@@ -120,7 +118,10 @@ __device__ __forceinline__ uint32_t stream5_next(Stream5& s, const uint32_t* sto
         s.cur = s.nxt;
         s.off = s.dir > 0 ? 0 : 25;
     }
-    s.nxt = ld_word(store, nw, s.word + s.dir);   // every call, as stream_next
+    // the next word is re-read on every call, by every lane at once: a load issued only by
+    // the lanes that cross a word boundary would leave the register pending for the whole
+    // warp until it returns (re-read words hit L1; measured faster for protein, not for DNA)
+    s.nxt = ld_word(store, nw, s.word + s.dir);
     return c;
 }
 
@@ -583,6 +584,8 @@ __device__ __forceinline__ void group_loop(const Problem& P, const Queues& Q, co
     Res<CG, A> res;
     uint32_t uidx = 0, pair = 0, next = 0, end = 0;
     bool active = false, skip_odd = false;
+    int32_t d_start = 0;
+    uint64_t cells_start = 0;
     for (;;) {
         if (!active) {
             bool got = false;
@@ -618,6 +621,8 @@ __device__ __forceinline__ void group_loop(const Problem& P, const Queues& Q, co
             }
             skip_odd = (s.d & 1) == 0;   // a side continued on an even anti-diagonal
             active = true;
+            d_start = s.d;
+            cells_start = s.cells;
         }
         int r = kCont;
         if (!skip_odd) r = group_step<G, CG, true, A>(s, res, R0, R1, P, tab, gl, gm, gsm);
@@ -625,6 +630,11 @@ __device__ __forceinline__ void group_loop(const Problem& P, const Queues& Q, co
         if (r == kCont) r = group_step<G, CG, false, A>(s, res, R1, R0, P, tab, gl, gm, gsm);
         if (r == kCont) continue;
         active = false;
+        if (gl == 0) {
+            // window fill of this level: in-band cells against the slots evaluated
+            atomicAdd(&P.stats[9], (unsigned long long)(s.cells - cells_start));
+            atomicAdd(&P.stats[10], (unsigned long long)(s.d + 1 - d_start) * (unsigned long long)W);
+        }
         if (r == kDone) {
             if (gl == 0) {
                 write_side(P.results, pair, s.side, s.best, uint32_t(s.bi), uint32_t(s.bj), s.flags, s.cells);
@@ -690,8 +700,10 @@ __global__ void __launch_bounds__(128, MINB) k_group(Problem P, Queues Q, int in
 struct RolePlan {
     int every1, every2;         // warp gw starts in role 2 if gw % every2 == every2 - 1,
                                 // else in role 1 if gw % every1 == 0, else in role 0
-    uint32_t producers0;        // warps that start in role 0
-    uint32_t producers1;        // warps that start in role 0 or 1
+    uint32_t producers0;        // warps that run role 0
+    uint32_t producers1;        // warps that run role 0 or 1
+    uint32_t n_long;            // units at the head of the cost order taken by the long role
+    uint32_t long_warps;        // warps gw < long_warps start in the long role, then role 0
 };
 
 __host__ __device__ __forceinline__ int start_role(uint32_t gw, int every1, int every2) {
@@ -720,16 +732,32 @@ __device__ __forceinline__ void signal_done(uint32_t* done) {
     __syncwarp();
 }
 
-template <int G0, int C0, int G1, int C1, int G2, int C2, int MINB, int A>
+// GL x CL (GL = 0: none) is the long role: the first R.long_warps warps take the R.n_long
+// longest sides (the head of the cost order) with GL-lane groups, whose anti-diagonals take
+// less time than a single lane's, so that the longest serial chains do not set the
+// makespan; those warps then join role 0 on the rest of the order.
+template <int G0, int C0, int G1, int C1, int G2, int C2, int MINB, int A, int GL, int CL>
 __global__ void __launch_bounds__(128, MINB) k_fused(Problem P, Queues Q, RolePlan R, int chunk) {
     extern __shared__ __align__(16) int32_t group_smem[];
     build_table<A>(group_smem, P);
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     uint32_t* done0 = &Q.ctr[1 + 2 * kLevels];
     uint32_t* done1 = &Q.ctr[2 + 2 * kLevels];
-    const int role = start_role(gw, R.every1, R.every2);
+    const bool long_role = GL > 0 && gw < R.long_warps;
+    const int role = long_role ? 0 : start_role(gw, R.every1, R.every2);
+    if constexpr (GL > 0) {
+        if (long_role) {
+            Source SL = static_source(Q, -1);
+            SL.pull = &Q.ctr[kLongPull];
+            SL.n = R.n_long;
+            group_loop<GL, CL, A>(P, Q, SL, 0, 1, group_smem, 0);
+        }
+    }
     if (role == 0) {
-        group_loop<G0, C0, A>(P, Q, static_source(Q, -1), 0, chunk, group_smem, 0);
+        Source S0 = static_source(Q, -1);
+        S0.list = Q.order + R.n_long;
+        S0.n = Q.n_units - R.n_long;
+        group_loop<G0, C0, A>(P, Q, S0, 0, chunk, group_smem, 0);
         signal_done(done0);
     }
     if (role <= 1) {
@@ -747,6 +775,9 @@ static cudaError_t launch_group(const Problem& P, const Queues& Q, int in_q, int
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_group<G, CG, MINB, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (e != cudaSuccess) return e;
+        // the largest shared-memory carveout, so that the blocks the registers allow fit
+        e = cudaFuncSetAttribute(k_group<G, CG, MINB, A>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        if (e != cudaSuccess) return e;
         attr = true;
     }
     k_group<G, CG, MINB, A><<<blocks, 128, smem, st>>>(P, Q, in_q, out_q, chunk);
@@ -758,16 +789,19 @@ constexpr size_t group_smem_bytes() {
     return (size_t(kLutInts) + size_t(128 / G) * 2 * G * CG) * sizeof(int32_t);
 }
 
-template <int G0, int C0, int G1, int C1, int G2, int C2, int MINB, int A>
+template <int G0, int C0, int G1, int C1, int G2, int C2, int MINB, int A, int GL = 0, int CL = 4>
 static cudaError_t launch_fused(const Problem& P, const Queues& Q, const TierConfig& cfg, int n_sm,
                                 cudaStream_t st) {
     size_t smem = group_smem_bytes<G0, C0>();
     if (group_smem_bytes<G1, C1>() > smem) smem = group_smem_bytes<G1, C1>();
     if (group_smem_bytes<G2, C2>() > smem) smem = group_smem_bytes<G2, C2>();
-    auto fn = k_fused<G0, C0, G1, C1, G2, C2, MINB, A>;
+    if (GL > 0 && group_smem_bytes<(GL > 0 ? GL : 1), CL>() > smem) smem = group_smem_bytes<(GL > 0 ? GL : 1), CL>();
+    auto fn = k_fused<G0, C0, G1, C1, G2, C2, MINB, A, GL, CL>;
     static int occ = 0;
     if (occ == 0) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         if (e != cudaSuccess) return e;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 128, smem);
         if (e != cudaSuccess) return e;
@@ -776,12 +810,17 @@ static cudaError_t launch_fused(const Problem& P, const Queues& Q, const TierCon
     // every block must be resident at once: consumers wait for producers of the same grid
     const int blocks = n_sm * occ;
     const uint32_t n_warps = uint32_t(blocks) * 4;
-    RolePlan R{cfg.every1, cfg.every2, 0, 0};
+    RolePlan R{cfg.every1, cfg.every2, 0, 0, 0, 0};
+    if (GL > 0 && cfg.long_permille > 0) {
+        R.n_long = uint32_t(uint64_t(Q.n_units) * uint32_t(cfg.long_permille) / 1000u);
+        R.long_warps = std::min(R.n_long, n_warps / 4);   // at most a quarter of the grid
+    }
     for (uint32_t w = 0; w < n_warps; w++) {
-        const int r = start_role(w, R.every1, R.every2);
+        const int r = w < R.long_warps ? 0 : start_role(w, R.every1, R.every2);
         R.producers0 += r == 0;
         R.producers1 += r <= 1;
     }
+    if (R.producers0 == 0) return cudaErrorInvalidValue;   // nobody would take the ordered units
     Problem p = P;
     Queues q = Q;
     int ch = cfg.chunk;

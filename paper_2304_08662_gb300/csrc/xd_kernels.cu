@@ -61,13 +61,18 @@ __global__ void k_pack_prot(const uint8_t* __restrict__ codes, uint64_t n_codes,
 }
 
 // ---------------------------------------------------------------------------------------
-// a2: work units.  Each pair gives a right and a left unit (Sec. 4.1.2).  Cost proxy is
-// the quadratic maximum work m * n of Sec. 4.2; units are bucketed by its log2 so that
-// the most expensive run first.  Invalid tuples raise kErrSeed and become empty units;
+// a2: work units.  Each pair gives a right and a left unit (Sec. 4.1.2).  Units run longest
+// first.  The cost proxy is the anti-diagonal count rather than the quadratic maximum work
+// m * n of Sec. 4.2: an X-Drop side's work is its band times its anti-diagonals, and its
+// latency (the serial chain that bounds a batch's makespan) is its anti-diagonal count,
+// about 2 min(m, n) when the alignment runs to the end of the shorter sequence.  Buckets are
+// quarter octaves of min(m, n) + 1.  Invalid tuples raise kErrSeed and become empty units;
 // sides whose scores could leave the exact range raise kErrRange and also become empty.
 __device__ __forceinline__ uint32_t cost_bucket(uint32_t m, uint32_t n) {
-    uint64_t c = uint64_t(m) * n + 1;
-    return 63u - uint32_t(__clzll(c));        // 0 .. 63
+    const uint32_t s = min(m, n) + 1u;
+    const uint32_t lg = 31u - uint32_t(__clz(s));               // floor(log2 s)
+    const uint32_t frac = lg >= 2 ? (s >> (lg - 2)) & 3u : 0u;  // next two bits
+    return min(4u * lg + frac, 63u);                             // 0 .. 63
 }
 
 __global__ void k_units(const xd_pair* __restrict__ pairs, uint32_t n_pairs,

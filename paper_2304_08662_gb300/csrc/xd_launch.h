@@ -5,7 +5,10 @@
 
 namespace xd {
 
-constexpr int kNumCtr = 4 + 2 * kLevels;   // then: producer warps finished (two), record counter
+// queue counters: [0] order pull, [1 + 2k] / [2 + 2k] length / pull of q[k], then producer
+// warps finished (two), the record counter, and the pull counter of the long-side head
+constexpr int kNumCtr = 5 + 2 * kLevels;
+constexpr int kLongPull = 4 + 2 * kLevels;
 
 cudaError_t launch_pack(int alpha, const uint8_t* codes, uint64_t n_codes, uint32_t* store,
                         uint32_t* err, int n_sm, cudaStream_t st);
@@ -43,6 +46,8 @@ struct TierConfig {
     bool fused;                         // fuse levels 0-2 into one persistent grid
     int every1, every2;                 // fused grid: warps starting in role 1 / role 2
     int fused_minb;                     // fused grid register budget: resident blocks per SM
+    int long_permille;                  // fused grid: head of the cost order (per mille of the
+                                        // units) run first by 32-lane groups (0 = none)
 };
 
 // Runs register level `level` of the chain: pulls the cost-ordered list (level 0) or

@@ -56,7 +56,8 @@ class xd_timing(ctypes.Structure):
                 ("tier_ms", ctypes.c_float * 3), ("totals_ms", ctypes.c_float), ("total_ms", ctypes.c_float),
                 ("tier_units", ctypes.c_uint64 * 3), ("tier_cells", ctypes.c_uint64 * 3),
                 ("escalations", ctypes.c_uint64), ("discarded_cells", ctypes.c_uint64),
-                ("launches", ctypes.c_uint64), ("window_shifts", ctypes.c_uint64)]
+                ("launches", ctypes.c_uint64), ("window_shifts", ctypes.c_uint64),
+                ("register_band_cells", ctypes.c_uint64), ("register_slot_cells", ctypes.c_uint64)]
 
 
 assert ctypes.sizeof(xd_batch) == 88 and RESULT_DTYPE.itemsize == 56 and ctypes.sizeof(xd_config) == 40
@@ -224,7 +225,8 @@ def xd_get_timing(ctx):
             "tier_ms": list(t.tier_ms), "totals_ms": t.totals_ms, "total_ms": t.total_ms,
             "tier_units": list(t.tier_units), "tier_cells": list(t.tier_cells),
             "escalations": t.escalations, "discarded_cells": t.discarded_cells,
-            "launches": t.launches, "window_shifts": t.window_shifts}
+            "launches": t.launches, "window_shifts": t.window_shifts,
+            "register_band_cells": t.register_band_cells, "register_slot_cells": t.register_slot_cells}
 
 
 PROBE_OPS = {"add": 0, "max": 1, "dpx_addmax": 2, "dpx_max3": 3, "lop3": 4, "imad": 5,
