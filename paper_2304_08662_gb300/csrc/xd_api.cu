@@ -433,7 +433,7 @@ void default_tiers(xd_ctx* c) {
     if (t.every1 == 1) t.every1 = 2;   // every warp in role 1 would leave the ordered units to nobody
     if (t.every2 == 1) t.every2 = 2;
     t.fused_minb = env_int("XD_FUSED_MINB", 2);
-    t.long_permille = std::max(0, std::min(250, env_int("XD_LONG_PERMILLE", 5)));
+    t.long_permille = std::max(0, std::min(250, env_int("XD_LONG_PERMILLE", 0)));
     set_chain(t, {kG1C32, kG16C16, kG32C16, kG32C32});
     c->tiers_small_x = t;
     set_chain(c->tiers_small_x, {kG1C32, kG16C16, kG32C16, kG32C32});
@@ -858,9 +858,9 @@ std::string format_entry(const TuneEntry& t) {
     for (int k = 0; k < t.cfg.n_levels; k++) chain += (k ? "," : "") + std::to_string(t.cfg.variant[k]);
     char buf[256];
     std::snprintf(buf, sizeof(buf),
-                  "alpha=%d xb=%d lb=%d sb=%d chain=%s chunk=%d fused=%d every1=%d every2=%d minb=%d ms=%.4f",
+                  "alpha=%d xb=%d lb=%d sb=%d chain=%s chunk=%d fused=%d every1=%d every2=%d minb=%d long=%d ms=%.4f",
                   t.alpha, t.xb, t.lb, t.sb, chain.c_str(), t.cfg.chunk, t.cfg.fused ? 1 : 0, t.cfg.every1,
-                  t.cfg.every2, t.cfg.fused_minb, double(t.ms));
+                  t.cfg.every2, t.cfg.fused_minb, t.cfg.long_permille, double(t.ms));
     return buf;
 }
 
@@ -902,6 +902,7 @@ bool parse_entry(const std::string& line, const TierConfig& base, TuneEntry& out
             else if (k == "every1") out.cfg.every1 = x == 1 ? 2 : std::max(0, x);   // 1: no warp in role 0
             else if (k == "every2") out.cfg.every2 = x == 1 ? 2 : std::max(0, x);
             else if (k == "minb") out.cfg.fused_minb = x;
+            else if (k == "long") out.cfg.long_permille = std::max(0, std::min(250, x));
             else if (k == "ms") out.ms = float(std::atof(v.c_str()));
         }
     }
@@ -1473,7 +1474,13 @@ xd_status xd_autotune(xd_ctx* c, const xd_batch* b, const char* path, float* bes
             if (r == XD_OK) r = consider(cand);
         }
     if (r == XD_OK && best.cfg.fused)
-        for (auto mix : {std::pair<int, int>{2, 8}, {8, 32}, {4, 8}, {8, 16}, {0, 16}, {4, 0}, {4, 32}}) {
+        for (int lp : {2, 5, 10}) {
+            TierConfig cand = best.cfg;
+            cand.long_permille = lp;
+            if (r == XD_OK) r = consider(cand);
+        }
+    if (r == XD_OK && best.cfg.fused)
+        for (auto mix : {std::pair<int, int>{2, 8}, {4, 16}, {8, 32}, {4, 8}, {8, 16}, {0, 16}, {4, 0}, {3, 6}}) {
             TierConfig cand = best.cfg;
             cand.every1 = mix.first;
             cand.every2 = mix.second;

@@ -436,6 +436,13 @@ __device__ __forceinline__ int group_step(SideState& s, Res<CG, A>& res, int32_t
 // atomic counter and published by storing the unit index over the kNoUnit sentinel.
 constexpr uint32_t kNoUnit = 0xffffffffu;
 constexpr uint32_t kMaxSpin = 1u << 24;
+constexpr uint64_t kWaitLimitNs = 10ull * 1000 * 1000 * 1000;   // 10 s without progress
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 struct Source {
     const uint32_t* list;
@@ -468,9 +475,17 @@ __device__ __forceinline__ bool next_unit(const Source& S, int gl, int lane, uin
     uint32_t u = kNoUnit;
     int got = 0;
     if (gl == 0) {
+        // Poll with plain coherent loads and exponential back-off (an idle consumer must not
+        // load L2 with atomics).  The wait gives up, raising kErrWait, once neither the
+        // queue length nor the finished-producer count has changed for kWaitLimitNs.
+        const volatile uint32_t* reserve = S.reserve;
+        const volatile uint32_t* done = S.producers_done;
         const uint32_t ticket = atomicAdd(S.pull, 1u);
-        for (uint32_t it = 0;; it++) {
-            if (ticket < atomicAdd(S.reserve, 0u)) {
+        uint32_t last_res = 0xffffffffu, last_done = 0xffffffffu, pause = 128;
+        uint64_t t_change = globaltimer_ns();
+        for (;;) {
+            const uint32_t res = *reserve;
+            if (ticket < res) {
                 const volatile uint32_t* slot = S.list + ticket;
                 uint32_t v = *slot;
                 for (uint32_t w = 0; v == kNoUnit && w < kMaxSpin; w++) {
@@ -481,16 +496,24 @@ __device__ __forceinline__ bool next_unit(const Source& S, int gl, int lane, uin
                 else { u = v; got = 1; }
                 break;
             }
-            if (atomicAdd(S.producers_done, 0u) >= S.n_producers) {
+            const uint32_t fin = *done;
+            if (fin >= S.n_producers) {
                 __threadfence();
-                if (ticket < atomicAdd(S.reserve, 0u)) continue;   // a final push landed meanwhile
+                if (ticket < *reserve) continue;   // a final push landed meanwhile
                 break;
             }
-            if (it >= kMaxSpin) {
+            const uint64_t now = globaltimer_ns();
+            if (res != last_res || fin != last_done) {
+                last_res = res;
+                last_done = fin;
+                t_change = now;
+                pause = 128;
+            } else if (now - t_change > kWaitLimitNs) {
                 atomicOr(err, kErrWait);
                 break;
             }
-            __nanosleep(256);
+            __nanosleep(pause);
+            pause = min(pause * 2u, 8192u);
         }
     }
     if (G > 1) {
@@ -570,15 +593,19 @@ __device__ __forceinline__ bool load_record(const Problem& P, uint32_t ri, SideS
 // Runs side extensions from S with groups of G lanes until S is exhausted; overflows go to
 // q[out_q], carrying an escalation record when the next level is a register level.
 // gsm_block: the block's shared rows (2W ints per group).
+// smem: the block's similarity table, then one shift area of warp_ints ints per warp (at
+// least 64 * CG: 2W ints for each of the warp's 32 / G groups).  The areas belong to warps,
+// not to groups, so that warps of one block may run groups of different shapes at the same
+// time (the roles of the fused grid) without sharing shift buffers.
 template <int G, int CG, int A>
 __device__ __forceinline__ void group_loop(const Problem& P, const Queues& Q, const Source& S, int out_q,
-                                           int chunk, int32_t* smem, int stage) {
+                                           int chunk, int32_t* smem, int stage, int warp_ints) {
     constexpr int W = G * CG;
     const int lane = threadIdx.x & 31;
     const int gl = lane % G;
     const uint32_t gm = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane - gl));
     const int32_t* tab = smem;
-    int32_t* gsm = smem + kLutInts + (threadIdx.x / G) * 2 * W;
+    int32_t* gsm = smem + kLutInts + (threadIdx.x >> 5) * warp_ints + ((threadIdx.x & 31) / G) * 2 * W;
     int32_t R0[CG], R1[CG];
     SideState s{};
     Res<CG, A> res;
@@ -686,7 +713,7 @@ template <int G, int CG, int MINB, int A>
 __global__ void __launch_bounds__(128, MINB) k_group(Problem P, Queues Q, int in_q, int out_q, int chunk) {
     extern __shared__ __align__(16) int32_t group_smem[];
     build_table<A>(group_smem, P);
-    group_loop<G, CG, A>(P, Q, static_source(Q, in_q), out_q, chunk, group_smem, in_q < 0 ? 0 : 1);
+    group_loop<G, CG, A>(P, Q, static_source(Q, in_q), out_q, chunk, group_smem, in_q < 0 ? 0 : 1, 64 * CG);
 }
 
 // The first register levels fused into one persistent, cooperatively launched grid.
@@ -732,12 +759,22 @@ __device__ __forceinline__ void signal_done(uint32_t* done) {
     __syncwarp();
 }
 
+// Shift-area ints per warp of a fused grid: 64 x the largest slots per lane of its roles.
+template <int C0, int C1, int C2, int CL>
+__host__ __device__ constexpr int fused_warp_ints() {
+    int c = C0 > C1 ? C0 : C1;
+    c = c > C2 ? c : C2;
+    c = c > CL ? c : CL;
+    return 64 * c;
+}
+
 // GL x CL (GL = 0: none) is the long role: the first R.long_warps warps take the R.n_long
 // longest sides (the head of the cost order) with GL-lane groups, whose anti-diagonals take
 // less time than a single lane's, so that the longest serial chains do not set the
 // makespan; those warps then join role 0 on the rest of the order.
 template <int G0, int C0, int G1, int C1, int G2, int C2, int MINB, int A, int GL, int CL>
 __global__ void __launch_bounds__(128, MINB) k_fused(Problem P, Queues Q, RolePlan R, int chunk) {
+    constexpr int kWarpInts = fused_warp_ints<C0, C1, C2, CL>();
     extern __shared__ __align__(16) int32_t group_smem[];
     build_table<A>(group_smem, P);
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -750,21 +787,21 @@ __global__ void __launch_bounds__(128, MINB) k_fused(Problem P, Queues Q, RolePl
             Source SL = static_source(Q, -1);
             SL.pull = &Q.ctr[kLongPull];
             SL.n = R.n_long;
-            group_loop<GL, CL, A>(P, Q, SL, 0, 1, group_smem, 0);
+            group_loop<GL, CL, A>(P, Q, SL, 0, 1, group_smem, 0, kWarpInts);
         }
     }
     if (role == 0) {
         Source S0 = static_source(Q, -1);
         S0.list = Q.order + R.n_long;
         S0.n = Q.n_units - R.n_long;
-        group_loop<G0, C0, A>(P, Q, S0, 0, chunk, group_smem, 0);
+        group_loop<G0, C0, A>(P, Q, S0, 0, chunk, group_smem, 0, kWarpInts);
         signal_done(done0);
     }
     if (role <= 1) {
-        group_loop<G1, C1, A>(P, Q, live_source(Q, 0, done0, R.producers0), 1, 1, group_smem, 0);
+        group_loop<G1, C1, A>(P, Q, live_source(Q, 0, done0, R.producers0), 1, 1, group_smem, 0, kWarpInts);
         signal_done(done1);
     }
-    group_loop<G2, C2, A>(P, Q, live_source(Q, 1, done1, R.producers1), 2, 1, group_smem, 0);
+    group_loop<G2, C2, A>(P, Q, live_source(Q, 1, done1, R.producers1), 2, 1, group_smem, 0, kWarpInts);
 }
 
 template <int G, int CG, int MINB, int A>
@@ -792,11 +829,9 @@ constexpr size_t group_smem_bytes() {
 template <int G0, int C0, int G1, int C1, int G2, int C2, int MINB, int A, int GL = 0, int CL = 4>
 static cudaError_t launch_fused(const Problem& P, const Queues& Q, const TierConfig& cfg, int n_sm,
                                 cudaStream_t st) {
-    size_t smem = group_smem_bytes<G0, C0>();
-    if (group_smem_bytes<G1, C1>() > smem) smem = group_smem_bytes<G1, C1>();
-    if (group_smem_bytes<G2, C2>() > smem) smem = group_smem_bytes<G2, C2>();
-    if (GL > 0 && group_smem_bytes<(GL > 0 ? GL : 1), CL>() > smem) smem = group_smem_bytes<(GL > 0 ? GL : 1), CL>();
-    auto fn = k_fused<G0, C0, G1, C1, G2, C2, MINB, A, GL, CL>;
+    constexpr int kCL = (GL > 0) ? CL : 4;
+    const size_t smem = (size_t(kLutInts) + 4 * size_t(fused_warp_ints<C0, C1, C2, kCL>())) * sizeof(int32_t);
+    auto fn = k_fused<G0, C0, G1, C1, G2, C2, MINB, A, GL, kCL>;
     static int occ = 0;
     if (occ == 0) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));

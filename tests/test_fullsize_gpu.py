@@ -122,3 +122,37 @@ def test_full_size_uneven_restricted(ctx, uneven, uneven_unrestricted, delta):
         for fld in FIELDS:
             assert np.array_equal(got[side][fld][clear], uneven_unrestricted[side][fld][clear]), (side, fld)
     _sampled_parity(got, b, 100, seed=33 + delta)
+
+
+def _ctx_env(env):
+    keys = ("XD_FUSED", "XD_FUSED_PROT", "XD_EVERY1", "XD_EVERY2", "XD_LONG_PERMILLE")
+    old = {k: os.environ.get(k) for k in keys}
+    for k in keys:
+        os.environ.pop(k, None)
+    os.environ.update(env)
+    try:
+        return xdrop.xd_create(0)
+    finally:
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+@pytest.mark.parametrize("X", [10, 20, 50])
+def test_full_size_fused_grid_equals_level_launches(X):
+    """Every one of the 100,000 long-read pairs: the persistent grid whose warps run
+    different group shapes at once (and the long-side role) must give exactly the results of
+    one launch per register level."""
+    b = synth.dna_longread().with_params(X=X)
+    fused = _ctx_env({"XD_EVERY1": "2", "XD_EVERY2": "4", "XD_LONG_PERMILLE": "5"})
+    split = _ctx_env({"XD_FUSED": "0"})
+    try:
+        a = _run_device(fused, b)
+        c = _run_device(split, b)
+    finally:
+        xdrop.xd_destroy(fused)
+        xdrop.xd_destroy(split)
+    diff = np.nonzero((a.view(np.uint8).reshape(len(a), -1) != c.view(np.uint8).reshape(len(c), -1)).any(axis=1))[0]
+    assert diff.size == 0, f"{diff.size} pairs differ, first {diff[:10].tolist()}"
