@@ -428,8 +428,8 @@ void default_tiers(xd_ctx* c) {
     for (int v : {kG4C8, kG8C8, kG16C8, kG32C8}) t.blocks_per_sm[v] = 4;
     t.chunk = std::max(1, env_int("XD_CHUNK", 1));
     t.fused = env_int("XD_FUSED", 1) != 0;
-    t.every1 = std::max(0, env_int("XD_EVERY1", 2));
-    t.every2 = std::max(0, env_int("XD_EVERY2", 8));
+    t.every1 = std::max(0, env_int("XD_EVERY1", 8));
+    t.every2 = std::max(0, env_int("XD_EVERY2", 32));
     if (t.every1 == 1) t.every1 = 2;   // every warp in role 1 would leave the ordered units to nobody
     if (t.every2 == 1) t.every2 = 2;
     t.fused_minb = env_int("XD_FUSED_MINB", 2);

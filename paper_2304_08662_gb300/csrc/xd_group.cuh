@@ -720,7 +720,8 @@ __global__ void __launch_bounds__(128, MINB) k_group(Problem P, Queues Q, int in
 // Each warp walks the role sequence 0 -> 1 -> 2: role 0 runs the cost-ordered units with
 // groups of G0 lanes and appends overflows to the live queue q[0]; role 1 consumes q[0]
 // with groups of G1 lanes and appends its overflows to the live queue q[1]; role 2
-// consumes q[1] with groups of G2 lanes, overflows go to q[2] for the later launches.
+// consumes q[1] with groups of G2 lanes, overflows go to q[2] for the later register
+// launches, or to the band tier when the chain has no level after the grid.
 // Some warps start directly in role 1 or 2, so wider sides begin while narrower levels
 // still run.  A warp that leaves role 0 (1) counts itself in done[0] (done[1]); consumers
 // stop once their queue is drained and all its producers have counted themselves.
@@ -731,6 +732,8 @@ struct RolePlan {
     uint32_t producers1;        // warps that run role 0 or 1
     uint32_t n_long;            // units at the head of the cost order taken by the long role
     uint32_t long_warps;        // warps gw < long_warps start in the long role, then role 0
+    int out2;                   // queue of role 2's overflows: q[2] when later register levels
+                                // follow the grid, else the band tier's queue
 };
 
 __host__ __device__ __forceinline__ int start_role(uint32_t gw, int every1, int every2) {
@@ -801,7 +804,7 @@ __global__ void __launch_bounds__(128, MINB) k_fused(Problem P, Queues Q, RolePl
         group_loop<G1, C1, A>(P, Q, live_source(Q, 0, done0, R.producers0), 1, 1, group_smem, 0, kWarpInts);
         signal_done(done1);
     }
-    group_loop<G2, C2, A>(P, Q, live_source(Q, 1, done1, R.producers1), 2, 1, group_smem, 0, kWarpInts);
+    group_loop<G2, C2, A>(P, Q, live_source(Q, 1, done1, R.producers1), R.out2, 1, group_smem, 0, kWarpInts);
 }
 
 template <int G, int CG, int MINB, int A>
@@ -845,7 +848,7 @@ static cudaError_t launch_fused(const Problem& P, const Queues& Q, const TierCon
     // every block must be resident at once: consumers wait for producers of the same grid
     const int blocks = n_sm * occ;
     const uint32_t n_warps = uint32_t(blocks) * 4;
-    RolePlan R{cfg.every1, cfg.every2, 0, 0, 0, 0};
+    RolePlan R{cfg.every1, cfg.every2, 0, 0, 0, 0, cfg.n_levels > 3 ? 2 : kBandQ};
     if (GL > 0 && cfg.long_permille > 0) {
         R.n_long = uint32_t(uint64_t(Q.n_units) * uint32_t(cfg.long_permille) / 1000u);
         R.long_warps = std::min(R.n_long, n_warps / 4);   // at most a quarter of the grid

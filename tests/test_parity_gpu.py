@@ -189,8 +189,12 @@ def chain_batches():
     rng = np.random.default_rng(808)
     dna = [synth.dna_longread(n_pairs=200).with_params(X=X) for X in (10, 50)]
     dna.append(synth.from_strings(random_pairs(rng, 150, "dna", 400), X=30))
+    # bands wider than every register window (X = infinity): these sides pass through all
+    # levels to the band tier
+    dna.append(synth.from_strings(random_pairs(rng, 12, "dna", 1600), X=X_INF))
     prot = [synth.protein(n_pairs=500),
-            synth.from_strings(random_pairs(rng, 150, "protein", 300), alphabet="protein", gap=-2, X=80)]
+            synth.from_strings(random_pairs(rng, 150, "protein", 300), alphabet="protein", gap=-2, X=80),
+            synth.from_strings(random_pairs(rng, 10, "protein", 1400), alphabet="protein", gap=-2, X=X_INF)]
     return dna, prot
 
 
