@@ -250,22 +250,32 @@ __global__ void __launch_bounds__(128) k_generic(Problem P, Queues Q, int32_t* s
 
 
 // ---------------------------------------------------------------------------------------
-// Band tier: one warp per side extension, the two previous anti-diagonals in a shared
-// memory ring of kBandW slots per row.  Slot s of anti-diagonal d is cell
+// Band tier: NW warps (a block) per side extension, the two previous anti-diagonals in a
+// shared memory ring of kBandW slots per row.  Slot s of anti-diagonal d is cell
 // i = floor(d/2) + rb + s (the register tiers' layout: the diagonal predecessor is the same
 // slot of row d-2, the gap predecessors slots s-1, s (odd d) or s, s+1 (even d) of row
 // d-1); slot s lives at ring position (s + base) mod kBandW, so re-centring the window
 // only moves base and clears the slots it exposes.  Each anti-diagonal is swept over its
-// band only, 32 cells at a time; the new anti-diagonal overwrites row d-2 in place, and
+// band only, 32 NW cells at a time; the new anti-diagonal overwrites row d-2 in place, and
 // the two slots just outside the band are set to -inf so that the next two anti-diagonals
-// read correct neighbours.  Takes DNA and protein, any band up to kBandW - 2 cells, and
-// continues sides from escalation records of the register levels.
+// read correct neighbours.  The live range and the best cell are reduced per warp, then
+// across the block through a double-buffered shared array (one barrier per anti-diagonal).
+// Sides reach this tier when their band outgrows every register window (a few very wide
+// bands, whose anti-diagonals a whole block shares).  Takes DNA and protein, any band up
+// to kBandW - 2 cells, and continues sides from escalation records of the register levels.
 constexpr int kBandW = 8192;
+constexpr int kBandWarps = 8;
+
+template <int NW>
+__device__ __forceinline__ void band_sync() {
+    if constexpr (NW == 1) __syncwarp();
+    else __syncthreads();
+}
 
 __device__ __forceinline__ int32_t band_load_rec(const Problem& P, uint32_t ri, int32_t* R0, int32_t* R1,
                                                  int32_t& rb, int64_t& d, int32_t& L, int32_t& U, int32_t& T,
                                                  int32_t& best, int64_t& bi, int64_t& bj, int64_t& barg,
-                                                 uint32_t& flags, uint64_t& cells, int lane) {
+                                                 uint32_t& flags, uint64_t& cells, int tid, int nt) {
     const int32_t* r = P.rec + ri;
     const int32_t w0 = __ldcg(r + 0);
     const int32_t off = (kBandW - w0) / 2;
@@ -281,7 +291,7 @@ __device__ __forceinline__ int32_t band_load_rec(const Problem& P, uint32_t ri, 
     flags = uint32_t(__ldcg(r + 10));
     cells = uint64_t(uint32_t(__ldcg(r + 11))) | (uint64_t(uint32_t(__ldcg(r + 12))) << 32);
     // record rows: d-1 then d-2, slots 0 .. w0-1
-    for (int s = lane; s < w0; s += 32) {
+    for (int s = tid; s < w0; s += nt) {
         R0[s + off] = __ldcg(r + 16 + s);
         R1[s + off] = __ldcg(r + 16 + w0 + s);
     }
@@ -289,16 +299,20 @@ __device__ __forceinline__ int32_t band_load_rec(const Problem& P, uint32_t ri, 
 }
 
 // Returns false when the band outgrew the ring (the side then goes to the generic tier).
+// red: 8 NW ints of shared memory for the block reductions.
+template <int NW>
 __device__ bool extend_band(const Problem& P, const Unit& u, uint32_t uidx, int32_t* R0, int32_t* R1,
-                            const int32_t* sim, int lane) {
+                            const int32_t* sim, int32_t* red, int tid) {
     constexpr int W = kBandW;
+    constexpr int NT = 32 * NW;
+    const int lane = tid & 31, warp = tid >> 5;
     const int64_t m = u.m, n = u.n;
     const int64_t dir = u.side ? -1 : 1;
-    for (int s = lane; s < W; s += 32) {
+    for (int s = tid; s < W; s += NT) {
         R0[s] = kNeg;
         R1[s] = kNeg;
     }
-    __syncwarp();
+    band_sync<NW>();
     int32_t* P1 = R0;       // anti-diagonal d-1
     int32_t* P2 = R1;       // anti-diagonal d-2, overwritten by d
     int32_t rb = -W / 2, T = 0, best = 0, L = 0, U = 0;
@@ -307,11 +321,11 @@ __device__ bool extend_band(const Problem& P, const Unit& u, uint32_t uidx, int3
     uint64_t cells = 1;
     const uint32_t ri = P.rec_of ? __ldcg(P.rec_of + uidx) : 0xffffffffu;
     if (ri != 0xffffffffu && __ldcg(P.rec + ri) <= W) {
-        band_load_rec(P, ri, R0, R1, rb, d, L, U, T, best, bi, bj, barg, flags, cells, lane);
-    } else if (lane == 0) {
+        band_load_rec(P, ri, R0, R1, rb, d, L, U, T, best, bi, bj, barg, flags, cells, tid, NT);
+    } else if (tid == 0) {
         P1[W / 2] = 0;      // S(0,0) = 0 at d = 0 (slot W/2)
     }
-    __syncwarp();
+    band_sync<NW>();
     const int32_t g = P.gap;
     for (; d <= m + n; d++) {
         int64_t lo = L, hi = int64_t(U) + 1;
@@ -342,18 +356,18 @@ __device__ bool extend_band(const Problem& P, const Unit& u, uint32_t uidx, int3
             const int64_t ak = k > 0 ? k : -k;
             const int64_t from = ak >= W ? 0 : (k > 0 ? W - k : 0);
             const int64_t cnt = ak >= W ? W : ak;
-            for (int64_t t = lane; t < cnt; t += 32) {
+            for (int64_t t = tid; t < cnt; t += NT) {
                 const uint32_t pos = uint32_t((from + t + base) & (W - 1));
                 P1[pos] = kNeg;
                 P2[pos] = kNeg;
             }
-            __syncwarp();
+            band_sync<NW>();
         }
         const int32_t thr = max(T - P.X, kDeadLine);
         const bool odd = d & 1;
         int32_t first = INT32_MAX, last = -1, bmax = kNeg, bslot = INT32_MAX;
-        for (int64_t s0 = slo; s0 <= shi; s0 += 32) {
-            const int64_t s = s0 + lane;
+        for (int64_t s0 = slo; s0 <= shi; s0 += NT) {
+            const int64_t s = s0 + tid;
             if (s <= shi) {
                 const int64_t i = ib + s, j = d - i;
                 const uint32_t ps = uint32_t((s + base) & (W - 1));
@@ -378,16 +392,44 @@ __device__ bool extend_band(const Problem& P, const Unit& u, uint32_t uidx, int3
                 }
             }
         }
-        if (lane == 0) {
+        if (tid == 0) {
             P2[uint32_t((slo - 1 + base) & (W - 1))] = kNeg;
             P2[uint32_t((shi + 1 + base) & (W - 1))] = kNeg;
         }
         cells += uint64_t(hi - lo + 1);
         first = __reduce_min_sync(0xffffffffu, first);
         last = __reduce_max_sync(0xffffffffu, last);
-        const int32_t wmax = __reduce_max_sync(0xffffffffu, bmax);
+        int32_t wmax = __reduce_max_sync(0xffffffffu, bmax);
         bslot = __reduce_min_sync(0xffffffffu, bmax == wmax ? bslot : INT32_MAX);
-        __syncwarp();
+        if constexpr (NW > 1) {
+            // across the block: this anti-diagonal's half of the double buffer
+            int32_t* rd = red + (d & 1) * 4 * NW;
+            if (lane == 0) {
+                rd[warp] = first;
+                rd[NW + warp] = last;
+                rd[2 * NW + warp] = wmax;
+                rd[3 * NW + warp] = bslot;
+            }
+            __syncthreads();
+            first = INT32_MAX;
+            last = -1;
+            wmax = kNeg;
+            bslot = INT32_MAX;
+#pragma unroll
+            for (int w = 0; w < NW; w++) {
+                first = min(first, rd[w]);
+                last = max(last, rd[NW + w]);
+                const int32_t v = rd[2 * NW + w];
+                if (v > wmax) {
+                    wmax = v;
+                    bslot = rd[3 * NW + w];
+                } else if (v == wmax) {
+                    bslot = min(bslot, rd[3 * NW + w]);
+                }
+            }
+        } else {
+            __syncwarp();
+        }
         if (first == INT32_MAX) break;
         const int64_t arg = ib + bslot;
         if (wmax > T) {
@@ -403,37 +445,48 @@ __device__ bool extend_band(const Problem& P, const Unit& u, uint32_t uidx, int3
         P2 = P1;
         P1 = tmp;
     }
-    if (lane == 0) {
+    if (tid == 0) {
         write_side(P.results, u.pair, u.side, best, uint32_t(bi), uint32_t(bj), flags, cells);
         atomicAdd(&P.stats[1], 1ull);
         atomicAdd(&P.stats[5], (unsigned long long)cells);
     }
-    __syncwarp();
+    band_sync<NW>();
     return true;
 }
 
-__global__ void __launch_bounds__(32) k_band(Problem P, Queues Q) {
+template <int NW>
+__global__ void __launch_bounds__(32 * NW) k_band(Problem P, Queues Q) {
     extern __shared__ int32_t band_smem[];
     int32_t* sim = band_smem;
-    int32_t* R0 = band_smem + 416;
+    int32_t* red = band_smem + 400;                 // 8 NW ints (NW <= 2: within the pad)
+    int32_t* R0 = band_smem + 416 + (NW > 2 ? 8 * NW : 0);
     int32_t* R1 = R0 + kBandW;
-    for (int t = threadIdx.x; t < P.alpha * P.alpha; t += blockDim.x) sim[t] = P.sim[t];
-    __syncwarp();
-    const int lane = threadIdx.x & 31;
+    __shared__ uint32_t take;
+    const int tid = threadIdx.x;
+    for (int t = tid; t < P.alpha * P.alpha; t += blockDim.x) sim[t] = P.sim[t];
+    if (NW > 2) red = band_smem + 416;
+    band_sync<NW>();
     const uint32_t n_q = *reinterpret_cast<volatile uint32_t*>(&Q.ctr[1 + 2 * kBandQ]);
     for (;;) {
         uint32_t k = 0;
-        if (lane == 0) k = atomicAdd(&Q.ctr[2 + 2 * kBandQ], 1u);
-        k = __shfl_sync(0xffffffffu, k, 0);
+        if constexpr (NW == 1) {
+            if (tid == 0) k = atomicAdd(&Q.ctr[2 + 2 * kBandQ], 1u);
+            k = __shfl_sync(0xffffffffu, k, 0);
+        } else {
+            if (tid == 0) take = atomicAdd(&Q.ctr[2 + 2 * kBandQ], 1u);
+            __syncthreads();
+            k = take;
+            __syncthreads();
+        }
         if (k >= n_q) break;
         const uint32_t uidx = Q.q[kBandQ][k];
         const Unit u = P.units[uidx];
-        if (!extend_band(P, u, uidx, R0, R1, sim, lane)) {
-            if (lane == 0) {
+        if (!extend_band<NW>(P, u, uidx, R0, R1, sim, red, tid)) {
+            if (tid == 0) {
                 push_unit(Q, kGenericQ, uidx);
                 atomicAdd(&P.stats[3], 1ull);
             }
-            __syncwarp();
+            band_sync<NW>();
         }
     }
 }
@@ -525,14 +578,15 @@ cudaError_t launch_generic(const Problem& P, const Queues& Q, int32_t* scratch,
 }
 
 cudaError_t launch_band(const Problem& P, const Queues& Q, int n_sm, cudaStream_t st) {
-    const size_t smem = (416 + 2 * size_t(kBandW)) * sizeof(int32_t);
+    constexpr int NW = kBandWarps;
+    const size_t smem = (416 + 8 * NW + 2 * size_t(kBandW)) * sizeof(int32_t);
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_band, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        cudaError_t e = cudaFuncSetAttribute(k_band<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k_band<<<n_sm * 3, 32, smem, st>>>(P, Q);
+    k_band<NW><<<n_sm, 32 * NW, smem, st>>>(P, Q);
     return cudaGetLastError();
 }
 
