@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--x", type=int, default=None, help="X (default: the workload's)")
     ap.add_argument("--delta", type=int, default=0)
     ap.add_argument("--pairs", type=int, default=None, help="pairs (default: the workload's full size)")
+    ap.add_argument("--seeds", type=int, default=1, choices=[1, 2],
+                    help="seed tuples per overlap on the same reads (dna_longread only)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-pairs", type=int, default=8000, help="oracle sample size")
@@ -67,6 +69,8 @@ def make_batch(a, rank):
         kw["n_pairs"] = a.pairs
     if a.workload == "uneven":
         kw["delta"] = a.delta
+    if a.seeds == 2 and a.workload == "dna_longread":
+        kw["seeds_per_pair"] = 2
     b = gen(**kw) if rank == 0 else gen(seed=1000 + rank, **kw)
     if a.x is not None:
         b = b.with_params(X=a.x)
@@ -76,7 +80,9 @@ def make_batch(a, rank):
 
 
 def workload_config(a, b):
-    return {"workload": f"{a.workload}_{b.n_pairs}_x{b.X}" + (f"_delta{b.delta}" if b.delta else ""),
+    seeds = b.meta.get("seeds_per_pair", 1)
+    return {"workload": f"{a.workload}_{b.n_pairs // seeds}_x{b.X}" + (f"_delta{b.delta}" if b.delta else "") +
+                        (f"_{seeds}seeds" if seeds > 1 else ""),
             "pairs": b.n_pairs, "residues": int(b.codes.size), "X": b.X, "delta_b": b.delta,
             "alphabet": b.alphabet, "scoring": ("BLOSUM62" if b.alphabet == "protein" else
                                                 f"{b.match}/{b.mismatch}/{b.gap}"),

@@ -10,7 +10,10 @@
  * substitution (p_sub), else kept.  DNA indels have length 1, protein indels a geometric
  * length with mean 2.  The seed is a uniform k-mer inside the mutated region whose
  * positions all survived unchanged; if none did, one is planted by forcing a k-mer to
- * survive.  gen_pairs() is called twice: with out == NULL it only reports lengths.
+ * survive.  When a second seed is asked for, it is drawn last (so the sequences do not
+ * change) uniformly among the clean k-mers that do not overlap the first; without one, the
+ * first seed is repeated.  gen_pairs() is called twice: with out == NULL it only reports
+ * lengths.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -52,6 +55,7 @@ typedef struct {
     /* outputs */
     uint32_t* out_lv;             /* [n] length of V */
     uint32_t* h_seed, *v_seed;
+    uint32_t* h_seed2, *v_seed2;  /* second seed per pair, or NULL */
     uint8_t* out;                 /* NULL on the sizing pass */
     const uint64_t* h_off, *v_off;
     uint64_t begin, end;
@@ -83,13 +87,14 @@ static uint32_t indel_len(rng_t* r, const job_t* j) {
 enum { OP_KEEP = 0, OP_SUB = 1, OP_DEL = 2 };
 
 /* Scratch per thread: ops/ins/subst value per source position. */
-typedef struct { uint8_t* op; uint32_t* ins; uint8_t* val; uint64_t cap; } scratch_t;
+typedef struct { uint8_t* op; uint32_t* ins; uint8_t* val; uint32_t* tgt; uint64_t cap; } scratch_t;
 
 static void ensure(scratch_t* s, uint64_t n) {
     if (n <= s->cap) return;
-    free(s->op); free(s->ins); free(s->val);
+    free(s->op); free(s->ins); free(s->val); free(s->tgt);
     s->cap = n + 1024;
     s->op = malloc(s->cap); s->ins = malloc(4 * s->cap); s->val = malloc(s->cap);
+    s->tgt = malloc(4 * s->cap);
 }
 
 static void do_pair(const job_t* j, uint64_t p, scratch_t* sc) {
@@ -109,6 +114,7 @@ static void do_pair(const job_t* j, uint64_t p, scratch_t* sc) {
         uint32_t hs = next_below(&r, lh - k + 1), vs = next_below(&r, lv - k + 1);
         j->out_lv[p] = lv;
         j->h_seed[p] = hs; j->v_seed[p] = vs;
+        if (j->h_seed2) { j->h_seed2[p] = hs; j->v_seed2[p] = vs; }
         for (uint32_t t = 0; t < lv; t++) {
             uint8_t c = draw_residue(&r, j);
             if (V) V[t] = c;
@@ -122,7 +128,7 @@ static void do_pair(const job_t* j, uint64_t p, scratch_t* sc) {
     uint32_t ls = lh - src0;
     const uint8_t* src = hres + src0;
     double pd = j->p_del[p], pi = j->p_ins[p], ps = j->p_sub[p];
-    uint8_t* op = sc->op; uint32_t* ins = sc->ins; uint8_t* val = sc->val;
+    uint8_t* op = sc->op; uint32_t* ins = sc->ins; uint8_t* val = sc->val; uint32_t* tgt = sc->tgt;
     for (uint32_t t = 0; t < ls; t++) { op[t] = OP_KEEP; ins[t] = 0; val[t] = src[t]; }
     for (uint32_t t = 0; t < ls; t++) {
         double u = next_f64(&r);
@@ -165,6 +171,7 @@ static void do_pair(const job_t* j, uint64_t p, scratch_t* sc) {
     for (uint32_t t = 0; t < ls; t++) {
         for (uint32_t q = 0; q < ins[t]; q++) { uint8_t c = draw_residue(&r, j); if (V) V[o] = c; o++; }
         if (t == seed_src) seed_tgt = o;
+        tgt[t] = o;
         if (op[t] != OP_DEL) { if (V) V[o] = val[t]; o++; }
     }
     if (j->kind[p] == 1) {           /* dovetail: random tail up to the target length */
@@ -174,6 +181,39 @@ static void do_pair(const job_t* j, uint64_t p, scratch_t* sc) {
     j->out_lv[p] = o;
     j->h_seed[p] = src0 + seed_src;
     j->v_seed[p] = seed_tgt;
+    if (j->h_seed2) {
+        /* second seed: a clean k-mer that does not overlap the first, drawn last */
+        uint64_t n2 = 0;
+        run = 0;
+        for (uint32_t t = 0; t < ls; t++) {
+            int clean = op[t] == OP_KEEP && ins[t] == 0;
+            run = clean ? run + 1 : 0;
+            if (run >= k) {
+                uint32_t st = t + 1 - k;
+                if (st + k <= seed_src || st >= seed_src + k) n2++;
+            }
+        }
+        uint32_t s2 = seed_src;
+        double u2 = next_f64(&r);
+        if (n2 > 0) {
+            uint64_t pick = (uint64_t)(u2 * (double)n2);
+            if (pick >= n2) pick = n2 - 1;
+            run = 0;
+            for (uint32_t t = 0; t < ls; t++) {
+                int clean = op[t] == OP_KEEP && ins[t] == 0;
+                run = clean ? run + 1 : 0;
+                if (run >= k) {
+                    uint32_t st = t + 1 - k;
+                    if (st + k <= seed_src || st >= seed_src + k) {
+                        if (pick == 0) { s2 = st; break; }
+                        pick--;
+                    }
+                }
+            }
+        }
+        j->h_seed2[p] = src0 + s2;
+        j->v_seed2[p] = s2 == seed_src ? seed_tgt : tgt[s2];
+    }
     free(hres);
 }
 
@@ -181,14 +221,14 @@ static void* worker(void* arg) {
     job_t* j = (job_t*)arg;
     scratch_t sc = {0};
     for (uint64_t p = j->begin; p < j->end; p++) do_pair(j, p, &sc);
-    free(sc.op); free(sc.ins); free(sc.val);
+    free(sc.op); free(sc.ins); free(sc.val); free(sc.tgt);
     return NULL;
 }
 
 int gen_pairs(int alphabet, int k, uint64_t seed, const double* bg_cdf, const double* sub_cdf,
               uint64_t n, const uint8_t* kind, const uint32_t* lh, const uint32_t* lv,
               const uint32_t* ov, const double* p_sub, const double* p_ins, const double* p_del,
-              uint32_t* out_lv, uint32_t* h_seed, uint32_t* v_seed,
+              uint32_t* out_lv, uint32_t* h_seed, uint32_t* v_seed, uint32_t* h_seed2, uint32_t* v_seed2,
               uint8_t* out, const uint64_t* h_off, const uint64_t* v_off, int n_threads) {
     if (n_threads < 1) n_threads = 1;
     if (n_threads > 256) n_threads = 256;
@@ -200,6 +240,7 @@ int gen_pairs(int alphabet, int k, uint64_t seed, const double* bg_cdf, const do
         j->kind = kind; j->lh = lh; j->lv = lv; j->ov = ov;
         j->p_sub = p_sub; j->p_ins = p_ins; j->p_del = p_del;
         j->out_lv = out_lv; j->h_seed = h_seed; j->v_seed = v_seed;
+        j->h_seed2 = h_seed2; j->v_seed2 = v_seed2;
         j->out = out; j->h_off = h_off; j->v_off = v_off;
         j->begin = n * (uint64_t)t / n_threads;
         j->end = n * (uint64_t)(t + 1) / n_threads;

@@ -166,7 +166,7 @@ def _gen_lib():
     lib = ctypes.CDLL(so)
     P = ctypes.c_void_p
     lib.gen_pairs.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, P, P, ctypes.c_uint64,
-                              P, P, P, P, P, P, P, P, P, P, P, P, P, ctypes.c_int]
+                              P, P, P, P, P, P, P, P, P, P, P, P, P, P, P, ctypes.c_int]
     lib.gen_pairs.restype = ctypes.c_int
     _GEN = lib
     return lib
@@ -176,10 +176,11 @@ def _ptr(a):
     return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
 
 
-def _build(alphabet, k, seed, kind, lh, lv, ov, p_sub, p_ins, p_del):
+def _build(alphabet, k, seed, kind, lh, lv, ov, p_sub, p_ins, p_del, seeds_per_pair=1):
     """Construct all pairs with the C generator: sizing pass, layout, writing pass.
 
-    Sequences are laid out H0, V0, H1, V1, ... so pair p uses ids (2p, 2p+1)."""
+    Sequences are laid out H0, V0, H1, V1, ... so pair p uses ids (2p, 2p+1).  With two
+    seeds per pair, tuples 2p and 2p+1 are the two seeds of pair p (same sequences)."""
     lib = _gen_lib()
     n = len(kind)
     kind = np.ascontiguousarray(kind, dtype=np.uint8)
@@ -195,9 +196,11 @@ def _build(alphabet, k, seed, kind, lh, lv, ov, p_sub, p_ins, p_del):
     out_lv = np.zeros(n, dtype=np.uint32)
     hs = np.zeros(n, dtype=np.uint32)
     vs = np.zeros(n, dtype=np.uint32)
+    hs2 = np.zeros(n, dtype=np.uint32) if seeds_per_pair == 2 else None
+    vs2 = np.zeros(n, dtype=np.uint32) if seeds_per_pair == 2 else None
     threads = max(1, min(64, os.cpu_count() or 1))
     args = (alpha, k, seed, _ptr(bg_cdf), _ptr(sub_cdf), n, _ptr(kind), _ptr(lh), _ptr(lv), _ptr(ov),
-            _ptr(p_sub), _ptr(p_ins), _ptr(p_del), _ptr(out_lv), _ptr(hs), _ptr(vs))
+            _ptr(p_sub), _ptr(p_ins), _ptr(p_del), _ptr(out_lv), _ptr(hs), _ptr(vs), _ptr(hs2), _ptr(vs2))
     lib.gen_pairs(*args, None, None, None, threads)
     lens = np.empty(2 * n, dtype=np.uint32)
     lens[0::2] = lh
@@ -213,6 +216,13 @@ def _build(alphabet, k, seed, kind, lh, lv, ov, p_sub, p_ins, p_del):
     pairs[:, 2] = hs
     pairs[:, 3] = vs
     pairs[:, 4] = k
+    if seeds_per_pair == 2:
+        two = np.empty((2 * n, 5), dtype=np.uint32)
+        two[0::2] = pairs
+        two[1::2] = pairs
+        two[1::2, 2] = hs2
+        two[1::2, 3] = vs2
+        pairs = two
     return codes, offs, lens, pairs
 
 
@@ -238,9 +248,12 @@ def _lognormal_lengths(rng, n, median, sigma, lo, hi):
     return np.clip(np.exp(rng.normal(np.log(median), sigma, size=n)), lo, hi).astype(np.int64)
 
 
-def dna_longread(n_pairs=100_000, seed=43, X=20, unrelated_frac=0.10):
+def dna_longread(n_pairs=100_000, seed=43, X=20, unrelated_frac=0.10, seeds_per_pair=1):
     """Long-read dovetail overlaps: query = read A, target = read B whose prefix is A's
-    suffix (overlap U[20%, 100%] of the shorter read) carrying U[8%, 18%] error."""
+    suffix (overlap U[20%, 100%] of the shorter read) carrying U[8%, 18%] error.  With
+    seeds_per_pair = 2 every overlap gives two seed tuples on the same two stored reads (the
+    two-seeds-per-overlap shape of the assembly and search pipelines; the sequences are the
+    same as with one seed)."""
     rng = np.random.default_rng(seed)
     k = 17
     unrel = _choose(rng, n_pairs, int(round(n_pairs * unrelated_frac)))
@@ -249,9 +262,10 @@ def dna_longread(n_pairs=100_000, seed=43, X=20, unrelated_frac=0.10):
     ov = np.maximum(k + 1, (rng.uniform(0.2, 1.0, size=n_pairs) * np.minimum(la, lb)).astype(np.int64))
     e3 = rng.uniform(0.08, 0.18, size=n_pairs) / 3.0
     kind = np.where(unrel, 2, 1)
-    codes, offs, lens, pairs = _build(DNA, k, seed, kind, la, lb, ov, e3, e3, e3)
-    return Batch(DNA, codes, offs, lens, pairs, 1, -1, -1, None, X, 0,
-                 f"dna_longread_{n_pairs}_x{X}", {"seed": seed, "k": k})
+    codes, offs, lens, pairs = _build(DNA, k, seed, kind, la, lb, ov, e3, e3, e3, seeds_per_pair)
+    name = f"dna_longread_{n_pairs}_x{X}" + ("_2seeds" if seeds_per_pair == 2 else "")
+    return Batch(DNA, codes, offs, lens, pairs, 1, -1, -1, None, X, 0, name,
+                 {"seed": seed, "k": k, "seeds_per_pair": seeds_per_pair})
 
 
 def protein(n_pairs=1_000_000, seed=44, X=49, homolog_frac=0.60):

@@ -82,3 +82,20 @@ def _swap(b):
     p = b.pairs.copy()
     p[:, [0, 1]] = p[:, [1, 0]]
     return synth.Batch(b.alphabet, b.codes, b.offsets, b.lengths, p)
+
+
+def test_two_seeds_per_overlap_share_the_reads():
+    one = synth.dna_longread(n_pairs=300)
+    two = synth.dna_longread(n_pairs=300, seeds_per_pair=2)
+    assert np.array_equal(one.codes, two.codes) and np.array_equal(one.offsets, two.offsets)
+    assert two.n_pairs == 2 * one.n_pairs
+    assert np.array_equal(two.pairs[0::2], one.pairs)
+    assert np.array_equal(two.pairs[1::2, :2], one.pairs[:, :2])
+    p = two.pairs.astype(np.int64)
+    k = 17
+    h = two.codes[(two.offsets[p[:, 0]].astype(np.int64) + p[:, 2])[:, None] + np.arange(k)]
+    v = two.codes[(two.offsets[p[:, 1]].astype(np.int64) + p[:, 3])[:, None] + np.arange(k)]
+    assert (h == v).all()                                  # every seed is an exact k-mer match
+    d = np.abs(p[1::2, 2] - p[0::2, 2])
+    assert ((d == 0) | (d >= k)).all()                     # second seeds do not overlap the first
+    assert (d > 0).mean() > 0.5
