@@ -38,6 +38,10 @@ SM_COUNT_GB300 = 152
 # instructions all issue there (measured: 60-61 per clock at 1.99 GHz for each of them);
 # plain adds and multiply-adds can also use the FMA pipe.
 ALU_LANES_PER_SM = 64
+# DRAM bytes (read + write) of one launch of the dominant kernel, from one ncu capture of the
+# same workload and kernel build (profiles/k_fused_dna_longread_100k_x20.md); reported as
+# roofline.traffic only for that workload with the default configuration.
+DOMINANT_KERNEL_TRAFFIC = {"dna_longread_100000_x20": 260_895_488 + 14_763_264}
 
 
 def parse():
@@ -418,8 +422,10 @@ def main():
         cell_probe = xdrop.xd_probe(ctx, "cell_dna" if b.alphabet == "dna" else "cell_prot")
         tier_names = ["first register launch (fused persistent grid of levels 0-2, or level 0)",
                       "later register levels and band tier", "generic tier"]
+        tuned_env = any(k.startswith("XD_") for k in os.environ)
+        traffic = None if tuned_env else DOMINANT_KERNEL_TRAFFIC.get(workload_config(a, b)["workload"])
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                    "frac": achieved / peak if peak else None, "traffic": None,
+                    "frac": achieved / peak if peak else None, "traffic": traffic,
                     "kernel": tier_names[top], "ops_per_cell": ALG_OPS_PER_CELL,
                     "peak_basis": f"{props.multi_processor_count} SMs x {ALU_LANES_PER_SM} integer ALU-pipe "
                                   f"lanes x {sm_max:.0f} MHz (max SM clock)",

@@ -434,6 +434,7 @@ void default_tiers(xd_ctx* c) {
     if (t.every2 == 1) t.every2 = 2;
     t.fused_minb = env_int("XD_FUSED_MINB", 2);
     t.long_permille = std::max(0, std::min(250, env_int("XD_LONG_PERMILLE", 0)));
+    t.long_shape = std::max(0, std::min(2, env_int("XD_LONG_SHAPE", 0)));
     set_chain(t, {kG1C32, kG16C16, kG32C16, kG32C32});
     c->tiers_small_x = t;
     // X <= 15: bands mostly fit 22 slots (measured at X = 10: 184 vs 152 GCUPS for 32 slots)

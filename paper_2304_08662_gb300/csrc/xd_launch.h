@@ -48,7 +48,8 @@ struct TierConfig {
     int every1, every2;                 // fused grid: warps starting in role 1 / role 2
     int fused_minb;                     // fused grid register budget: resident blocks per SM
     int long_permille;                  // fused grid: head of the cost order (per mille of the
-                                        // units) run first by 32-lane groups (0 = none)
+                                        // units) run first by wider groups (0 = none)
+    int long_shape;                     // their groups: 0 = 32 lanes x 4 slots, 1 = 8 x 4, 2 = 4 x 8
 };
 
 // Runs register level `level` of the chain: pulls the cost-ordered list (level 0) or

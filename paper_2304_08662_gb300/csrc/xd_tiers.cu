@@ -56,6 +56,8 @@ cudaError_t launch_fused_levels(const Problem& P, const Queues& Q, const TierCon
     if (a == kG1C32 && b == kG16C16 && d == kG32C16)
         return cfg.fused_minb == 4   ? launch_fused<1, 32, 16, 16, 32, 16, 4, 4>(P, Q, cfg, n_sm, st)
                : cfg.fused_minb == 3 ? launch_fused<1, 32, 16, 16, 32, 16, 3, 4>(P, Q, cfg, n_sm, st)
+               : cfg.long_shape == 1 ? launch_fused<1, 32, 16, 16, 32, 16, 2, 4, 8, 4>(P, Q, cfg, n_sm, st)
+               : cfg.long_shape == 2 ? launch_fused<1, 32, 16, 16, 32, 16, 2, 4, 4, 8>(P, Q, cfg, n_sm, st)
                                      : launch_fused<1, 32, 16, 16, 32, 16, 2, 4, 32, 4>(P, Q, cfg, n_sm, st);
     if (a == kG1C32 && b == kG8C16 && d == kG32C16) return launch_fused<1, 32, 8, 16, 32, 16, 2, 4>(P, Q, cfg, n_sm, st);
     if (a == kG1C32 && b == kG32C8 && d == kG32C16) return launch_fused<1, 32, 32, 8, 32, 16, 2, 4, 32, 4>(P, Q, cfg, n_sm, st);
