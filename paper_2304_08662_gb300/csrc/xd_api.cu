@@ -218,7 +218,7 @@ struct xd_ctx {
     uint32_t reserved_len = 0;
     cudaStream_t dev_stream = nullptr;
     bool generic_only = false;
-    TierConfig tiers{}, tiers_small_x{}, tiers_large_x{}, tiers_protein{};
+    TierConfig tiers{}, tiers_tiny_x{}, tiers_small_x{}, tiers_large_x{}, tiers_protein{};
     TierConfig tiers_latency{}, tiers_latency_mid{}, tiers_latency_prot{};
     uint32_t latency_units = 0;        // batches with fewer side extensions use tiers_latency
     std::vector<TuneEntry> tuned;      // autotuned configurations by (alphabet, X, length) bucket
@@ -433,12 +433,16 @@ void default_tiers(xd_ctx* c) {
     if (t.every1 == 1) t.every1 = 2;   // every warp in role 1 would leave the ordered units to nobody
     if (t.every2 == 1) t.every2 = 2;
     t.fused_minb = env_int("XD_FUSED_MINB", 2);
-    t.long_permille = std::max(0, std::min(250, env_int("XD_LONG_PERMILLE", 0)));
-    t.long_shape = std::max(0, std::min(2, env_int("XD_LONG_SHAPE", 0)));
+    // the longest 0.2% of the sides first, with 8 lanes x 4 slots (measured +3-4% at X = 20)
+    t.long_permille = std::max(0, std::min(250, env_int("XD_LONG_PERMILLE", 2)));
+    t.long_shape = std::max(0, std::min(2, env_int("XD_LONG_SHAPE", 1)));
     set_chain(t, {kG1C32, kG16C16, kG32C16, kG32C32});
+    // X <= 15: narrower first windows (measured at X = 10: 20 slots 195, 24 slots 184,
+    // 32 slots 152 GCUPS); 20 slots up to X = 12, 24 slots up to X = 15
     c->tiers_small_x = t;
-    // X <= 15: bands mostly fit 22 slots (measured at X = 10: 184 vs 152 GCUPS for 32 slots)
     set_chain(c->tiers_small_x, {kG1C24, kG16C16, kG32C16, kG32C32});
+    c->tiers_tiny_x = t;
+    set_chain(c->tiers_tiny_x, {kG1C20, kG16C16, kG32C16, kG32C32});
     c->tiers_large_x = t;
     set_chain(c->tiers_large_x, {kG4C16, kG16C16, kG32C32});
     c->tiers_large_x.every1 = std::max(0, env_int("XD_EVERY1", 4));   // measured: 4 / 16 for this chain
@@ -467,7 +471,7 @@ void default_tiers(xd_ctx* c) {
     }
     if (const char* ch = std::getenv("XD_CHAIN")) {
         TierConfig forced = t;
-        if (parse_chain(ch, forced)) c->tiers = c->tiers_small_x = c->tiers_large_x = forced;
+        if (parse_chain(ch, forced)) c->tiers = c->tiers_tiny_x = c->tiers_small_x = c->tiers_large_x = forced;
     }
 }
 
@@ -489,6 +493,7 @@ const TierConfig& tiers_for(const xd_ctx* c, const BatchView& b) {
         return units < c->latency_units / 2 ? c->tiers_latency : c->tiers_latency_mid;
     }
     if (b.alpha == 20) return c->tiers_protein;
+    if (b.X <= 12) return c->tiers_tiny_x;
     if (b.X <= 15) return c->tiers_small_x;
     if (b.X <= 30) return c->tiers;
     return c->tiers_large_x;
@@ -918,7 +923,7 @@ bool parse_entry(const std::string& line, const TierConfig& base, TuneEntry& out
         for (int k = 0; k < out.cfg.n_levels; k++) {
             const int v = out.cfg.variant[k];
             if (!(v == kG1C16 || v == kG4C16 || v == kG8C16 || v == kG16C16 || v == kG32C16 || v == kG32C32 ||
-                  v == kG8C8 || v == kG32C8)) {
+                  v == kG8C8 || v == kG32C8 || v == kG1C32 || v == kG1C24 || v == kG4C8)) {
                 why = "variant " + std::to_string(v) + " is not compiled for protein";
                 return false;
             }
@@ -963,7 +968,7 @@ void put_entry(std::vector<TuneEntry>& v, const TuneEntry& t) {
 // Lanes per side extension of a variant (the threads per alignment of its level).
 int tier_group_of(int v) {
     switch (v) {
-        case kG1C16: case kG1C32: case kG1C24: return 1;
+        case kG1C16: case kG1C32: case kG1C24: case kG1C20: return 1;
         case kG4C16: case kG4C32: case kG4C8: return 4;
         case kG8C16: case kG8C32: case kG8C8: return 8;
         case kG16C16: case kG16C32: case kG16C8: return 16;

@@ -179,10 +179,10 @@ def test_uneven_restricted_shape(ctx, delta):
 # Every compiled (lanes per side, slots per lane) variant, as a level of some chain, fused
 # and as separate launches, on a mix of narrow and wide bands (DNA ids: 0 G1C16, 1 G1C32,
 # 2 G4C16, 3 G8C16, 4 G16C16, 5 G32C16, 6 G32C32, 7 G4C32, 8 G8C32, 9 G16C32, 10 G4C8,
-# 11 G8C8, 12 G16C8, 13 G32C8, 14 G1C24).
+# 11 G8C8, 12 G16C8, 13 G32C8, 14 G1C24, 15 G1C20).
 CHAINS_DNA = ["1,4,5,6", "0,2,4,6", "1,7,8,6", "1,3,5,6", "10,11,12,13,6", "0,3,9,6", "13,6", "2,4,6",
-              "14,4,5,6", "0,1,4,5,6", "1,13,5,6"]
-CHAINS_PROT = ["2,4,6", "0,2,4,6", "3,5,6", "11,13,6", "13,6"]
+              "14,4,5,6", "15,4,5,6", "0,1,4,5,6", "1,13,5,6"]
+CHAINS_PROT = ["2,4,6", "0,2,4,6", "3,5,6", "11,13,6", "13,6", "1,3,6", "14,4,6", "10,4,6"]
 
 
 @pytest.fixture(scope="module")
