@@ -41,7 +41,7 @@ ALU_LANES_PER_SM = 64
 # DRAM bytes (read + write) of one launch of the dominant kernel, from one ncu capture of the
 # same workload and kernel build (profiles/k_fused_dna_longread_100k_x20.md); reported as
 # roofline.traffic only for that workload with the default configuration.
-DOMINANT_KERNEL_TRAFFIC = {"dna_longread_100000_x20": 260_895_488 + 14_763_264}
+DOMINANT_KERNEL_TRAFFIC = {"dna_longread_100000_x20": 261_182_208 + 14_858_496}
 
 
 def parse():

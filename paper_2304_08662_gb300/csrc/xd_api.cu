@@ -424,7 +424,7 @@ constexpr uint32_t kLatencyUnits = 65536;
 void default_tiers(xd_ctx* c) {
     TierConfig& t = c->tiers;
     for (int v = 0; v < kNumGroupVariants; v++) t.blocks_per_sm[v] = 3;
-    for (int v : {kG1C32, kG32C32, kG4C32, kG8C32, kG16C32}) t.blocks_per_sm[v] = 2;
+    for (int v : {kG1C32, kG32C32, kG4C32, kG8C32, kG16C32, kG2C32}) t.blocks_per_sm[v] = 2;
     for (int v : {kG4C8, kG8C8, kG16C8, kG32C8}) t.blocks_per_sm[v] = 4;
     t.chunk = std::max(1, env_int("XD_CHUNK", 1));
     t.fused = env_int("XD_FUSED", 1) != 0;
@@ -445,10 +445,13 @@ void default_tiers(xd_ctx* c) {
     set_chain(c->tiers_tiny_x, {kG1C20, kG16C16, kG32C16, kG32C32});
     c->tiers_large_x = t;
     set_chain(c->tiers_large_x, {kG4C16, kG16C16, kG32C32});
-    c->tiers_large_x.every1 = std::max(0, env_int("XD_EVERY1", 4));   // measured: 4 / 16 for this chain
+    c->tiers_large_x.every1 = std::max(0, env_int("XD_EVERY1", 4));
     c->tiers_large_x.every2 = std::max(0, env_int("XD_EVERY2", 16));
     if (c->tiers_large_x.every1 == 1) c->tiers_large_x.every1 = 2;
     if (c->tiers_large_x.every2 == 1) c->tiers_large_x.every2 = 2;
+    // X > 30: one launch per level measured faster than the fused grid (451 vs 376 GCUPS at
+    // X = 50 on the long-read batch)
+    c->tiers_large_x.fused = env_int("XD_FUSED_LARGE", 0) != 0 && t.fused;
     c->tiers_protein = t;
     set_chain(c->tiers_protein, {kG4C16, kG16C16, kG32C32});
     c->tiers_protein.fused = env_int("XD_FUSED_PROT", 0) != 0;   // separate launches measured faster
@@ -923,7 +926,8 @@ bool parse_entry(const std::string& line, const TierConfig& base, TuneEntry& out
         for (int k = 0; k < out.cfg.n_levels; k++) {
             const int v = out.cfg.variant[k];
             if (!(v == kG1C16 || v == kG4C16 || v == kG8C16 || v == kG16C16 || v == kG32C16 || v == kG32C32 ||
-                  v == kG8C8 || v == kG32C8 || v == kG1C32 || v == kG1C24 || v == kG4C8)) {
+                  v == kG8C8 || v == kG32C8 || v == kG1C32 || v == kG1C24 || v == kG4C8 || v == kG2C32 ||
+                  v == kG2C16)) {
                 why = "variant " + std::to_string(v) + " is not compiled for protein";
                 return false;
             }
@@ -969,6 +973,7 @@ void put_entry(std::vector<TuneEntry>& v, const TuneEntry& t) {
 int tier_group_of(int v) {
     switch (v) {
         case kG1C16: case kG1C32: case kG1C24: case kG1C20: return 1;
+        case kG2C32: case kG2C16: return 2;
         case kG4C16: case kG4C32: case kG4C8: return 4;
         case kG8C16: case kG8C32: case kG8C8: return 8;
         case kG16C16: case kG16C32: case kG16C8: return 16;

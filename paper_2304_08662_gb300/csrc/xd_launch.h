@@ -35,8 +35,8 @@ cudaError_t launch_accumulate(const unsigned long long* batch, unsigned long lon
 enum GroupVariant {
     kG1C16 = 0, kG1C32 = 1, kG4C16 = 2, kG8C16 = 3, kG16C16 = 4, kG32C16 = 5, kG32C32 = 6,
     kG4C32 = 7, kG8C32 = 8, kG16C32 = 9, kG4C8 = 10, kG8C8 = 11, kG16C8 = 12, kG32C8 = 13,
-    kG1C24 = 14, kG1C20 = 15,
-    kNumGroupVariants = 16
+    kG1C24 = 14, kG1C20 = 15, kG2C32 = 16, kG2C16 = 17,
+    kNumGroupVariants = 18
 };
 
 struct TierConfig {

@@ -22,6 +22,8 @@ int variant_window(int v) {
         case kG32C8: return 256;
         case kG1C24: return 24;
         case kG1C20: return 20;
+        case kG2C32: return 64;
+        case kG2C16: return 32;
         default: return 0;
     }
 }

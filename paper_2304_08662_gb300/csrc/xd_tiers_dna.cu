@@ -23,6 +23,8 @@ cudaError_t launch_level_dna(const Problem& P, const Queues& Q, int variant, int
         case kG32C8: return launch_group<32, 8, 4, 4>(P, Q, in_q, out_q, blocks, chunk, st);
         case kG1C24: return launch_group<1, 24, 3, 4>(P, Q, in_q, out_q, blocks, chunk, st);
         case kG1C20: return launch_group<1, 20, 3, 4>(P, Q, in_q, out_q, blocks, chunk, st);
+        case kG2C32: return launch_group<2, 32, 2, 4>(P, Q, in_q, out_q, blocks, chunk, st);
+        case kG2C16: return launch_group<2, 16, 3, 4>(P, Q, in_q, out_q, blocks, chunk, st);
         default: return cudaErrorInvalidValue;
     }
 }

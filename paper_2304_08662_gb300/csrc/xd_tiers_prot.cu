@@ -18,6 +18,8 @@ cudaError_t launch_level_prot(const Problem& P, const Queues& Q, int variant, in
         case kG1C32: return launch_group<1, 32, 2, 20>(P, Q, in_q, out_q, blocks, chunk, st);
         case kG1C24: return launch_group<1, 24, 3, 20>(P, Q, in_q, out_q, blocks, chunk, st);
         case kG4C8: return launch_group<4, 8, 4, 20>(P, Q, in_q, out_q, blocks, chunk, st);
+        case kG2C32: return launch_group<2, 32, 2, 20>(P, Q, in_q, out_q, blocks, chunk, st);
+        case kG2C16: return launch_group<2, 16, 3, 20>(P, Q, in_q, out_q, blocks, chunk, st);
         default: return cudaErrorInvalidValue;
     }
 }
