@@ -441,13 +441,22 @@ def main():
         if not a.no_e2e:
             hargs = xdrop.BatchArgs.from_host(b)
             hout = np.zeros(b.n_pairs, dtype=xdrop.RESULT_DTYPE)
-            t = xdrop.xd_submit_batch(ctx, hargs)
-            xdrop.xd_poll(ctx, t, hout, -1)
+            # warm-up: every launch slot once (each grows its device buffers on first use)
+            warm = [xdrop.xd_submit_batch(ctx, hargs) for _ in range(3)]
+            for t in warm:
+                xdrop.xd_poll(ctx, t, hout, -1)
             if dist:
                 dist.barrier()
+            # two batches in flight: the next batch's staging copy and upload overlap the
+            # current one's extension kernels (every copy stays inside the timed region)
             t0 = time.perf_counter()
+            pending = []
             for _ in range(a.steps):
-                t = xdrop.xd_submit_batch(ctx, hargs)
+                pending.append(xdrop.xd_submit_batch(ctx, hargs))
+                if len(pending) == 2:
+                    if xdrop.xd_poll(ctx, pending.pop(0), hout, -1) != xdrop.XD_OK:
+                        raise RuntimeError("e2e batch failed")
+            for t in pending:
                 if xdrop.xd_poll(ctx, t, hout, -1) != xdrop.XD_OK:
                     raise RuntimeError("e2e batch failed")
             e2e_s = (time.perf_counter() - t0) / a.steps
@@ -458,7 +467,8 @@ def main():
             assert np.array_equal(hout, res), "host and device entry points disagree"
             h2d = int(b.codes.nbytes + b.offsets.nbytes + b.lengths.nbytes + b.pairs.nbytes)
             e2e = {"value": cells * world / e2e_s / 1e9, "unit": "GCUPS", "h2d_bytes_per_step": h2d,
-                   "d2h_bytes_per_step": int(hout.nbytes), "ms_per_step": e2e_s * 1e3}
+                   "d2h_bytes_per_step": int(hout.nbytes), "ms_per_step": e2e_s * 1e3,
+                   "in_flight": 2}
 
         serving = None
         if rank == 0 and a.serve > 0 and a.workload == "dna_longread":

@@ -453,7 +453,9 @@ void default_tiers(xd_ctx* c) {
     // X = 50 on the long-read batch)
     c->tiers_large_x.fused = env_int("XD_FUSED_LARGE", 0) != 0 && t.fused;
     c->tiers_protein = t;
-    set_chain(c->tiers_protein, {kG4C16, kG16C16, kG32C32});
+    // measured on 1,000,000 protein pairs: 4 x 16 -> 8 x 16 -> 32 x 32 (268 GCUPS) ahead of
+    // 4 x 16 -> 16 x 16 -> 32 x 32 (248)
+    set_chain(c->tiers_protein, {kG4C16, kG8C16, kG32C32});
     c->tiers_protein.fused = env_int("XD_FUSED_PROT", 0) != 0;   // separate launches measured faster
     // small batches (measured on long-read and protein batches of 1,000 - 30,000 pairs):
     // DNA below half the threshold 32 lanes x 16 slots, above it 16 x 8 first; protein 32 x 8
