@@ -153,6 +153,35 @@ xd_status xd_create(const xd_config* cfg, xd_ctx** out);
  * are outstanding: nothing was queued; retry after polling), XD_EDEVICE. */
 xd_status xd_submit_batch(xd_ctx* ctx, const xd_batch* batch, uint64_t* ticket);
 
+/* Resident sequence store: the detached sequence set of Sec. 4.1.1 kept on the device across
+ * batches, one per alphabet.  xd_store_add copies n_seqs sequences (host codes, offsets
+ * and lengths as in xd_batch), packs each distinct sequence once, and writes one handle per
+ * input sequence to handles[n_seqs]; a sequence equal (same codes) to one already stored
+ * gets the existing handle, so shared reads are stored once.  The store counts against
+ * store_bytes_cap for the context's lifetime.  Synchronous.  Errors: XD_EINVAL (codes
+ * outside the alphabet, sequences past n_codes), XD_ENOMEM (cap), XD_EDEVICE. */
+xd_status xd_store_add(xd_ctx* ctx, xd_alphabet alpha, uint32_t n_seqs, uint64_t n_codes,
+                       const uint8_t* seq_codes, const uint64_t* seq_offsets, const uint32_t* seq_lengths,
+                       uint32_t* handles);
+
+/* Sequences held and device bytes used by the resident store of one alphabet. */
+xd_status xd_store_info(const xd_ctx* ctx, xd_alphabet alpha, uint64_t* n_seqs, uint64_t* device_bytes);
+
+/* Seed tuples on the resident store: h_id / v_id are handles from xd_store_add. */
+typedef struct {
+    xd_alphabet alpha;
+    uint32_t n_pairs;
+    const xd_pair* pairs;
+    xd_scoring scoring;
+    int32_t X;
+    uint32_t delta_b;
+} xd_pairs_batch;
+
+/* As xd_submit_batch, but only the seed tuples travel: the sequences are already resident.
+ * Poll with xd_poll.  Such batches merge with each other (same scoring, X and delta_b), not
+ * with host batches.  Errors as xd_submit_batch; XD_EINVAL also for unknown handles. */
+xd_status xd_submit_pairs(xd_ctx* ctx, const xd_pairs_batch* batch, uint64_t* ticket);
+
 /* Wait up to wait_ms milliseconds (0 = do not wait, < 0 = wait without limit) for the
  * batch of `ticket`; on XD_OK copies n_pairs results to the host array `out` and retires
  * the ticket.  Returns XD_PENDING if not finished and wait_ms == 0, XD_ETIMEDOUT if the

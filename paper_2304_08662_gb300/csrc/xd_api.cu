@@ -90,6 +90,8 @@ struct BatchView {
     int8_t sim[400] = {};
     int32_t gap = 0, X = 0, max_abs = 1;
     uint32_t delta = 0, max_len = 0;
+    const uint32_t* packed = nullptr;   // resident store: residues already packed (no codes)
+    uint64_t packed_words = 0;
 };
 
 // One submitted host batch (a request).  Its inputs are copied to a pinned buffer at
@@ -105,6 +107,7 @@ struct Request {
     HostBuf in;
     size_t o_offs = 0, o_lens = 0, o_pairs = 0, in_bytes = 0;
     size_t need = 0;             // device bytes admitted for it
+    bool pairs_only = false;     // seed tuples on the resident sequence store
     std::vector<xd_result> out;
 };
 
@@ -207,6 +210,19 @@ struct TuneEntry {
     float ms = 0;
 };
 
+// The resident sequence store of one alphabet: sequences packed once on the device and kept
+// across batches (the paper's detached sequence set, Sec. 4.1.1), deduplicated by content.
+struct SeqStore {
+    DevBuf words;                        // packed residues
+    uint64_t used_words = 0;
+    std::vector<uint64_t> off;           // residue position of each sequence
+    std::vector<uint32_t> len;
+    DevBuf d_off, d_len;                 // the same tables on the device
+    std::vector<uint8_t> codes;          // host copy of every stored sequence (exact dedup)
+    std::vector<uint64_t> host_off;
+    std::unordered_map<uint64_t, std::vector<uint32_t>> by_hash;
+};
+
 struct xd_ctx {
     int device = 0;
     int n_sm = 1;
@@ -249,6 +265,7 @@ struct xd_ctx {
     // the fused persistent kernel's blocks wait on one another, so two of them never run at
     // the same time: each waits for the previous one through this event
     cudaEvent_t coop_done = nullptr;
+    SeqStore store[2];                 // DNA, protein
     // CUDA graph of the device entry point: a batch that repeats the previous call's
     // arguments exactly is captured once and then replayed
     bool graphs = true;
@@ -526,12 +543,14 @@ xd_status run_pipeline(xd_ctx* c, Scratch& s, const BatchView& b, xd_result* d_o
     XD_CUDA(c, cudaMemsetAsync(s.err.p, 0, 4, st));
     XD_CUDA(c, cudaMemsetAsync(s.bstats.p, 0, 16 * 8, st));
     auto* err = static_cast<uint32_t*>(s.err.p);
-    auto* store = static_cast<uint32_t*>(s.store.p);
-    XD_CUDA(c, launch_pack(b.alpha, b.codes, b.n_codes, store, err, c->n_sm, st));
+    const uint32_t* store = b.packed ? b.packed : static_cast<const uint32_t*>(s.store.p);
+    if (!b.packed)
+        XD_CUDA(c, launch_pack(b.alpha, b.codes, b.n_codes, static_cast<uint32_t*>(s.store.p), err, c->n_sm, st));
     XD_CUDA(c, mark(1));
     Problem P{};
     P.store = store;
-    P.n_words = std::max<uint64_t>(1, (b.n_codes + (b.alpha == 4 ? 15 : 5)) / (b.alpha == 4 ? 16 : 6));
+    P.n_words = b.packed ? std::max<uint64_t>(1, b.packed_words)
+                         : std::max<uint64_t>(1, (b.n_codes + (b.alpha == 4 ? 15 : 5)) / (b.alpha == 4 ? 16 : 6));
     P.max_abs = b.max_abs;
     P.units = static_cast<const Unit*>(s.units.p);
     P.results = d_out;
@@ -678,7 +697,7 @@ void launch_merged(xd_ctx* c, Slot& slot) {
     for (auto it = c->pending.begin(); it != c->pending.end();) {
         Request* r = *it;
         const bool fits = take.empty() ||
-                          (c->merge && same_params(r->v, first->v) &&
+                          (c->merge && same_params(r->v, first->v) && r->pairs_only == first->pairs_only &&
                            n_pairs + r->v.n_pairs <= c->max_batch_pairs &&
                            n_codes + r->v.n_codes <= c->max_batch_codes &&
                            n_seqs + r->v.n_seqs <= 0xffffffffull);
@@ -769,6 +788,17 @@ void launch_merged(xd_ctx* c, Slot& slot) {
     v.offsets = reinterpret_cast<const uint64_t*>(d + o_offs);
     v.lengths = reinterpret_cast<const uint32_t*>(d + o_lens);
     v.pairs = reinterpret_cast<const xd_pair*>(d + o_pairs);
+    if (first->pairs_only) {
+        // seed tuples on the resident store: its packed residues and tables, no upload
+        const SeqStore& ss = c->store[v.alpha == 4 ? 0 : 1];
+        v.codes = nullptr;
+        v.n_codes = 0;
+        v.packed = static_cast<const uint32_t*>(ss.words.p);
+        v.packed_words = ss.used_words;
+        v.offsets = static_cast<const uint64_t*>(ss.d_off.p);
+        v.lengths = static_cast<const uint32_t*>(ss.d_len.p);
+        v.n_seqs = uint32_t(ss.off.size());
+    }
     auto* d_res = static_cast<xd_result*>(slot.d_results.p);
     xd_status ps = run_pipeline(c, slot.s, v, d_res, st, c->coop_done);
     if (ps != XD_OK) return fail_all(ps, c->err);
@@ -1202,6 +1232,184 @@ xd_status xd_device_status(xd_ctx* c, uint32_t* flags) {
     return XD_OK;
 }
 
+xd_status xd_store_add(xd_ctx* c, xd_alphabet alpha, uint32_t n_seqs, uint64_t n_codes, const uint8_t* seq_codes,
+                       const uint64_t* seq_offsets, const uint32_t* seq_lengths, uint32_t* handles) {
+    if (!c || (n_seqs && (!seq_offsets || !seq_lengths || !handles)) || (n_codes && !seq_codes)) return XD_EINVAL;
+    if (alpha != XD_DNA2 && alpha != XD_PROT5) return fail(c, XD_EINVAL, "unknown alphabet");
+    std::unique_lock<std::mutex> lk(c->mu);
+    XD_CUDA(c, cudaSetDevice(c->device));
+    const int A = alpha == XD_DNA2 ? 4 : 20;
+    const uint64_t per = A == 4 ? 16 : 6;
+    SeqStore& ss = c->store[alpha == XD_DNA2 ? 0 : 1];
+    for (uint32_t q = 0; q < n_seqs; q++)
+        if (seq_offsets[q] + seq_lengths[q] > n_codes)
+            return fail(c, XD_EINVAL, "sequence " + std::to_string(q) + " extends past n_codes");
+    if (!codes_valid(seq_codes, n_codes, A)) return fail(c, XD_EINVAL, "residue code outside the alphabet");
+    // deduplicate by content (hash, then exact comparison with the host copy)
+    std::vector<uint8_t> fresh;
+    std::vector<std::pair<uint32_t, uint64_t>> placed;   // new id, offset in fresh
+    const uint32_t first_new = uint32_t(ss.off.size());
+    std::vector<uint32_t> out(n_seqs);
+    std::unordered_map<uint64_t, std::vector<uint32_t>> pending_hash;   // within this call
+    for (uint32_t q = 0; q < n_seqs; q++) {
+        const uint8_t* src = seq_codes + seq_offsets[q];
+        const uint32_t L = seq_lengths[q];
+        uint64_t h = 1469598103934665603ull ^ L;
+        for (uint32_t t = 0; t < L; t++) h = (h ^ src[t]) * 1099511628211ull;
+        int64_t found = -1;
+        if (auto it = ss.by_hash.find(h); it != ss.by_hash.end())
+            for (uint32_t id : it->second)
+                if (ss.len[id] == L && std::memcmp(ss.codes.data() + ss.host_off[id], src, L) == 0) { found = id; break; }
+        if (found < 0)
+            if (auto it = pending_hash.find(h); it != pending_hash.end())
+                for (uint32_t id : it->second) {
+                    const uint64_t o = placed[id - first_new].second;
+                    if (ss.len[id] == L && std::memcmp(fresh.data() + o, src, L) == 0) { found = id; break; }
+                }
+        if (found < 0) {
+            const uint32_t id = uint32_t(ss.off.size());
+            placed.push_back({id, uint64_t(fresh.size())});
+            fresh.insert(fresh.end(), src, src + L);
+            ss.len.push_back(L);
+            ss.off.push_back(0);           // set below
+            ss.host_off.push_back(0);
+            pending_hash[h].push_back(id);
+            found = id;
+        }
+        out[q] = uint32_t(found);
+    }
+    const uint32_t n_new = uint32_t(ss.off.size()) - first_new;
+    if (n_new) {
+        const uint64_t words = (fresh.size() + per - 1) / per;
+        const uint64_t add_bytes = words * 4 + 12ull * n_new;
+        if (c->admitted + add_bytes > c->cap) {
+            ss.len.resize(first_new);
+            ss.off.resize(first_new);
+            ss.host_off.resize(first_new);
+            return fail(c, XD_ENOMEM, "the resident store would exceed the device memory cap");
+        }
+        c->admitted += add_bytes;   // the store stays admitted for the context's lifetime
+        // growing a device buffer frees the old one: wait for every launch that may read it
+        auto grow_keep = [&](DevBuf& b, size_t need, size_t keep) -> cudaError_t {
+            if (need <= b.cap) return cudaSuccess;
+            cudaError_t e = cudaDeviceSynchronize();
+            if (e != cudaSuccess) return e;
+            DevBuf nb;
+            e = grow(nb, std::max(need, 2 * b.cap));
+            if (e == cudaSuccess && keep) e = cudaMemcpy(nb.p, b.p, keep, cudaMemcpyDeviceToDevice);
+            if (e != cudaSuccess) {
+                release(nb);
+                return e;
+            }
+            release(b);
+            b = nb;
+            return cudaSuccess;
+        };
+        const uint64_t base_word = ss.used_words;
+        XD_CUDA(c, grow_keep(ss.words, (base_word + words + 4) * 4, base_word * 4));
+        XD_CUDA(c, grow_keep(ss.d_off, ss.off.size() * 8, first_new * 8ull));
+        XD_CUDA(c, grow_keep(ss.d_len, ss.len.size() * 4, first_new * 4ull));
+        for (const auto& pl : placed) {
+            ss.off[pl.first] = base_word * per + pl.second;
+            ss.host_off[pl.first] = ss.codes.size() + pl.second;
+        }
+        ss.codes.insert(ss.codes.end(), fresh.begin(), fresh.end());
+        for (auto& kv : pending_hash)
+            for (uint32_t id : kv.second) ss.by_hash[kv.first].push_back(id);
+        // upload and pack the new residues behind the stored ones
+        DevBuf tmp, terr;
+        cudaError_t e = grow(tmp, fresh.size() + 16);
+        if (e == cudaSuccess) e = grow(terr, 16);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(tmp.p, fresh.data(), fresh.size(), cudaMemcpyHostToDevice, c->dev_stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(terr.p, 0, 4, c->dev_stream);
+        if (e == cudaSuccess && !fresh.empty())
+            e = launch_pack(A, static_cast<const uint8_t*>(tmp.p), fresh.size(),
+                            static_cast<uint32_t*>(ss.words.p) + base_word, static_cast<uint32_t*>(terr.p),
+                            c->n_sm, c->dev_stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(static_cast<uint64_t*>(ss.d_off.p) + first_new, ss.off.data() + first_new,
+                                8ull * n_new, cudaMemcpyHostToDevice, c->dev_stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(static_cast<uint32_t*>(ss.d_len.p) + first_new, ss.len.data() + first_new,
+                                4ull * n_new, cudaMemcpyHostToDevice, c->dev_stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->dev_stream);
+        release(tmp);
+        release(terr);
+        XD_CUDA(c, e);
+        ss.used_words = base_word + words;
+    }
+    std::memcpy(handles, out.data(), 4ull * n_seqs);
+    return XD_OK;
+}
+
+xd_status xd_store_info(const xd_ctx* c, xd_alphabet alpha, uint64_t* n_seqs, uint64_t* device_bytes) {
+    if (!c || (alpha != XD_DNA2 && alpha != XD_PROT5)) return XD_EINVAL;
+    std::lock_guard<std::mutex> lk(const_cast<xd_ctx*>(c)->mu);
+    const SeqStore& ss = c->store[alpha == XD_DNA2 ? 0 : 1];
+    if (n_seqs) *n_seqs = ss.off.size();
+    if (device_bytes) *device_bytes = ss.words.cap + ss.d_off.cap + ss.d_len.cap;
+    return XD_OK;
+}
+
+xd_status xd_submit_pairs(xd_ctx* c, const xd_pairs_batch* pb, uint64_t* ticket) {
+    if (!c || !pb || !ticket) return XD_EINVAL;
+    if (pb->n_pairs && !pb->pairs) return fail(c, XD_EINVAL, "null pairs");
+    std::unique_lock<std::mutex> lk(c->mu);
+    xd_batch b{};
+    b.alpha = pb->alpha;
+    b.n_pairs = pb->n_pairs;
+    b.pairs = pb->pairs;
+    b.scoring = pb->scoring;
+    b.X = pb->X;
+    b.delta_b = pb->delta_b;
+    BatchView v;
+    xd_status s = scoring_view(c, &b, v);
+    if (s != XD_OK) return s;
+    const SeqStore& ss = c->store[v.alpha == 4 ? 0 : 1];
+    uint32_t ml = 0;
+    for (uint32_t p = 0; p < pb->n_pairs; p++) {
+        const xd_pair& e = pb->pairs[p];
+        if (e.h_id >= ss.len.size() || e.v_id >= ss.len.size())
+            return fail(c, XD_EINVAL, "pair " + std::to_string(p) + ": handle not in the resident store");
+        const uint64_t lh = ss.len[e.h_id], lv = ss.len[e.v_id];
+        if (uint64_t(e.h_seed) + e.seed_len > lh || uint64_t(e.v_seed) + e.seed_len > lv)
+            return fail(c, XD_EINVAL, "pair " + std::to_string(p) + ": seed outside its sequence");
+        const uint64_t rm = lh - e.h_seed - e.seed_len, rn = lv - e.v_seed - e.seed_len;
+        if (int64_t(rm + rn) * v.max_abs >= kScoreLimit || int64_t(e.h_seed + e.v_seed) * v.max_abs >= kScoreLimit)
+            return fail(c, XD_EINVAL, "pair " + std::to_string(p) + ": scores could exceed 2^29 in magnitude");
+        ml = std::max<uint32_t>(ml, uint32_t(std::max<uint64_t>(rm, e.h_seed)));
+    }
+    v.max_len = ml;
+    v.n_seqs = 0;
+    v.n_codes = 0;
+    const size_t in_bytes = align_up(sizeof(xd_pair) * pb->n_pairs, 256);
+    const size_t out_bytes = sizeof(xd_result) * size_t(pb->n_pairs) + 16;
+    const ScratchPlan plan = plan_scratch(c, v.alpha, 0, pb->n_pairs, ml);
+    const size_t need = in_bytes + out_bytes + plan_bytes(plan) - plan.generic;
+    if (c->admitted + need > c->cap) return fail(c, XD_ENOMEM, "batch does not fit the device memory cap now");
+    if (c->requests.size() >= kMaxRequests) return fail(c, XD_ENOMEM, "too many requests outstanding");
+    auto* r = new Request();
+    r->v = v;
+    r->pairs_only = true;
+    r->o_offs = r->o_lens = r->o_pairs = 0;
+    r->in_bytes = in_bytes;
+    r->need = need;
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e == cudaSuccess) e = take_pinned(c, in_bytes, r->in);
+    if (e != cudaSuccess) {
+        delete r;
+        return cuda_fail(c, e, "pinned staging buffer");
+    }
+    std::memcpy(r->in.p, pb->pairs, sizeof(xd_pair) * pb->n_pairs);
+    c->admitted += need;
+    r->ticket = c->next_ticket++;
+    c->requests[r->ticket] = r;
+    c->pending.push_back(r);
+    *ticket = r->ticket;
+    c->wake.notify_one();
+    return XD_OK;
+}
+
 xd_status xd_submit_batch(xd_ctx* c, const xd_batch* b, uint64_t* ticket) {
     if (!c || !b || !ticket) return XD_EINVAL;
     std::unique_lock<std::mutex> lk(c->mu);
@@ -1555,6 +1763,11 @@ xd_status xd_destroy(xd_ctx* c) {
     }
     release(c->dev);
     release(c->stats);
+    for (SeqStore& ss : c->store) {
+        release(ss.words);
+        release(ss.d_off);
+        release(ss.d_len);
+    }
     for (auto& set : c->ev_sets)
         for (cudaEvent_t ev : set) cudaEventDestroy(ev);
     if (c->dev_stream) cudaStreamDestroy(c->dev_stream);

@@ -47,7 +47,8 @@ bool fused_supported(const TierConfig& c, int alpha) {
            (a == kG1C16 && b == kG4C16 && d == kG16C16) || (a == kG1C16 && b == kG8C16 && d == kG32C16) ||
            (a == kG4C16 && b == kG16C16 && d == kG32C32) || (a == kG1C32 && b == kG32C8 && d == kG32C16) ||
            (a == kG1C16 && b == kG32C8 && d == kG32C16) || (a == kG1C16 && b == kG1C32 && d == kG16C16) ||
-           (a == kG1C24 && b == kG16C16 && d == kG32C16) || (a == kG1C20 && b == kG16C16 && d == kG32C16);
+           (a == kG1C24 && b == kG16C16 && d == kG32C16) || (a == kG1C20 && b == kG16C16 && d == kG32C16) ||
+           (a == kG1C32 && b == kG8C32 && d == kG32C16) || (a == kG1C32 && b == kG8C32 && d == kG16C32);
 }
 
 cudaError_t launch_fused_levels(const Problem& P, const Queues& Q, const TierConfig& cfg, int n_sm,
@@ -68,6 +69,8 @@ cudaError_t launch_fused_levels(const Problem& P, const Queues& Q, const TierCon
     if (a == kG1C16 && b == kG1C32 && d == kG16C16) return launch_fused<1, 16, 1, 32, 16, 16, 2, 4, 32, 4>(P, Q, cfg, n_sm, st);
     if (a == kG1C24 && b == kG16C16 && d == kG32C16) return launch_fused<1, 24, 16, 16, 32, 16, 2, 4, 32, 4>(P, Q, cfg, n_sm, st);
     if (a == kG1C20 && b == kG16C16 && d == kG32C16) return launch_fused<1, 20, 16, 16, 32, 16, 2, 4, 32, 4>(P, Q, cfg, n_sm, st);
+    if (a == kG1C32 && b == kG8C32 && d == kG32C16) return launch_fused<1, 32, 8, 32, 32, 16, 2, 4, 8, 4>(P, Q, cfg, n_sm, st);
+    if (a == kG1C32 && b == kG8C32 && d == kG16C32) return launch_fused<1, 32, 8, 32, 16, 32, 2, 4, 8, 4>(P, Q, cfg, n_sm, st);
     if (a == kG1C16 && b == kG4C16 && d == kG16C16) return launch_fused<1, 16, 4, 16, 16, 16, 3, 4>(P, Q, cfg, n_sm, st);
     if (a == kG1C16 && b == kG8C16 && d == kG32C16) return launch_fused<1, 16, 8, 16, 32, 16, 3, 4>(P, Q, cfg, n_sm, st);
     if (a == kG4C16 && b == kG16C16 && d == kG32C32) return launch_fused<4, 16, 16, 16, 32, 32, 2, 4, 32, 4>(P, Q, cfg, n_sm, st);

@@ -42,6 +42,11 @@ class xd_batch(ctypes.Structure):
                 ("delta_b", ctypes.c_uint32)]
 
 
+class xd_pairs_batch(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_int), ("n_pairs", ctypes.c_uint32), ("pairs", ctypes.c_void_p),
+                ("scoring", xd_scoring), ("X", ctypes.c_int32), ("delta_b", ctypes.c_uint32)]
+
+
 class xd_stats(ctypes.Structure):
     _fields_ = [("batches", ctypes.c_uint64), ("pairs", ctypes.c_uint64), ("cells", ctypes.c_uint64),
                 ("units_tier", ctypes.c_uint64 * 3), ("escalations", ctypes.c_uint64),
@@ -84,12 +89,16 @@ def lib():
         L.xd_probe.argtypes = [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
         L.xd_run_device_noalloc.argtypes = [ctypes.POINTER(xd_batch), ctypes.c_uint32, V, V]
         L.xd_autotune.argtypes = [P, ctypes.POINTER(xd_batch), ctypes.c_char_p, ctypes.POINTER(ctypes.c_float)]
+        L.xd_store_add.argtypes = [P, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64, V, V, V, V]
+        L.xd_store_info.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
+        L.xd_submit_pairs.argtypes = [P, ctypes.POINTER(xd_pairs_batch), ctypes.POINTER(ctypes.c_uint64)]
         L.xd_destroy.argtypes = [P]
         L.xd_last_error.argtypes = [P]
         L.xd_last_error.restype = ctypes.c_char_p
         L.xd_version.restype = ctypes.c_char_p
         for name in ("xd_create", "xd_submit_batch", "xd_poll", "xd_run_device", "xd_reserve",
-                     "xd_device_status", "xd_get_stats", "xd_destroy", "xd_set_timing", "xd_get_timing", "xd_probe", "xd_run_device_noalloc", "xd_autotune"):
+                     "xd_device_status", "xd_get_stats", "xd_destroy", "xd_set_timing", "xd_get_timing", "xd_probe", "xd_run_device_noalloc", "xd_autotune",
+                     "xd_store_add", "xd_store_info", "xd_submit_pairs"):
             getattr(L, name).restype = ctypes.c_int
         _LIB = L
     return _LIB
@@ -250,6 +259,41 @@ def xd_autotune(ctx, args, path=None):
     if rc != XD_OK:
         raise XdError(rc, xd_last_error(ctx))
     return ms.value
+
+
+def xd_store_add(ctx, alphabet, codes, offsets, lengths):
+    """Add sequences to the resident store; returns one uint32 handle per sequence."""
+    codes = np.ascontiguousarray(codes, dtype=np.uint8)
+    offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+    lengths = np.ascontiguousarray(lengths, dtype=np.uint32)
+    handles = np.zeros(lengths.size, dtype=np.uint32)
+    rc = lib().xd_store_add(ctx, XD_DNA2 if alphabet == "dna" else XD_PROT5, lengths.size, codes.size,
+                            _ptr(codes), _ptr(offsets), _ptr(lengths), _ptr(handles))
+    if rc != XD_OK:
+        raise XdError(rc, xd_last_error(ctx))
+    return handles
+
+
+def xd_store_info(ctx, alphabet):
+    n, b = ctypes.c_uint64(), ctypes.c_uint64()
+    rc = lib().xd_store_info(ctx, XD_DNA2 if alphabet == "dna" else XD_PROT5, ctypes.byref(n), ctypes.byref(b))
+    if rc != XD_OK:
+        raise XdError(rc, xd_last_error(ctx))
+    return n.value, b.value
+
+
+def xd_submit_pairs(ctx, alphabet, pairs, match=1, mismatch=-1, gap=-1, matrix=None, X=20, delta=0):
+    """Submit seed tuples whose h_id / v_id are resident-store handles; returns a ticket."""
+    pairs = np.ascontiguousarray(pairs, dtype=np.uint32).reshape(-1, 5)
+    mat = None if matrix is None else np.ascontiguousarray(matrix, dtype=np.int8)
+    sc = xd_scoring(int(match), int(mismatch), int(gap), None if mat is None else _ptr(mat))
+    pb = xd_pairs_batch(XD_DNA2 if alphabet == "dna" else XD_PROT5, pairs.shape[0], _ptr(pairs), sc, int(X),
+                        int(delta))
+    t = ctypes.c_uint64()
+    rc = lib().xd_submit_pairs(ctx, ctypes.byref(pb), ctypes.byref(t))
+    if rc != XD_OK:
+        raise XdError(rc, xd_last_error(ctx))
+    return t.value
 
 
 # ----------------------------------------------------------------------------- helpers
