@@ -180,12 +180,16 @@ class RequestMix:
         b = pool.pair_range(a, a + size)
         if pool is self.dna:
             b = b.with_params(X=int(rng.choice([10, 20, 50])))
+        b.meta["first_seq"] = 2 * a          # the range's sequences in the pool: 2a, 2a + 1, ...
         return b
 
 
-def serve_run(xdrop, ctx, mix, rate_rps, duration, max_requests=None):
+def serve_run(xdrop, ctx, mix, rate_rps, duration, max_requests=None, submit=None):
     """Open-loop Poisson arrivals at rate_rps for `duration` seconds (rate_rps = inf: all
-    at once).  Latency = completion time - scheduled arrival time.  Returns a summary."""
+    at once).  Latency = completion time - scheduled arrival time.  Returns a summary.
+    submit(b) -> ticket sends one request (default: the batch with its sequences)."""
+    if submit is None:
+        submit = lambda b: xdrop.xd_submit_batch(ctx, xdrop.BatchArgs.from_host(b))  # noqa: E731
     import threading
     rng = np.random.default_rng(99)
     arrivals, t = [], 0.0
@@ -243,10 +247,9 @@ def serve_run(xdrop, ctx, mix, rate_rps, duration, max_requests=None):
             time.sleep(at - now)
         start[k] = t0 + at
         sub_begin[k] = time.perf_counter()
-        args = xdrop.BatchArgs.from_host(b)
         while True:
             try:
-                tk = xdrop.xd_submit_batch(ctx, args)
+                tk = submit(b)
                 break
             except xdrop.XdError as e:
                 if e.status != xdrop.XD_ENOMEM:
@@ -284,14 +287,32 @@ def serving_bench(xdrop, device, dna_pool, seconds, loads, inflight):
            "mix": "50% DNA long-read (X in {10, 20, 50}), 50% protein (BLOSUM62, X = 49)",
            "arrivals": "Poisson, open loop; latency from scheduled arrival to completion"}
     modes = {"continuous": dict(max_inflight=inflight, batching=1),
-             "per_batch": dict(max_inflight=1, batching=-1)}
+             "per_batch": dict(max_inflight=1, batching=-1),
+             "continuous_resident": dict(max_inflight=inflight, batching=1)}
+    res["continuous_resident_note"] = ("the pools' reads added once to the resident sequence store; "
+                                       "each request sends only its seed tuples")
     for name, kw in modes.items():
         ctx = xdrop.xd_create(device, **kw)
         try:
+            submit = None
+            if name == "continuous_resident":
+                handles = {id(p): xdrop.xd_store_add(ctx, p.alphabet, p.codes, p.offsets, p.lengths)
+                           for p in (dna_pool, prot_pool)}
+                pools = {"dna": dna_pool, "protein": prot_pool}
+
+                def submit(b, ctx=ctx, handles=handles, pools=pools):
+                    h = handles[id(pools[b.alphabet])]
+                    pr = b.pairs.copy()
+                    base = b.meta["first_seq"]
+                    pr[:, 0] = h[base + b.pairs[:, 0]]
+                    pr[:, 1] = h[base + b.pairs[:, 1]]
+                    return xdrop.xd_submit_pairs(ctx, b.alphabet, pr, b.match, b.mismatch, b.gap, b.matrix,
+                                                 b.X, b.delta)
             # warm-up (pinned buffers, scratch), then the saturated peak
-            serve_run(xdrop, ctx, RequestMix(dna_pool, prot_pool, 1), float("inf"), 0, max_requests=60)
+            serve_run(xdrop, ctx, RequestMix(dna_pool, prot_pool, 1), float("inf"), 0, max_requests=60,
+                      submit=submit)
             peak = serve_run(xdrop, ctx, RequestMix(dna_pool, prot_pool, 2), float("inf"), 0,
-                             max_requests=240)
+                             max_requests=240, submit=submit)
             if name == "continuous":
                 res["peak_pairs_per_s"] = peak["pairs_per_s"]
                 res["peak_gcups"] = peak["gcups"]
@@ -299,7 +320,7 @@ def serving_bench(xdrop, device, dna_pool, seconds, loads, inflight):
             for ld in loads:
                 rate_pairs = ld * res["peak_pairs_per_s"]
                 rate_rps = rate_pairs / mean_pairs
-                r = serve_run(xdrop, ctx, RequestMix(dna_pool, prot_pool, 3), rate_rps, seconds)
+                r = serve_run(xdrop, ctx, RequestMix(dna_pool, prot_pool, 3), rate_rps, seconds, submit=submit)
                 r["load"] = ld
                 r["offered_pairs_per_s"] = rate_pairs
                 out["loads"].append(r)
