@@ -63,6 +63,9 @@ def parse():
                     help="seconds per offered load of the serving run (0 = skip)")
     ap.add_argument("--serve-loads", default="0.25,0.5,0.9")
     ap.add_argument("--serve-inflight", type=int, default=3)
+    ap.add_argument("--tune-table", default=None, help="tuning table written by xd_autotune")
+    ap.add_argument("--autotune", default=None, help="run xd_autotune on the workload first and write "
+                                                      "the table to this path")
     return ap.parse_args()
 
 
@@ -381,8 +384,11 @@ def main():
 
     b = make_batch(a, rank)
     cells_paper = paper_cells(b)
-    ctx = xdrop.xd_create(local)
+    ctx = xdrop.xd_create(local, tune_table=a.tune_table)
     try:
+        if a.autotune:
+            tuned_ms = xdrop.xd_autotune(ctx, xdrop.BatchArgs.from_host(b), a.autotune)
+            print(json.dumps({"autotune": a.autotune, "best_ms": tuned_ms}), file=sys.stderr, flush=True)
         codes = torch.from_numpy(b.codes).to(dev)
         offs = torch.from_numpy(b.offsets.view(np.int64)).to(dev)
         lens = torch.from_numpy(b.lengths.view(np.int32)).to(dev)

@@ -453,6 +453,9 @@ void default_tiers(xd_ctx* c) {
     // the longest 0.2% of the sides first, with 8 lanes x 4 slots (measured +3-4% at X = 20)
     t.long_permille = std::max(0, std::min(250, env_int("XD_LONG_PERMILLE", 2)));
     t.long_shape = std::max(0, std::min(2, env_int("XD_LONG_SHAPE", 1)));
+    // failure-detection tests: a short wait limit and a producer that never finishes
+    t.wait_limit_ms = std::max(0, env_int("XD_TEST_WAIT_MS", 0));
+    t.phantom_producer = env_int("XD_TEST_PHANTOM_PRODUCER", 0) != 0;
     set_chain(t, {kG1C32, kG16C16, kG32C16, kG32C32});
     // X <= 15: narrower first windows (measured at X = 10: 20 slots 195, 24 slots 184,
     // 32 slots 152 GCUPS); 20 slots up to X = 12, 24 slots up to X = 15

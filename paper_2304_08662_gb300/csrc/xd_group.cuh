@@ -436,7 +436,7 @@ __device__ __forceinline__ int group_step(SideState& s, Res<CG, A>& res, int32_t
 // atomic counter and published by storing the unit index over the kNoUnit sentinel.
 constexpr uint32_t kNoUnit = 0xffffffffu;
 constexpr uint32_t kMaxSpin = 1u << 24;
-constexpr uint64_t kWaitLimitNs = 10ull * 1000 * 1000 * 1000;   // 10 s without progress
+constexpr uint64_t kWaitLimitNs = 10ull * 1000 * 1000 * 1000;   // default: 10 s without progress
 
 __device__ __forceinline__ uint64_t globaltimer_ns() {
     uint64_t t;
@@ -452,6 +452,7 @@ struct Source {
     uint32_t* reserve;          // live: length counter
     uint32_t* producers_done;   // live: producer warps that have finished
     uint32_t n_producers;
+    uint64_t wait_limit_ns;     // live: give up after this long without progress
 };
 
 // Next unit for the group (group-uniform result).  Returns false when the source is
@@ -477,7 +478,7 @@ __device__ __forceinline__ bool next_unit(const Source& S, int gl, int lane, uin
     if (gl == 0) {
         // Poll with plain coherent loads and exponential back-off (an idle consumer must not
         // load L2 with atomics).  The wait gives up, raising kErrWait, once neither the
-        // queue length nor the finished-producer count has changed for kWaitLimitNs.
+        // queue length nor the finished-producer count has changed for S.wait_limit_ns.
         const volatile uint32_t* reserve = S.reserve;
         const volatile uint32_t* done = S.producers_done;
         const uint32_t ticket = atomicAdd(S.pull, 1u);
@@ -508,7 +509,7 @@ __device__ __forceinline__ bool next_unit(const Source& S, int gl, int lane, uin
                 last_done = fin;
                 t_change = now;
                 pause = 128;
-            } else if (now - t_change > kWaitLimitNs) {
+            } else if (now - t_change > S.wait_limit_ns) {
                 atomicOr(err, kErrWait);
                 break;
             }
@@ -734,6 +735,8 @@ struct RolePlan {
     uint32_t long_warps;        // warps gw < long_warps start in the long role, then role 0
     int out2;                   // queue of role 2's overflows: q[2] when later register levels
                                 // follow the grid, else the band tier's queue
+    uint64_t wait_limit_ns;     // live-queue waits give up (kErrWait) after this long without
+                                // progress
 };
 
 __host__ __device__ __forceinline__ int start_role(uint32_t gw, int every1, int every2) {
@@ -742,7 +745,8 @@ __host__ __device__ __forceinline__ int start_role(uint32_t gw, int every1, int 
     return 0;
 }
 
-__device__ __forceinline__ Source live_source(const Queues& Q, int k, uint32_t* done, uint32_t producers) {
+__device__ __forceinline__ Source live_source(const Queues& Q, int k, uint32_t* done, uint32_t producers,
+                                              uint64_t wait_limit_ns) {
     Source S{};
     S.list = Q.q[k];
     S.pull = &Q.ctr[2 + 2 * k];
@@ -750,6 +754,7 @@ __device__ __forceinline__ Source live_source(const Queues& Q, int k, uint32_t* 
     S.reserve = &Q.ctr[1 + 2 * k];
     S.producers_done = done;
     S.n_producers = producers;
+    S.wait_limit_ns = wait_limit_ns;
     return S;
 }
 
@@ -801,10 +806,12 @@ __global__ void __launch_bounds__(128, MINB) k_fused(Problem P, Queues Q, RolePl
         signal_done(done0);
     }
     if (role <= 1) {
-        group_loop<G1, C1, A>(P, Q, live_source(Q, 0, done0, R.producers0), 1, 1, group_smem, 0, kWarpInts);
+        group_loop<G1, C1, A>(P, Q, live_source(Q, 0, done0, R.producers0, R.wait_limit_ns), 1, 1, group_smem, 0,
+                              kWarpInts);
         signal_done(done1);
     }
-    group_loop<G2, C2, A>(P, Q, live_source(Q, 1, done1, R.producers1), R.out2, 1, group_smem, 0, kWarpInts);
+    group_loop<G2, C2, A>(P, Q, live_source(Q, 1, done1, R.producers1, R.wait_limit_ns), R.out2, 1, group_smem, 0,
+                          kWarpInts);
 }
 
 template <int G, int CG, int MINB, int A>
@@ -848,7 +855,8 @@ static cudaError_t launch_fused(const Problem& P, const Queues& Q, const TierCon
     // every block must be resident at once: consumers wait for producers of the same grid
     const int blocks = n_sm * occ;
     const uint32_t n_warps = uint32_t(blocks) * 4;
-    RolePlan R{cfg.every1, cfg.every2, 0, 0, 0, 0, cfg.n_levels > 3 ? 2 : kBandQ};
+    RolePlan R{cfg.every1, cfg.every2, 0, 0, 0, 0, cfg.n_levels > 3 ? 2 : kBandQ,
+               cfg.wait_limit_ms > 0 ? uint64_t(cfg.wait_limit_ms) * 1000000ull : kWaitLimitNs};
     if (GL > 0 && cfg.long_permille > 0) {
         R.n_long = uint32_t(uint64_t(Q.n_units) * uint32_t(cfg.long_permille) / 1000u);
         R.long_warps = std::min(R.n_long, n_warps / 4);   // at most a quarter of the grid
@@ -859,6 +867,10 @@ static cudaError_t launch_fused(const Problem& P, const Queues& Q, const TierCon
         R.producers1 += r <= 1;
     }
     if (R.producers0 == 0) return cudaErrorInvalidValue;   // nobody would take the ordered units
+    // failure-detection test: a role-0 producer that never finishes, so that the role-1
+    // consumers' waits run out (bounded) and the batch reports kErrWait
+    R.producers0 += cfg.phantom_producer ? 1u : 0u;
+    R.producers1 += cfg.phantom_producer ? 1u : 0u;
     Problem p = P;
     Queues q = Q;
     int ch = cfg.chunk;

@@ -50,6 +50,8 @@ struct TierConfig {
     int long_permille;                  // fused grid: head of the cost order (per mille of the
                                         // units) run first by wider groups (0 = none)
     int long_shape;                     // their groups: 0 = 32 lanes x 4 slots, 1 = 8 x 4, 2 = 4 x 8
+    int wait_limit_ms;                  // fused grid: live-queue wait limit (0 = default, 10 s)
+    bool phantom_producer;              // failure-detection test: one producer never finishes
 };
 
 // Runs register level `level` of the chain: pulls the cost-ordered list (level 0) or
