@@ -17,6 +17,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "xdrop.h"
 #include "xd_device.cuh"
@@ -25,6 +26,12 @@
 namespace {
 
 using namespace xd;
+
+// NVTX range over a host-side scope (visible to timeline profilers; free without one).
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
 
 struct DevBuf {
     void* p = nullptr;
@@ -528,6 +535,7 @@ const TierConfig& tiers_for(const xd_ctx* c, const BatchView& b) {
 // chain: an event that orders the fused persistent launches of the context (may be null).
 xd_status run_pipeline(xd_ctx* c, Scratch& s, const BatchView& b, xd_result* d_out, cudaStream_t st,
                        cudaEvent_t chain) {
+    Range range("xd.pipeline");
     ScratchPlan plan = plan_scratch(c, b.alpha, b.n_codes, b.n_pairs, b.max_len);
     XD_CUDA(c, ensure_scratch(s, plan));
     bool timed = c->timing && c->ev_used < 4096;
@@ -694,6 +702,7 @@ void finish_request(xd_ctx* c, Request* r, xd_status st, const std::string& msg)
 // request of the same parameters while the merged batch stays under the size caps.
 // Called with the context lock held.
 void launch_merged(xd_ctx* c, Slot& slot) {
+    Range range("xd.launch");
     std::vector<Request*> take;
     const Request* first = c->pending.front();
     uint64_t n_codes = 0, n_seqs = 0, n_pairs = 0;
@@ -1415,6 +1424,7 @@ xd_status xd_submit_pairs(xd_ctx* c, const xd_pairs_batch* pb, uint64_t* ticket)
 
 xd_status xd_submit_batch(xd_ctx* c, const xd_batch* b, uint64_t* ticket) {
     if (!c || !b || !ticket) return XD_EINVAL;
+    Range range("xd.submit");
     std::unique_lock<std::mutex> lk(c->mu);
     BatchView v;
     xd_status s = scoring_view(c, b, v);
