@@ -29,6 +29,7 @@
 #pragma once
 #include <algorithm>
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 #include "xd_device.cuh"
 #include "xd_launch.h"
@@ -39,6 +40,33 @@ namespace xd {
 constexpr int32_t kNegR = -(1 << 24);
 constexpr int32_t kDeadR = -(1 << 23);
 constexpr int64_t kRegLimit = int64_t(1) << 23;
+
+// ---------------------------------------------------------------------------------------
+// DNA with 16-bit packed scores: representation kDna16 of the group kernels (template
+// argument A; the alphabet is DNA).
+//
+// Register p of a lane holds slot p in its low half and slot p + CG/2 in its high half, so
+// one 16x2 DPX instruction updates two cells.  A score S of anti-diagonal d is kept as
+// z = S - (B0 + gap * d).  With the base falling by |gap| per anti-diagonal, the gap
+// predecessors (d-1) need no adjustment and the diagonal one (d-2) gains the constant
+// -2 gap, which the similarity table already holds: the cell of Sec. 2.2 becomes
+// max(max(up, left), diag + Sim - 2 gap), two instructions for two cells.  The X-Drop
+// threshold T - X of anti-diagonal d sits at z = theta_d; it starts at kTheta0 and grows by
+// |gap| per anti-diagonal plus the growth of T, and every slot is rebased once it passes
+// kTheta16.  Dead cells hold -1 (all ones), so anything computed from them stays below
+// theta, and the live test is the sign of z - theta.  Live z lie in
+// [theta - s_max, theta + X + s_max], within 16 bits when X <= kMaxX16, -127 <= gap <= 0
+// and |Sim| <= 127.
+constexpr int kDna16 = 2;
+constexpr int32_t kTheta0 = 1024;
+constexpr int32_t kTheta16 = 16384;
+constexpr int32_t kMaxX16 = 15000;
+constexpr uint32_t kDead2 = 0xffffffffu;
+
+__host__ __device__ constexpr int alpha_of(int A) { return A == kDna16 ? 4 : A; }
+__host__ __device__ inline bool dna16_ok(const Problem& P) {
+    return P.alpha == 4 && P.X >= 0 && P.X <= kMaxX16 && P.gap <= 0 && P.gap >= -127;
+}
 
 enum { kCont = 0, kDone = 1, kOverflow = 2 };
 
@@ -131,6 +159,7 @@ struct SideState {
     uint64_t cells;
     int32_t m, n, d, rb, dir;
     int32_t L, U, T, best, bi, bj, barg;
+    int32_t B0;                 // kDna16: z = S - (B0 + gap d)
     uint32_t flags, side;
     bool refresh;
 };
@@ -305,9 +334,14 @@ __device__ __forceinline__ void cells_of(int32_t (&P1)[CG], int32_t (&P2)[CG], i
 // the four fields (e >> 2f) & 3, f = 0..3 (zero = match).  Protein: Sim row-major, H code
 // major.  Entries past the 20 x 20 matrix are zero (offsets of codes >= 20 land there; only
 // cells outside the band can carry such codes).
+__device__ __forceinline__ void build_table16(int32_t* tab, const Problem& P);
+
 template <int A>
 __device__ __forceinline__ void build_table(int32_t* tab, const Problem& P) {
-    if constexpr (A == 4) {
+    if constexpr (A == kDna16) {
+        build_table16(tab, P);
+        return;
+    } else if constexpr (A == 4) {
         const int32_t mat = P.sim[0], mis = P.sim[1];
         for (int e = threadIdx.x; e < 256; e += blockDim.x) {
             int4 v;
@@ -323,6 +357,137 @@ __device__ __forceinline__ void build_table(int32_t* tab, const Problem& P) {
     __syncthreads();
 }
 constexpr int kLutInts = 1024;
+
+
+// 2-bit field k of the low 32 bits -> bits 4k, 4k + 1.
+__device__ __forceinline__ uint64_t spread2(uint64_t s) {
+    s = (s | (s << 16)) & 0x0000FFFF0000FFFFull;
+    s = (s | (s << 8)) & 0x00FF00FF00FF00FFull;
+    s = (s | (s << 4)) & 0x0F0F0F0F0F0F0F0Full;
+    s = (s | (s << 2)) & 0x3333333333333333ull;
+    return s;
+}
+
+// Both halves of a register to all ones where negative, zeros elsewhere (byte permute in
+// sign-replicate mode).
+__device__ __forceinline__ uint32_t sign_spread(uint32_t u) {
+    uint32_t r;
+    asm("prmt.b32 %0, %1, %1, 0xBB99;" : "=r"(r) : "r"(u));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t pack2(int32_t lo, int32_t hi) {
+    return (uint32_t(lo) & 0xffffu) | (uint32_t(hi) << 16);
+}
+__device__ __forceinline__ int32_t lo16(uint32_t v) { return int32_t(int16_t(uint16_t(v & 0xffffu))); }
+__device__ __forceinline__ int32_t hi16(uint32_t v) { return int32_t(v) >> 16; }
+
+// DNA residue slices in the register order of kDna16: the field of slot t < CG/2 at bits
+// 4t, 4t + 1, that of slot CG/2 + t at bits 4t + 2, 4t + 3, so that byte q of the xor of H
+// and V covers registers 2q and 2q + 1.
+template <int CG>
+struct Res<CG, kDna16> {
+    static constexpr int H = CG / 2;
+    uint64_t hs, vs;
+    Stream sh, sv;
+
+    __device__ __forceinline__ static uint64_t interleave(uint64_t x) {
+        const uint64_t m = H == 16 ? 0xffffffffull : ((1ull << (2 * H)) - 1ull);
+        return spread2(x & m) | (spread2((x >> (2 * H)) & m) << 2);
+    }
+    __device__ __forceinline__ void load(const Problem& P, const SideState& s, int64_t hb, int64_t vb) {
+        const uint64_t h = s.dir > 0 ? slice_at(P.store, P.n_words, s.h0 + hb, false)
+                                     : slice_at(P.store, P.n_words, s.h0 - hb - 31, true);
+        const uint64_t v = s.dir > 0 ? slice_at(P.store, P.n_words, s.v0 + vb - 31, true)
+                                     : slice_at(P.store, P.n_words, s.v0 - vb, false);
+        hs = interleave(h);
+        vs = interleave(v);
+        stream_init(sh, P.store, P.n_words, s.h0 + s.dir * (hb + CG), s.dir);
+        stream_init(sv, P.store, P.n_words, s.v0 + s.dir * (vb + 1), s.dir);
+    }
+    // slots move down by one, the new residue enters slot CG - 1
+    __device__ __forceinline__ void push_h(const Problem& P) {
+        const uint64_t c = stream_next(sh, P.store, P.n_words);
+        hs = (hs >> 4) | (((hs >> 2) & 3ull) << (4 * (H - 1))) | (c << (4 * (H - 1) + 2));
+    }
+    // slots move up by one, the new residue enters slot 0
+    __device__ __forceinline__ void push_v(const Problem& P) {
+        const uint64_t c = stream_next(sv, P.store, P.n_words);
+        const uint64_t m = H == 16 ? ~0ull : ((1ull << (4 * H)) - 1ull);
+        vs = ((vs << 4) & m) | (((vs >> (4 * (H - 1))) & 3ull) << 2) | c;
+    }
+};
+
+// The block's table for kDna16: 256 int2 entries; entry e holds Sim - 2 gap of the four
+// 2-bit fields of e (zero = match), fields 0 / 1 in .x (low / high half), 2 / 3 in .y.
+__device__ __forceinline__ void build_table16(int32_t* tab, const Problem& P) {
+    const int32_t mat = P.sim[0] - 2 * P.gap, mis = P.sim[1] - 2 * P.gap;
+    for (int e = threadIdx.x; e < 256; e += blockDim.x) {
+        const int32_t f0 = (e & 3) ? mis : mat, f1 = ((e >> 2) & 3) ? mis : mat;
+        const int32_t f2 = ((e >> 4) & 3) ? mis : mat, f3 = ((e >> 6) & 3) ? mis : mat;
+        tab[2 * e] = int32_t(pack2(f0, f1));
+        tab[2 * e + 1] = int32_t(pack2(f2, f3));
+    }
+    __syncthreads();
+}
+
+// The lane's CG cells in kDna16.  P1 holds d-1, P2 holds d-2 and receives d; upb / lfb are
+// the neighbouring lanes' registers holding the slot before the first / after the last
+// (kDead2 at the group's ends).  nbv: slots outside the band, slot p at bit p and slot
+// CG/2 + p at bit 16 + p.  nth2: -theta in both halves.  Returns the packed maximum of the
+// new slots (-1 where none is live) and the dead mask in the layout of nbv.
+template <int CG, bool ODD>
+__device__ __forceinline__ void cells16(uint32_t (&P1)[CG / 2], uint32_t (&P2)[CG / 2], uint32_t upb,
+                                        uint32_t lfb, const Res<CG, kDna16>& res, uint32_t nbv, uint32_t nth2,
+                                        const int32_t* tab, uint32_t& mx, uint32_t& dacc) {
+    constexpr int H = CG / 2;
+    static_assert(CG % 4 == 0 && H <= 16, "slots come in pairs of registers");
+    const uint64_t x = res.hs ^ res.vs;
+    const int2* t2 = reinterpret_cast<const int2*>(tab);
+    mx = kDead2;
+    dacc = 0;
+#pragma unroll
+    for (int q = 0; q < H / 2; q++) {
+        const int2 s2 = t2[uint32_t(x >> (8 * q)) & 0xffu];
+        uint32_t v[2];
+#pragma unroll
+        for (int r = 0; r < 2; r++) {
+            const int p = 2 * q + r;
+            uint32_t up, lf;
+            if (ODD) {
+                up = p > 0 ? P1[p - 1] : __byte_perm(upb, P1[H - 1], 0x5432);
+                lf = P1[p];
+            } else {
+                up = P1[p];
+                lf = p < H - 1 ? P1[p + 1] : __byte_perm(P1[0], lfb, 0x5432);
+            }
+            const uint32_t raw = __viaddmax_s16x2(P2[p], uint32_t(r ? s2.y : s2.x), __vmaxs2(up, lf));
+            uint32_t u = __viaddmax_s16x2(raw, nth2, 0x80008000u);   // raw - theta
+            u |= (nbv << (15 - p)) & 0x80008000u;                   // outside the band: negative
+            const uint32_t M = sign_spread(u);
+            v[r] = raw | M;
+            P2[p] = v[r];
+            dacc |= M & ((1u << p) | (1u << (16 + p)));
+        }
+        mx = __vimax3_s16x2(mx, v[0], v[1]);
+    }
+}
+
+// Lane-local slot of the first (lowest) slot of V holding z, or -1.
+template <int CG>
+__device__ __forceinline__ int32_t first_of16(const uint32_t (&V)[CG / 2], int32_t z) {
+    constexpr int H = CG / 2;
+    const uint32_t nz2 = (uint32_t(-z) & 0xffffu) * 0x10001u;
+    uint32_t lt = 0;
+#pragma unroll
+    for (int p = 0; p < H; p++) {
+        const uint32_t t = __viaddmax_s16x2(V[p], nz2, 0x80008000u);   // v - z, negative where v < z
+        lt |= (t >> (15 - p)) & ((1u << p) | (1u << (16 + p)));
+    }
+    const uint32_t hm = (1u << H) - 1u;
+    const uint32_t eq = ~lt & (hm * 0x10001u);
+    return __ffs((eq & hm) | ((eq >> 16) << H)) - 1;
+}
 
 template <int G>
 __device__ __forceinline__ int32_t gmax(int32_t v, uint32_t gm) {
@@ -417,6 +582,110 @@ __device__ __forceinline__ int group_step(SideState& s, Res<CG, A>& res, int32_t
     const int32_t lv = kmax >> 6;
     const int32_t wmax = gmax<G>(lv, gm);
     const int32_t arg = ib + gmin<G>(lv == wmax ? sb + (63 - (kmax & 63)) : INT32_MAX, gm);
+    s.L = ib + first;
+    s.U = ib + last;
+    if (wmax > s.T) {
+        s.T = wmax;
+        s.best = wmax;
+        s.bi = arg;
+        s.bj = d - arg;
+    }
+    s.barg = arg;
+    s.d = d + 1;
+    return d == s.m + s.n ? kDone : kCont;
+}
+
+// One anti-diagonal of the group's side extension in kDna16 (the steps of group_step, on
+// packed scores).
+template <int G, int CG, bool ODD>
+__device__ __forceinline__ int group_step16(SideState& s, Res<CG, kDna16>& res, uint32_t (&P1)[CG / 2],
+                                            uint32_t (&P2)[CG / 2], const Problem& P, const int32_t* tab, int gl,
+                                            uint32_t gm, int32_t* gsm) {
+    constexpr int W = G * CG, H = CG / 2;
+    const int32_t d = s.d;
+    int32_t ib = (d >> 1) + s.rb;
+    int32_t lo, hi;
+    band_of(s, P, d, lo, hi);
+    int32_t slo = lo - ib, shi = hi - ib;
+    if (slo < 1 || shi > W - 2) {
+        const int32_t w = hi - lo + 1;
+        if (w > W - 2) return kOverflow;
+        const int32_t k = slo - (1 + (W - 2 - w) / 2);
+        // re-centre through the group's shared row, one int per slot in slot order
+#pragma unroll
+        for (int p = 0; p < H; p++) {
+            gsm[gl * CG + p] = lo16(P1[p]);
+            gsm[gl * CG + H + p] = hi16(P1[p]);
+            gsm[W + gl * CG + p] = lo16(P2[p]);
+            gsm[W + gl * CG + H + p] = hi16(P2[p]);
+        }
+        if (G > 1) __syncwarp(gm);
+#pragma unroll
+        for (int p = 0; p < H; p++) {
+            const int a = gl * CG + p + k, b = a + H;
+            const bool ia = a >= 0 && a < W, ibb = b >= 0 && b < W;
+            P1[p] = pack2(ia ? gsm[a] : -1, ibb ? gsm[b] : -1);
+            P2[p] = pack2(ia ? gsm[W + a] : -1, ibb ? gsm[W + b] : -1);
+        }
+        if (G > 1) __syncwarp(gm);
+        s.rb += k;
+        ib += k;
+        slo -= k;
+        shi -= k;
+        s.refresh = true;
+        if (gl == 0) atomicAdd(&P.stats[8], 1ull);
+    }
+    const int32_t sb = gl * CG;
+    update_slices<CG, ODD, kDna16>(s, res, P, int64_t(ib) - 1 + sb, int64_t(d) - ib - 1 - sb);
+    const uint32_t nb = ~slot_mask(slo - sb, shi - sb, CG);
+    const uint32_t nbv = H == 16 ? nb : ((nb & ((1u << H) - 1u)) | ((nb >> H) << 16));
+    int32_t zb = s.B0 + P.gap * d;
+    int32_t theta = s.T - P.X - zb;
+    if (theta > kTheta16) {
+        // rebase: every slot falls by delta, dead slots stay at -1
+        const int32_t delta = theta - kTheta0;
+        const uint32_t nd2 = (uint32_t(-delta) & 0xffffu) * 0x10001u;
+#pragma unroll
+        for (int p = 0; p < H; p++) {
+            P1[p] = __viaddmax_s16x2(P1[p], nd2, kDead2);
+            P2[p] = __viaddmax_s16x2(P2[p], nd2, kDead2);
+        }
+        s.B0 += delta;
+        zb += delta;
+        theta -= delta;
+    }
+    const uint32_t nth2 = (uint32_t(-theta) & 0xffffu) * 0x10001u;
+    uint32_t upb = kDead2, lfb = kDead2;
+    if (G > 1) {
+        if (ODD) {
+            upb = __shfl_up_sync(gm, P1[H - 1], 1, G);
+            if (gl == 0) upb = kDead2;
+        } else {
+            lfb = __shfl_down_sync(gm, P1[0], 1, G);
+            if (gl == G - 1) lfb = kDead2;
+        }
+    }
+    uint32_t mx, dacc;
+    cells16<CG, ODD>(P1, P2, upb, lfb, res, nbv, nth2, tab, mx, dacc);
+    s.cells += uint64_t(hi - lo + 1);
+    const uint32_t hm = (1u << H) - 1u;
+    const uint32_t lv = ~dacc & (hm * 0x10001u);
+    const uint32_t lm = (lv & hm) | ((lv >> 16) << H);
+    const bool any = lm != 0;
+    int32_t first = any ? sb + __ffs(lm) - 1 : INT32_MAX;
+    int32_t last = any ? sb + 31 - __clz(lm) : -1;
+    first = gmin<G>(first, gm);
+    if (first == INT32_MAX) return kDone;
+    last = gmax<G>(last, gm);
+    const int32_t zl = max(lo16(mx), hi16(mx));
+    const int32_t zw = gmax<G>(zl, gm);
+    const int32_t wmax = zw + zb;
+    int32_t arg = s.barg;
+    if (P.delta || wmax > s.T) {
+        // lowest i holding the maximum: needed for a new best, or to centre a restricted band
+        const int32_t a = zl == zw ? sb + first_of16<CG>(P2, zw) : INT32_MAX;
+        arg = ib + gmin<G>(a, gm);
+    }
     s.L = ib + first;
     s.U = ib + last;
     if (wmax > s.T) {
@@ -591,6 +860,80 @@ __device__ __forceinline__ bool load_record(const Problem& P, uint32_t ri, SideS
     return true;
 }
 
+// kDna16 records: the same layout, scores converted to and from S (dead slots: kNegR).
+template <int G, int CG>
+__device__ __forceinline__ void save_record16(const Problem& P, uint32_t ri, const SideState& s,
+                                              const uint32_t (&P1)[CG / 2], const uint32_t (&P2)[CG / 2], int gl) {
+    constexpr int W = G * CG, H = CG / 2;
+    int32_t* r = P.rec + ri;
+    const int32_t z1 = s.B0 + P.gap * (s.d - 1), z2 = s.B0 + P.gap * (s.d - 2);
+#pragma unroll
+    for (int p = 0; p < H; p++) {
+        const int32_t a = lo16(P1[p]), b = hi16(P1[p]), c = lo16(P2[p]), e = hi16(P2[p]);
+        __stcg(r + kRecHeader + gl * CG + p, a >= 0 ? a + z1 : kNegR);
+        __stcg(r + kRecHeader + gl * CG + H + p, b >= 0 ? b + z1 : kNegR);
+        __stcg(r + kRecHeader + W + gl * CG + p, c >= 0 ? c + z2 : kNegR);
+        __stcg(r + kRecHeader + W + gl * CG + H + p, e >= 0 ? e + z2 : kNegR);
+    }
+    if (gl == 0) {
+        __stcg(r + 0, W);
+        __stcg(r + 1, s.d);
+        __stcg(r + 2, s.rb);
+        __stcg(r + 3, s.L);
+        __stcg(r + 4, s.U);
+        __stcg(r + 5, s.T);
+        __stcg(r + 6, s.best);
+        __stcg(r + 7, s.bi);
+        __stcg(r + 8, s.bj);
+        __stcg(r + 9, s.barg);
+        __stcg(r + 10, int32_t(s.flags));
+        __stcg(r + 11, int32_t(uint32_t(s.cells)));
+        __stcg(r + 12, int32_t(uint32_t(s.cells >> 32)));
+    }
+}
+
+template <int G, int CG>
+__device__ __forceinline__ bool load_record16(const Problem& P, uint32_t ri, SideState& s, uint32_t (&A)[CG / 2],
+                                              uint32_t (&B)[CG / 2], int gl) {
+    constexpr int W = G * CG, H = CG / 2;
+    const int32_t* r = P.rec + ri;
+    const int32_t w0 = __ldcg(r + 0);
+    if (w0 > W) return false;
+    const int32_t off = (W - w0) / 2;
+    s.d = __ldcg(r + 1);
+    s.rb = __ldcg(r + 2) - off;
+    s.L = __ldcg(r + 3);
+    s.U = __ldcg(r + 4);
+    s.T = __ldcg(r + 5);
+    s.best = __ldcg(r + 6);
+    s.bi = __ldcg(r + 7);
+    s.bj = __ldcg(r + 8);
+    s.barg = __ldcg(r + 9);
+    s.flags = uint32_t(__ldcg(r + 10));
+    s.cells = uint64_t(uint32_t(__ldcg(r + 11))) | (uint64_t(uint32_t(__ldcg(r + 12))) << 32);
+    // theta of the next anti-diagonal at kTheta0
+    s.B0 = s.T - P.X - P.gap * s.d - kTheta0;
+    const int32_t z1 = s.B0 + P.gap * (s.d - 1), z2 = s.B0 + P.gap * (s.d - 2);
+    const bool odd = s.d & 1;   // odd d: A holds d-1; even d: B holds d-1
+    int32_t v1[2], v2[2];
+#pragma unroll
+    for (int p = 0; p < H; p++) {
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int src = gl * CG + p + h * H - off;
+            const bool in = src >= 0 && src < w0;
+            const int32_t x1 = in ? __ldcg(r + kRecHeader + src) : kNegR;
+            const int32_t x2 = in ? __ldcg(r + kRecHeader + w0 + src) : kNegR;
+            v1[h] = x1 < kDeadR ? -1 : x1 - z1;
+            v2[h] = x2 < kDeadR ? -1 : x2 - z2;
+        }
+        const uint32_t a = pack2(v1[0], v1[1]), b = pack2(v2[0], v2[1]);
+        A[p] = odd ? a : b;
+        B[p] = odd ? b : a;
+    }
+    return true;
+}
+
 // Runs side extensions from S with groups of G lanes until S is exhausted; overflows go to
 // q[out_q], carrying an escalation record when the next level is a register level.
 // gsm_block: the block's shared rows (2W ints per group).
@@ -607,7 +950,11 @@ __device__ __forceinline__ void group_loop(const Problem& P, const Queues& Q, co
     const uint32_t gm = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane - gl));
     const int32_t* tab = smem;
     int32_t* gsm = smem + kLutInts + (threadIdx.x >> 5) * warp_ints + ((threadIdx.x & 31) / G) * 2 * W;
-    int32_t R0[CG], R1[CG];
+    // kDna16: CG/2 registers of two 16-bit slots each, else CG int32 slots
+    constexpr bool PK = A == kDna16;
+    constexpr int NR = PK ? CG / 2 : CG;
+    using Reg = std::conditional_t<PK, uint32_t, int32_t>;
+    Reg R0[NR], R1[NR];
     SideState s{};
     Res<CG, A> res;
     uint32_t uidx = 0, pair = 0, next = 0, end = 0;
@@ -619,7 +966,8 @@ __device__ __forceinline__ void group_loop(const Problem& P, const Queues& Q, co
             bool got = false;
             while (next_unit<G>(S, gl, lane, gm, chunk, next, end, uidx, P.err)) {
                 const Unit u = P.units[uidx];
-                if ((int64_t(u.m) + u.n) * P.max_abs >= kRegLimit || P.alpha != A) {
+                if ((int64_t(u.m) + u.n) * P.max_abs >= kRegLimit || P.alpha != alpha_of(A) ||
+                    (PK && !dna16_ok(P))) {
                     if (gl == 0) push_unit(Q, kBandQ, uidx);
                     continue;
                 }
@@ -638,14 +986,31 @@ __device__ __forceinline__ void group_loop(const Problem& P, const Queues& Q, co
                 continue;
             }
             const uint32_t ri = P.rec_of ? __ldcg(P.rec_of + uidx) : kNoUnit;
-            if (ri == kNoUnit || !load_record<G, CG>(P, ri, s, R0, R1, gl)) {
+            bool resumed = false;
+            if (ri != kNoUnit) {
+                if constexpr (PK) resumed = load_record16<G, CG>(P, ri, s, R0, R1, gl);
+                else resumed = load_record<G, CG>(P, ri, s, R0, R1, gl);
+            }
+            if (!resumed) {
                 // S(0,0) = 0 in the middle of the window, every other cell -inf (Sec. 2.2)
+                if constexpr (PK) {
+                    constexpr int t0 = (W / 2) % CG, p0 = t0 % (CG / 2);
+                    s.B0 = -P.X - P.gap - kTheta0;   // theta of d = 1 at kTheta0
+                    const int32_t z0 = -s.B0;
 #pragma unroll
-                for (int t = 0; t < CG; t++) {
-                    R0[t] = kNegR;
-                    R1[t] = kNegR;
+                    for (int p = 0; p < NR; p++) {
+                        R0[p] = kDead2;
+                        R1[p] = kDead2;
+                    }
+                    if (gl == (W / 2) / CG) R0[p0] = t0 < CG / 2 ? pack2(z0, -1) : pack2(-1, z0);
+                } else {
+#pragma unroll
+                    for (int t = 0; t < CG; t++) {
+                        R0[t] = kNegR;
+                        R1[t] = kNegR;
+                    }
+                    if (gl == (W / 2) / CG) R0[(W / 2) % CG] = 0;
                 }
-                if (gl == (W / 2) / CG) R0[(W / 2) % CG] = 0;
             }
             skip_odd = (s.d & 1) == 0;   // a side continued on an even anti-diagonal
             active = true;
@@ -653,9 +1018,15 @@ __device__ __forceinline__ void group_loop(const Problem& P, const Queues& Q, co
             cells_start = s.cells;
         }
         int r = kCont;
-        if (!skip_odd) r = group_step<G, CG, true, A>(s, res, R0, R1, P, tab, gl, gm, gsm);
-        skip_odd = false;
-        if (r == kCont) r = group_step<G, CG, false, A>(s, res, R1, R0, P, tab, gl, gm, gsm);
+        if constexpr (PK) {
+            if (!skip_odd) r = group_step16<G, CG, true>(s, res, R0, R1, P, tab, gl, gm, gsm);
+            skip_odd = false;
+            if (r == kCont) r = group_step16<G, CG, false>(s, res, R1, R0, P, tab, gl, gm, gsm);
+        } else {
+            if (!skip_odd) r = group_step<G, CG, true, A>(s, res, R0, R1, P, tab, gl, gm, gsm);
+            skip_odd = false;
+            if (r == kCont) r = group_step<G, CG, false, A>(s, res, R1, R0, P, tab, gl, gm, gsm);
+        }
         if (r == kCont) continue;
         active = false;
         if (gl == 0) {
@@ -679,8 +1050,13 @@ __device__ __forceinline__ void group_loop(const Problem& P, const Queues& Q, co
             if (gl == 0) ri = atomicAdd(P.rec_ctr, need);
             if (G > 1) ri = __shfl_sync(gm, ri, lane - gl);
             if (ri <= P.rec_cap && P.rec_cap - ri >= need) {
-                if (s.d & 1) save_record<G, CG>(P, ri, s, R0, R1, gl);
-                else save_record<G, CG>(P, ri, s, R1, R0, gl);
+                if constexpr (PK) {
+                    if (s.d & 1) save_record16<G, CG>(P, ri, s, R0, R1, gl);
+                    else save_record16<G, CG>(P, ri, s, R1, R0, gl);
+                } else {
+                    if (s.d & 1) save_record<G, CG>(P, ri, s, R0, R1, gl);
+                    else save_record<G, CG>(P, ri, s, R1, R0, gl);
+                }
                 if (G > 1) __syncwarp(gm);
             } else {
                 ri = kNoUnit;

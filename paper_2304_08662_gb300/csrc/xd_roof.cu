@@ -26,6 +26,7 @@ enum ProbeOp {
     kProbeVmax16 = 10,     // 16x2: x = max(x, y) per half
     kProbeCellDna = 100,   // the register tiers' cell update (cells_of), DNA, 32 slots
     kProbeCellProt = 101,  // the same, protein (similarity-table offsets), 32 slots
+    kProbeCellDna16 = 102, // the 16-bit packed DNA update (cells16 + first-maximum search)
 };
 
 template <int OP>
@@ -116,6 +117,43 @@ __global__ void __launch_bounds__(128, 2) k_probe_cells(int32_t* out, int iters,
     if (acc == uint32_t(seed) && kmax == seed) out[blockIdx.x] = int32_t(acc);
 }
 
+// The packed DNA update of the group kernels (cells16, then the search for the first
+// maximum) on 32 slots held in 16 registers, alternating odd / even anti-diagonals, every
+// slot inside the band.
+__global__ void __launch_bounds__(128, 2) k_probe_cells16(int32_t* out, int iters, int32_t seed) {
+    __shared__ __align__(16) int32_t tab[kLutInts];
+    Problem P{};
+    P.sim[0] = 1;
+    P.sim[1] = -1;
+    P.gap = -1;
+    build_table16(tab, P);
+    uint32_t R0[16], R1[16];
+#pragma unroll
+    for (int t = 0; t < 16; t++) {
+        R0[t] = pack2(2000 + ((t * 7 + seed) & 15), 2000 + ((t * 5 + seed) & 15));
+        R1[t] = pack2(2000 + ((t * 3 + seed) & 15), 2000 + ((t * 11 + seed) & 15));
+    }
+    Res<32, kDna16> res;
+    uint64_t x = 0x9E3779B97F4A7C15ull ^ uint64_t(threadIdx.x) * 0xBF58476D1CE4E5B9ull;
+    res.hs = x;
+    res.vs = x * 0x94D049BB133111EBull;
+    uint32_t nth2 = (uint32_t(-1960) & 0xffffu) * 0x10001u, acc = 0;
+    int32_t z = 0;
+    for (int k = 0; k < iters; k++) {
+        uint32_t mx, dacc;
+        cells16<32, true>(R0, R1, kDead2, kDead2, res, 0u, nth2, tab, mx, dacc);
+        z = max(lo16(mx), hi16(mx));
+        acc ^= dacc ^ uint32_t(first_of16<32>(R1, z));
+        nth2 = (uint32_t(40 - z) & 0xffffu) * 0x10001u;
+        cells16<32, false>(R1, R0, kDead2, kDead2, res, 0u, nth2, tab, mx, dacc);
+        z = max(lo16(mx), hi16(mx));
+        acc ^= dacc ^ uint32_t(first_of16<32>(R0, z));
+        nth2 = (uint32_t(40 - z) & 0xffffu) * 0x10001u;
+        res.hs = (res.hs << 2) | (res.hs >> 62);
+    }
+    if (acc == uint32_t(seed) && z == seed) out[blockIdx.x] = int32_t(acc);
+}
+
 template <int OP>
 static cudaError_t run_probe(int blocks, int iters, cudaStream_t st, int32_t* out) {
     k_probe<OP><<<blocks, 256, 0, st>>>(out, iters, 12345);
@@ -131,7 +169,7 @@ cudaError_t probe_rate(int op, int n_sm, double* rate, float* ms_out) {
     cudaEventCreate(&a);
     cudaEventCreate(&b);
     const int blocks = n_sm * 8;
-    const bool cells = op == kProbeCellDna || op == kProbeCellProt;
+    const bool cells = op == kProbeCellDna || op == kProbeCellProt || op == kProbeCellDna16;
     int iters = cells ? 4000 : 20000;
     double per_thread = 0;
     int threads = 256;
@@ -153,6 +191,9 @@ cudaError_t probe_rate(int op, int n_sm, double* rate, float* ms_out) {
                 return cudaGetLastError();
             case kProbeCellProt:
                 k_probe_cells<20><<<n_sm * 2, 128, 0, 0>>>(out, iters, 12345);
+                return cudaGetLastError();
+            case kProbeCellDna16:
+                k_probe_cells16<<<n_sm * 2, 128, 0, 0>>>(out, iters, 12345);
                 return cudaGetLastError();
             default: return cudaErrorInvalidValue;
         }

@@ -1,5 +1,6 @@
-// Register tiers: the fused DNA grids (A = 4) and the dispatch of register levels to the
-// DNA or protein kernels.  The kernels themselves are the templates of xd_group.cuh.
+// Register tiers: the fused DNA grids (16-bit packed scores, A = kDna16) and the dispatch
+// of register levels to the DNA (packed or 32-bit) or protein kernels.  The kernels
+// themselves are the templates of xd_group.cuh.
 #include "xd_group.cuh"
 
 namespace xd {
@@ -35,7 +36,11 @@ cudaError_t launch_level(const Problem& P, const Queues& Q, const TierConfig& cf
     const int out_q = level == cfg.n_levels - 1 ? kBandQ : level;
     const int blocks = n_sm * cfg.blocks_per_sm[v];
     if (P.alpha == 20) return launch_level_prot(P, Q, v, in_q, out_q, blocks, cfg.chunk, st);
+    if (dna16_ok(P)) return launch_level_dna16(P, Q, v, in_q, out_q, blocks, cfg.chunk, st);
     return launch_level_dna(P, Q, v, in_q, out_q, blocks, cfg.chunk, st);
+}
+
+bool dna16_batch(const Problem& P) { return dna16_ok(P);
 }
 
 bool fused_supported(const TierConfig& c, int alpha) {
@@ -55,25 +60,26 @@ cudaError_t launch_fused_levels(const Problem& P, const Queues& Q, const TierCon
                                 cudaStream_t st) {
     const int a = cfg.variant[0], b = cfg.variant[1], d = cfg.variant[2];
     if (P.alpha == 20) return launch_fused_levels_prot(P, Q, cfg, n_sm, st);
-    if (a == kG1C32 && b == kG4C32 && d == kG8C32) return launch_fused<1, 32, 4, 32, 8, 32, 2, 4>(P, Q, cfg, n_sm, st);
-    if (a == kG1C32 && b == kG8C16 && d == kG16C16) return launch_fused<1, 32, 8, 16, 16, 16, 2, 4>(P, Q, cfg, n_sm, st);
+    if (!dna16_ok(P)) return cudaErrorInvalidValue;   // DNA grids are compiled packed only
+    if (a == kG1C32 && b == kG4C32 && d == kG8C32) return launch_fused<1, 32, 4, 32, 8, 32, 2, kDna16>(P, Q, cfg, n_sm, st);
+    if (a == kG1C32 && b == kG8C16 && d == kG16C16) return launch_fused<1, 32, 8, 16, 16, 16, 2, kDna16>(P, Q, cfg, n_sm, st);
     if (a == kG1C32 && b == kG16C16 && d == kG32C16)
-        return cfg.fused_minb == 4   ? launch_fused<1, 32, 16, 16, 32, 16, 4, 4>(P, Q, cfg, n_sm, st)
-               : cfg.fused_minb == 3 ? launch_fused<1, 32, 16, 16, 32, 16, 3, 4>(P, Q, cfg, n_sm, st)
-               : cfg.long_shape == 1 ? launch_fused<1, 32, 16, 16, 32, 16, 2, 4, 8, 4>(P, Q, cfg, n_sm, st)
-               : cfg.long_shape == 2 ? launch_fused<1, 32, 16, 16, 32, 16, 2, 4, 4, 8>(P, Q, cfg, n_sm, st)
-                                     : launch_fused<1, 32, 16, 16, 32, 16, 2, 4, 32, 4>(P, Q, cfg, n_sm, st);
-    if (a == kG1C32 && b == kG8C16 && d == kG32C16) return launch_fused<1, 32, 8, 16, 32, 16, 2, 4>(P, Q, cfg, n_sm, st);
-    if (a == kG1C32 && b == kG32C8 && d == kG32C16) return launch_fused<1, 32, 32, 8, 32, 16, 2, 4, 32, 4>(P, Q, cfg, n_sm, st);
-    if (a == kG1C16 && b == kG32C8 && d == kG32C16) return launch_fused<1, 16, 32, 8, 32, 16, 2, 4, 32, 4>(P, Q, cfg, n_sm, st);
-    if (a == kG1C16 && b == kG1C32 && d == kG16C16) return launch_fused<1, 16, 1, 32, 16, 16, 2, 4, 32, 4>(P, Q, cfg, n_sm, st);
-    if (a == kG1C24 && b == kG16C16 && d == kG32C16) return launch_fused<1, 24, 16, 16, 32, 16, 2, 4, 32, 4>(P, Q, cfg, n_sm, st);
-    if (a == kG1C20 && b == kG16C16 && d == kG32C16) return launch_fused<1, 20, 16, 16, 32, 16, 2, 4, 32, 4>(P, Q, cfg, n_sm, st);
-    if (a == kG1C32 && b == kG8C32 && d == kG32C16) return launch_fused<1, 32, 8, 32, 32, 16, 2, 4, 8, 4>(P, Q, cfg, n_sm, st);
-    if (a == kG1C32 && b == kG8C32 && d == kG16C32) return launch_fused<1, 32, 8, 32, 16, 32, 2, 4, 8, 4>(P, Q, cfg, n_sm, st);
-    if (a == kG1C16 && b == kG4C16 && d == kG16C16) return launch_fused<1, 16, 4, 16, 16, 16, 3, 4>(P, Q, cfg, n_sm, st);
-    if (a == kG1C16 && b == kG8C16 && d == kG32C16) return launch_fused<1, 16, 8, 16, 32, 16, 3, 4>(P, Q, cfg, n_sm, st);
-    if (a == kG4C16 && b == kG16C16 && d == kG32C32) return launch_fused<4, 16, 16, 16, 32, 32, 2, 4, 32, 4>(P, Q, cfg, n_sm, st);
+        return cfg.fused_minb == 4   ? launch_fused<1, 32, 16, 16, 32, 16, 4, kDna16>(P, Q, cfg, n_sm, st)
+               : cfg.fused_minb == 3 ? launch_fused<1, 32, 16, 16, 32, 16, 3, kDna16>(P, Q, cfg, n_sm, st)
+               : cfg.long_shape == 1 ? launch_fused<1, 32, 16, 16, 32, 16, 2, kDna16, 8, 4>(P, Q, cfg, n_sm, st)
+               : cfg.long_shape == 2 ? launch_fused<1, 32, 16, 16, 32, 16, 2, kDna16, 4, 8>(P, Q, cfg, n_sm, st)
+                                     : launch_fused<1, 32, 16, 16, 32, 16, 2, kDna16, 32, 4>(P, Q, cfg, n_sm, st);
+    if (a == kG1C32 && b == kG8C16 && d == kG32C16) return launch_fused<1, 32, 8, 16, 32, 16, 2, kDna16>(P, Q, cfg, n_sm, st);
+    if (a == kG1C32 && b == kG32C8 && d == kG32C16) return launch_fused<1, 32, 32, 8, 32, 16, 2, kDna16, 32, 4>(P, Q, cfg, n_sm, st);
+    if (a == kG1C16 && b == kG32C8 && d == kG32C16) return launch_fused<1, 16, 32, 8, 32, 16, 2, kDna16, 32, 4>(P, Q, cfg, n_sm, st);
+    if (a == kG1C16 && b == kG1C32 && d == kG16C16) return launch_fused<1, 16, 1, 32, 16, 16, 2, kDna16, 32, 4>(P, Q, cfg, n_sm, st);
+    if (a == kG1C24 && b == kG16C16 && d == kG32C16) return launch_fused<1, 24, 16, 16, 32, 16, 2, kDna16, 32, 4>(P, Q, cfg, n_sm, st);
+    if (a == kG1C20 && b == kG16C16 && d == kG32C16) return launch_fused<1, 20, 16, 16, 32, 16, 2, kDna16, 32, 4>(P, Q, cfg, n_sm, st);
+    if (a == kG1C32 && b == kG8C32 && d == kG32C16) return launch_fused<1, 32, 8, 32, 32, 16, 2, kDna16, 8, 4>(P, Q, cfg, n_sm, st);
+    if (a == kG1C32 && b == kG8C32 && d == kG16C32) return launch_fused<1, 32, 8, 32, 16, 32, 2, kDna16, 8, 4>(P, Q, cfg, n_sm, st);
+    if (a == kG1C16 && b == kG4C16 && d == kG16C16) return launch_fused<1, 16, 4, 16, 16, 16, 3, kDna16>(P, Q, cfg, n_sm, st);
+    if (a == kG1C16 && b == kG8C16 && d == kG32C16) return launch_fused<1, 16, 8, 16, 32, 16, 3, kDna16>(P, Q, cfg, n_sm, st);
+    if (a == kG4C16 && b == kG16C16 && d == kG32C32) return launch_fused<4, 16, 16, 16, 32, 32, 2, kDna16, 32, 4>(P, Q, cfg, n_sm, st);
     return cudaErrorInvalidValue;
 }
 
