@@ -46,26 +46,39 @@ constexpr int64_t kRegLimit = int64_t(1) << 23;
 // argument A; the alphabet is DNA).
 //
 // Register p of a lane holds slot p in its low half and slot p + CG/2 in its high half, so
-// one 16x2 DPX instruction updates two cells.  A score S of anti-diagonal d is kept as
-// z = S - (B0 + gap * d).  With the base falling by |gap| per anti-diagonal, the gap
+// one 16x2 DPX instruction updates two cells.  A score S of anti-diagonal d is kept as 32 z
+// with z = S - (B0 + gap * d).  With the base falling by |gap| per anti-diagonal, the gap
 // predecessors (d-1) need no adjustment and the diagonal one (d-2) gains the constant
 // -2 gap, which the similarity table already holds: the cell of Sec. 2.2 becomes
-// max(max(up, left), diag + Sim - 2 gap), two instructions for two cells.  The X-Drop
-// threshold T - X of anti-diagonal d sits at z = theta_d; it starts at kTheta0 and grows by
-// |gap| per anti-diagonal plus the growth of T, and every slot is rebased once it passes
-// kTheta16.  Dead cells hold -1 (all ones), so anything computed from them stays below
-// theta, and the live test is the sign of z - theta.  Live z lie in
-// [theta - s_max, theta + X + s_max], within 16 bits when X <= kMaxX16, -127 <= gap <= 0
-// and |Sim| <= 127.
+// max(max(up, left), diag + 32 (Sim - 2 gap)), two instructions for two cells.  The low
+// five bits of a live slot are zero, so one add-max of 31 - slot per register yields the
+// best cell of the lane together with its lowest slot (ties: lowest i).  The X-Drop
+// threshold T - X of anti-diagonal d sits at z = theta_d; theta starts at theta0 and grows
+// by |gap| per anti-diagonal plus the growth of T, and every slot is rebased once theta
+// passes theta1.  Dead cells hold -1 (all ones): anything computed from them stays below
+// 32 theta, and the live test is the sign of the slot minus 32 theta.
+//   theta0 = 2 (|gap| + s_max) + 1: a dead slot plus 32 (Sim - 2 gap) stays below
+//            32 theta, and live slots stay positive across a rebase;
+//   theta1 = 1022 - X - s_max: live z <= theta + X + s_max, so 32 z + 31 < 2^15.
+// A batch takes these levels when theta1 - theta0 >= 64 and -127 <= gap <= 0 (for scores
+// 1 / -1 / -1: X <= 952); other DNA batches take the 32-bit levels.
 constexpr int kDna16 = 2;
-constexpr int32_t kTheta0 = 1024;
-constexpr int32_t kTheta16 = 16384;
-constexpr int32_t kMaxX16 = 15000;
 constexpr uint32_t kDead2 = 0xffffffffu;
 
 __host__ __device__ constexpr int alpha_of(int A) { return A == kDna16 ? 4 : A; }
+
+struct Z16 {
+    int32_t th0, th1;
+};
+__host__ __device__ inline Z16 z16_of(const Problem& P) {
+    const int32_t a = P.sim[0], b = P.sim[1];
+    const int32_t sm = a > b ? (a > 0 ? a : 0) : (b > 0 ? b : 0);
+    return Z16{2 * (sm - P.gap) + 1, 1022 - P.X - sm};
+}
 __host__ __device__ inline bool dna16_ok(const Problem& P) {
-    return P.alpha == 4 && P.X >= 0 && P.X <= kMaxX16 && P.gap <= 0 && P.gap >= -127;
+    if (P.alpha != 4 || P.gap > 0 || P.gap < -127 || P.X < 0 || P.X > 1022) return false;
+    const Z16 z = z16_of(P);
+    return z.th1 - z.th0 >= 64;
 }
 
 enum { kCont = 0, kDone = 1, kOverflow = 2 };
@@ -418,10 +431,10 @@ struct Res<CG, kDna16> {
     }
 };
 
-// The block's table for kDna16: 256 int2 entries; entry e holds Sim - 2 gap of the four
-// 2-bit fields of e (zero = match), fields 0 / 1 in .x (low / high half), 2 / 3 in .y.
+// The block's table for kDna16: 256 int2 entries; entry e holds 32 (Sim - 2 gap) of the
+// four 2-bit fields of e (zero = match), fields 0 / 1 in .x (low / high half), 2 / 3 in .y.
 __device__ __forceinline__ void build_table16(int32_t* tab, const Problem& P) {
-    const int32_t mat = P.sim[0] - 2 * P.gap, mis = P.sim[1] - 2 * P.gap;
+    const int32_t mat = 32 * (P.sim[0] - 2 * P.gap), mis = 32 * (P.sim[1] - 2 * P.gap);
     for (int e = threadIdx.x; e < 256; e += blockDim.x) {
         const int32_t f0 = (e & 3) ? mis : mat, f1 = ((e >> 2) & 3) ? mis : mat;
         const int32_t f2 = ((e >> 4) & 3) ? mis : mat, f3 = ((e >> 6) & 3) ? mis : mat;
@@ -434,22 +447,22 @@ __device__ __forceinline__ void build_table16(int32_t* tab, const Problem& P) {
 // The lane's CG cells in kDna16.  P1 holds d-1, P2 holds d-2 and receives d; upb / lfb are
 // the neighbouring lanes' registers holding the slot before the first / after the last
 // (kDead2 at the group's ends).  nbv: slots outside the band, slot p at bit p and slot
-// CG/2 + p at bit 16 + p.  nth2: -theta in both halves.  Returns the packed maximum of the
-// new slots (-1 where none is live) and the dead mask in the layout of nbv.
+// CG/2 + p at bit 16 + p.  nth2: -32 theta in both halves.  Returns the packed maximum of
+// slot + 31 - lane slot over the new slots (the lane's best cell and its lowest slot; at
+// most 30 when none is live) and the dead mask in the layout of nbv.
 template <int CG, bool ODD>
 __device__ __forceinline__ void cells16(uint32_t (&P1)[CG / 2], uint32_t (&P2)[CG / 2], uint32_t upb,
                                         uint32_t lfb, const Res<CG, kDna16>& res, uint32_t nbv, uint32_t nth2,
-                                        const int32_t* tab, uint32_t& mx, uint32_t& dacc) {
+                                        const int32_t* tab, uint32_t& mk, uint32_t& dacc) {
     constexpr int H = CG / 2;
     static_assert(CG % 4 == 0 && H <= 16, "slots come in pairs of registers");
     const uint64_t x = res.hs ^ res.vs;
     const int2* t2 = reinterpret_cast<const int2*>(tab);
-    mx = kDead2;
+    mk = kDead2;
     dacc = 0;
 #pragma unroll
     for (int q = 0; q < H / 2; q++) {
         const int2 s2 = t2[uint32_t(x >> (8 * q)) & 0xffu];
-        uint32_t v[2];
 #pragma unroll
         for (int r = 0; r < 2; r++) {
             const int p = 2 * q + r;
@@ -462,31 +475,16 @@ __device__ __forceinline__ void cells16(uint32_t (&P1)[CG / 2], uint32_t (&P2)[C
                 lf = p < H - 1 ? P1[p + 1] : __byte_perm(P1[0], lfb, 0x5432);
             }
             const uint32_t raw = __viaddmax_s16x2(P2[p], uint32_t(r ? s2.y : s2.x), __vmaxs2(up, lf));
-            uint32_t u = __viaddmax_s16x2(raw, nth2, 0x80008000u);   // raw - theta
+            uint32_t u = __viaddmax_s16x2(raw, nth2, 0x80008000u);   // raw - 32 theta
             u |= (nbv << (15 - p)) & 0x80008000u;                   // outside the band: negative
             const uint32_t M = sign_spread(u);
-            v[r] = raw | M;
-            P2[p] = v[r];
+            const uint32_t v = raw | M;
+            P2[p] = v;
             dacc |= M & ((1u << p) | (1u << (16 + p)));
+            const uint32_t key = uint32_t(31 - p) | (uint32_t(31 - p - H) << 16);
+            mk = __viaddmax_s16x2(v, key, mk);
         }
-        mx = __vimax3_s16x2(mx, v[0], v[1]);
     }
-}
-
-// Lane-local slot of the first (lowest) slot of V holding z, or -1.
-template <int CG>
-__device__ __forceinline__ int32_t first_of16(const uint32_t (&V)[CG / 2], int32_t z) {
-    constexpr int H = CG / 2;
-    const uint32_t nz2 = (uint32_t(-z) & 0xffffu) * 0x10001u;
-    uint32_t lt = 0;
-#pragma unroll
-    for (int p = 0; p < H; p++) {
-        const uint32_t t = __viaddmax_s16x2(V[p], nz2, 0x80008000u);   // v - z, negative where v < z
-        lt |= (t >> (15 - p)) & ((1u << p) | (1u << (16 + p)));
-    }
-    const uint32_t hm = (1u << H) - 1u;
-    const uint32_t eq = ~lt & (hm * 0x10001u);
-    return __ffs((eq & hm) | ((eq >> 16) << H)) - 1;
 }
 
 template <int G>
@@ -599,8 +597,8 @@ __device__ __forceinline__ int group_step(SideState& s, Res<CG, A>& res, int32_t
 // packed scores).
 template <int G, int CG, bool ODD>
 __device__ __forceinline__ int group_step16(SideState& s, Res<CG, kDna16>& res, uint32_t (&P1)[CG / 2],
-                                            uint32_t (&P2)[CG / 2], const Problem& P, const int32_t* tab, int gl,
-                                            uint32_t gm, int32_t* gsm) {
+                                            uint32_t (&P2)[CG / 2], const Problem& P, const Z16& zc,
+                                            const int32_t* tab, int gl, uint32_t gm, int32_t* gsm) {
     constexpr int W = G * CG, H = CG / 2;
     const int32_t d = s.d;
     int32_t ib = (d >> 1) + s.rb;
@@ -641,10 +639,10 @@ __device__ __forceinline__ int group_step16(SideState& s, Res<CG, kDna16>& res, 
     const uint32_t nbv = H == 16 ? nb : ((nb & ((1u << H) - 1u)) | ((nb >> H) << 16));
     int32_t zb = s.B0 + P.gap * d;
     int32_t theta = s.T - P.X - zb;
-    if (theta > kTheta16) {
-        // rebase: every slot falls by delta, dead slots stay at -1
-        const int32_t delta = theta - kTheta0;
-        const uint32_t nd2 = (uint32_t(-delta) & 0xffffu) * 0x10001u;
+    if (theta > zc.th1) {
+        // rebase: every slot falls by 32 delta, dead slots stay at -1
+        const int32_t delta = theta - zc.th0;
+        const uint32_t nd2 = (uint32_t(-32 * delta) & 0xffffu) * 0x10001u;
 #pragma unroll
         for (int p = 0; p < H; p++) {
             P1[p] = __viaddmax_s16x2(P1[p], nd2, kDead2);
@@ -654,7 +652,7 @@ __device__ __forceinline__ int group_step16(SideState& s, Res<CG, kDna16>& res, 
         zb += delta;
         theta -= delta;
     }
-    const uint32_t nth2 = (uint32_t(-theta) & 0xffffu) * 0x10001u;
+    const uint32_t nth2 = (uint32_t(-32 * theta) & 0xffffu) * 0x10001u;
     uint32_t upb = kDead2, lfb = kDead2;
     if (G > 1) {
         if (ODD) {
@@ -665,8 +663,8 @@ __device__ __forceinline__ int group_step16(SideState& s, Res<CG, kDna16>& res, 
             if (gl == G - 1) lfb = kDead2;
         }
     }
-    uint32_t mx, dacc;
-    cells16<CG, ODD>(P1, P2, upb, lfb, res, nbv, nth2, tab, mx, dacc);
+    uint32_t mk, dacc;
+    cells16<CG, ODD>(P1, P2, upb, lfb, res, nbv, nth2, tab, mk, dacc);
     s.cells += uint64_t(hi - lo + 1);
     const uint32_t hm = (1u << H) - 1u;
     const uint32_t lv = ~dacc & (hm * 0x10001u);
@@ -677,15 +675,12 @@ __device__ __forceinline__ int group_step16(SideState& s, Res<CG, kDna16>& res, 
     first = gmin<G>(first, gm);
     if (first == INT32_MAX) return kDone;
     last = gmax<G>(last, gm);
-    const int32_t zl = max(lo16(mx), hi16(mx));
-    const int32_t zw = gmax<G>(zl, gm);
-    const int32_t wmax = zw + zb;
-    int32_t arg = s.barg;
-    if (P.delta || wmax > s.T) {
-        // lowest i holding the maximum: needed for a new best, or to centre a restricted band
-        const int32_t a = zl == zw ? sb + first_of16<CG>(P2, zw) : INT32_MAX;
-        arg = ib + gmin<G>(a, gm);
-    }
+    // best cell of the group: z, then 1023 - window slot (the lowest slot wins ties); a lane
+    // without live slots has a lane key <= 30 and loses to every live one (z >= theta0 > 0)
+    const int32_t kl = max(lo16(mk), hi16(mk));
+    const int32_t gk = gmax<G>(((kl >> 5) << 10) | (1023 - (sb + 31 - (kl & 31))), gm);
+    const int32_t wmax = (gk >> 10) + zb;
+    const int32_t arg = ib + 1023 - (gk & 1023);
     s.L = ib + first;
     s.U = ib + last;
     if (wmax > s.T) {
@@ -870,10 +865,10 @@ __device__ __forceinline__ void save_record16(const Problem& P, uint32_t ri, con
 #pragma unroll
     for (int p = 0; p < H; p++) {
         const int32_t a = lo16(P1[p]), b = hi16(P1[p]), c = lo16(P2[p]), e = hi16(P2[p]);
-        __stcg(r + kRecHeader + gl * CG + p, a >= 0 ? a + z1 : kNegR);
-        __stcg(r + kRecHeader + gl * CG + H + p, b >= 0 ? b + z1 : kNegR);
-        __stcg(r + kRecHeader + W + gl * CG + p, c >= 0 ? c + z2 : kNegR);
-        __stcg(r + kRecHeader + W + gl * CG + H + p, e >= 0 ? e + z2 : kNegR);
+        __stcg(r + kRecHeader + gl * CG + p, a >= 0 ? (a >> 5) + z1 : kNegR);
+        __stcg(r + kRecHeader + gl * CG + H + p, b >= 0 ? (b >> 5) + z1 : kNegR);
+        __stcg(r + kRecHeader + W + gl * CG + p, c >= 0 ? (c >> 5) + z2 : kNegR);
+        __stcg(r + kRecHeader + W + gl * CG + H + p, e >= 0 ? (e >> 5) + z2 : kNegR);
     }
     if (gl == 0) {
         __stcg(r + 0, W);
@@ -893,8 +888,8 @@ __device__ __forceinline__ void save_record16(const Problem& P, uint32_t ri, con
 }
 
 template <int G, int CG>
-__device__ __forceinline__ bool load_record16(const Problem& P, uint32_t ri, SideState& s, uint32_t (&A)[CG / 2],
-                                              uint32_t (&B)[CG / 2], int gl) {
+__device__ __forceinline__ bool load_record16(const Problem& P, const Z16& zc, uint32_t ri, SideState& s,
+                                              uint32_t (&A)[CG / 2], uint32_t (&B)[CG / 2], int gl) {
     constexpr int W = G * CG, H = CG / 2;
     const int32_t* r = P.rec + ri;
     const int32_t w0 = __ldcg(r + 0);
@@ -911,8 +906,8 @@ __device__ __forceinline__ bool load_record16(const Problem& P, uint32_t ri, Sid
     s.barg = __ldcg(r + 9);
     s.flags = uint32_t(__ldcg(r + 10));
     s.cells = uint64_t(uint32_t(__ldcg(r + 11))) | (uint64_t(uint32_t(__ldcg(r + 12))) << 32);
-    // theta of the next anti-diagonal at kTheta0
-    s.B0 = s.T - P.X - P.gap * s.d - kTheta0;
+    // theta of the next anti-diagonal at theta0
+    s.B0 = s.T - P.X - P.gap * s.d - zc.th0;
     const int32_t z1 = s.B0 + P.gap * (s.d - 1), z2 = s.B0 + P.gap * (s.d - 2);
     const bool odd = s.d & 1;   // odd d: A holds d-1; even d: B holds d-1
     int32_t v1[2], v2[2];
@@ -924,8 +919,8 @@ __device__ __forceinline__ bool load_record16(const Problem& P, uint32_t ri, Sid
             const bool in = src >= 0 && src < w0;
             const int32_t x1 = in ? __ldcg(r + kRecHeader + src) : kNegR;
             const int32_t x2 = in ? __ldcg(r + kRecHeader + w0 + src) : kNegR;
-            v1[h] = x1 < kDeadR ? -1 : x1 - z1;
-            v2[h] = x2 < kDeadR ? -1 : x2 - z2;
+            v1[h] = x1 < kDeadR ? -1 : 32 * (x1 - z1);
+            v2[h] = x2 < kDeadR ? -1 : 32 * (x2 - z2);
         }
         const uint32_t a = pack2(v1[0], v1[1]), b = pack2(v2[0], v2[1]);
         A[p] = odd ? a : b;
@@ -953,6 +948,7 @@ __device__ __forceinline__ void group_loop(const Problem& P, const Queues& Q, co
     // kDna16: CG/2 registers of two 16-bit slots each, else CG int32 slots
     constexpr bool PK = A == kDna16;
     constexpr int NR = PK ? CG / 2 : CG;
+    const Z16 zc = z16_of(P);
     using Reg = std::conditional_t<PK, uint32_t, int32_t>;
     Reg R0[NR], R1[NR];
     SideState s{};
@@ -988,15 +984,15 @@ __device__ __forceinline__ void group_loop(const Problem& P, const Queues& Q, co
             const uint32_t ri = P.rec_of ? __ldcg(P.rec_of + uidx) : kNoUnit;
             bool resumed = false;
             if (ri != kNoUnit) {
-                if constexpr (PK) resumed = load_record16<G, CG>(P, ri, s, R0, R1, gl);
+                if constexpr (PK) resumed = load_record16<G, CG>(P, zc, ri, s, R0, R1, gl);
                 else resumed = load_record<G, CG>(P, ri, s, R0, R1, gl);
             }
             if (!resumed) {
                 // S(0,0) = 0 in the middle of the window, every other cell -inf (Sec. 2.2)
                 if constexpr (PK) {
                     constexpr int t0 = (W / 2) % CG, p0 = t0 % (CG / 2);
-                    s.B0 = -P.X - P.gap - kTheta0;   // theta of d = 1 at kTheta0
-                    const int32_t z0 = -s.B0;
+                    s.B0 = -P.X - P.gap - zc.th0;   // theta of d = 1 at theta0
+                    const int32_t z0 = -32 * s.B0;
 #pragma unroll
                     for (int p = 0; p < NR; p++) {
                         R0[p] = kDead2;
@@ -1019,9 +1015,9 @@ __device__ __forceinline__ void group_loop(const Problem& P, const Queues& Q, co
         }
         int r = kCont;
         if constexpr (PK) {
-            if (!skip_odd) r = group_step16<G, CG, true>(s, res, R0, R1, P, tab, gl, gm, gsm);
+            if (!skip_odd) r = group_step16<G, CG, true>(s, res, R0, R1, P, zc, tab, gl, gm, gsm);
             skip_odd = false;
-            if (r == kCont) r = group_step16<G, CG, false>(s, res, R1, R0, P, tab, gl, gm, gsm);
+            if (r == kCont) r = group_step16<G, CG, false>(s, res, R1, R0, P, zc, tab, gl, gm, gsm);
         } else {
             if (!skip_odd) r = group_step<G, CG, true, A>(s, res, R0, R1, P, tab, gl, gm, gsm);
             skip_odd = false;

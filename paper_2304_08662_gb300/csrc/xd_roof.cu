@@ -117,9 +117,9 @@ __global__ void __launch_bounds__(128, 2) k_probe_cells(int32_t* out, int iters,
     if (acc == uint32_t(seed) && kmax == seed) out[blockIdx.x] = int32_t(acc);
 }
 
-// The packed DNA update of the group kernels (cells16, then the search for the first
-// maximum) on 32 slots held in 16 registers, alternating odd / even anti-diagonals, every
-// slot inside the band.
+// The packed DNA update of the group kernels (cells16 with its best-cell key) on 32 slots
+// held in 16 registers, alternating odd / even anti-diagonals, every slot inside the band
+// (the band mask is a run-time zero, so its instructions stay).
 __global__ void __launch_bounds__(128, 2) k_probe_cells16(int32_t* out, int iters, int32_t seed) {
     __shared__ __align__(16) int32_t tab[kLutInts];
     Problem P{};
@@ -130,28 +130,29 @@ __global__ void __launch_bounds__(128, 2) k_probe_cells16(int32_t* out, int iter
     uint32_t R0[16], R1[16];
 #pragma unroll
     for (int t = 0; t < 16; t++) {
-        R0[t] = pack2(2000 + ((t * 7 + seed) & 15), 2000 + ((t * 5 + seed) & 15));
-        R1[t] = pack2(2000 + ((t * 3 + seed) & 15), 2000 + ((t * 11 + seed) & 15));
+        R0[t] = pack2(32 * (200 + ((t * 7 + seed) & 15)), 32 * (200 + ((t * 5 + seed) & 15)));
+        R1[t] = pack2(32 * (200 + ((t * 3 + seed) & 15)), 32 * (200 + ((t * 11 + seed) & 15)));
     }
     Res<32, kDna16> res;
     uint64_t x = 0x9E3779B97F4A7C15ull ^ uint64_t(threadIdx.x) * 0xBF58476D1CE4E5B9ull;
     res.hs = x;
     res.vs = x * 0x94D049BB133111EBull;
-    uint32_t nth2 = (uint32_t(-1960) & 0xffffu) * 0x10001u, acc = 0;
-    int32_t z = 0;
-    for (int k = 0; k < iters; k++) {
-        uint32_t mx, dacc;
-        cells16<32, true>(R0, R1, kDead2, kDead2, res, 0u, nth2, tab, mx, dacc);
-        z = max(lo16(mx), hi16(mx));
-        acc ^= dacc ^ uint32_t(first_of16<32>(R1, z));
-        nth2 = (uint32_t(40 - z) & 0xffffu) * 0x10001u;
-        cells16<32, false>(R1, R0, kDead2, kDead2, res, 0u, nth2, tab, mx, dacc);
-        z = max(lo16(mx), hi16(mx));
-        acc ^= dacc ^ uint32_t(first_of16<32>(R0, z));
-        nth2 = (uint32_t(40 - z) & 0xffffu) * 0x10001u;
+    const uint32_t nbv = uint32_t(seed) >> 30;   // zero, unknown to the compiler
+    uint32_t nth2 = (uint32_t(-32 * 190) & 0xffffu) * 0x10001u, acc = 0;
+    int32_t k = 0;
+    for (int it = 0; it < iters; it++) {
+        uint32_t mk, dacc;
+        cells16<32, true>(R0, R1, kDead2, kDead2, res, nbv, nth2, tab, mk, dacc);
+        k = max(lo16(mk), hi16(mk));
+        acc ^= dacc;
+        nth2 = (uint32_t(32 * 20 - (k & ~31)) & 0xffffu) * 0x10001u;
+        cells16<32, false>(R1, R0, kDead2, kDead2, res, nbv, nth2, tab, mk, dacc);
+        k = max(lo16(mk), hi16(mk));
+        acc ^= dacc;
+        nth2 = (uint32_t(32 * 20 - (k & ~31)) & 0xffffu) * 0x10001u;
         res.hs = (res.hs << 2) | (res.hs >> 62);
     }
-    if (acc == uint32_t(seed) && z == seed) out[blockIdx.x] = int32_t(acc);
+    if (acc == uint32_t(seed) && k == seed) out[blockIdx.x] = int32_t(acc);
 }
 
 template <int OP>

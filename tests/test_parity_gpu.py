@@ -128,11 +128,12 @@ def test_random_tiny(ctx, alphabet, X):
     assert_parity(xdrop.extend_host(ctx, b), b)
 
 
-# DNA register levels keep scores in 16-bit halves when X <= 15000 and -127 <= gap <= 0
-# (else 32-bit levels): both sides of each bound, the extreme scores, and a gap of 0
+# DNA register levels keep scores in 16-bit halves when -127 <= gap <= 0 and
+# 1022 - X - s_max - (2 (|gap| + s_max) + 1) >= 64, s_max = max(match, mismatch, 0)
+# (else 32-bit levels): both sides of that bound for two scorings, and a gap of 0
 @pytest.mark.parametrize("X,gap,match,mismatch", [
-    (15000, -1, 1, -1), (15001, -1, 1, -1), (40, -127, 127, -127), (3000, -127, 127, -127),
-    (40, 0, 2, -3), (40, -128, 5, -4)])
+    (952, -1, 1, -1), (953, -1, 1, -1), (322, -127, 127, -127), (323, -127, 127, -127),
+    (40, -127, 127, -127), (15000, -1, 1, -1), (40, 0, 2, -3), (40, -128, 5, -4)])
 def test_score_ranges(ctx, X, gap, match, mismatch):
     rng = np.random.default_rng(7 + X - gap + match)
     rows = random_pairs(rng, 120, "dna", 500)
