@@ -36,12 +36,23 @@ ALG_OPS_PER_CELL = 9
 SM_COUNT_GB300 = 152
 # Integer ALU-pipe lanes per SM per clock: max, DPX, logic, select and byte-permute
 # instructions all issue there (measured: 60-61 per clock at 1.99 GHz for each of them);
-# plain adds and multiply-adds can also use the FMA pipe.
+# plain adds and multiply-adds can also use the FMA pipe.  The DNA register levels compute
+# (and protein) register levels compute on 16-bit halves (16x2 DPX at the same instruction
+# rate) when the scores allow, so their peak counts two 16-bit lanes per ALU lane.
 ALU_LANES_PER_SM = 64
 # DRAM bytes (read + write) of one launch of the dominant kernel, from one ncu capture of the
 # same workload and kernel build (profiles/k_fused_dna_longread_100k_x20.md); reported as
 # roofline.traffic only for that workload with the default configuration.
-DOMINANT_KERNEL_TRAFFIC = {"dna_longread_100000_x20": 261_182_208 + 14_858_496}
+DOMINANT_KERNEL_TRAFFIC = {"dna_longread_100000_x20": 261_023_232 + 16_260_864}
+
+
+def packed_scores(b):
+    """True when the library runs this batch's register levels on 16-bit scores (the bound
+    of the packed representation: -127 <= gap <= 0 and theta1 - theta0 >= 64)."""
+    if not (-127 <= b.gap <= 0) or not (0 <= b.X <= 1022):
+        return False
+    sm = max(b.match, b.mismatch, 0) if b.alphabet == "dna" else max(int(np.max(b.matrix)), 0)
+    return (1022 - b.X - sm) - (2 * (sm - b.gap) + 1) >= 64
 
 
 def parse():
@@ -443,10 +454,14 @@ def main():
         except (OSError, ValueError):
             pass
         sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-        peak = props.multi_processor_count * ALU_LANES_PER_SM * sm_max * 1e6 / 1e12
-        # measured in this run: the ALU pipe's issue rate (max) and the tiers' own cell update
-        alu_meas = xdrop.xd_probe(ctx, "max") / 1e12
-        cell_probe = xdrop.xd_probe(ctx, "cell_dna" if b.alphabet == "dna" else "cell_prot")
+        packed = packed_scores(b)
+        width = 2 if packed else 1    # 16-bit lanes per ALU lane
+        peak = width * props.multi_processor_count * ALU_LANES_PER_SM * sm_max * 1e6 / 1e12
+        # measured in this run: the ALU pipe's issue rate (max, or max on 16x2) and the tiers'
+        # own cell update
+        alu_meas = width * xdrop.xd_probe(ctx, "max_16x2" if packed else "max") / 1e12
+        cell_probe = xdrop.xd_probe(ctx, ("cell_dna" if b.alphabet == "dna" else "cell_prot") +
+                                    ("16" if packed else ""))
         tier_names = ["first register launch (fused persistent grid of levels 0-2, or level 0)",
                       "later register levels and band tier", "generic tier"]
         tuned_env = any(k.startswith("XD_") for k in os.environ)
@@ -455,7 +470,9 @@ def main():
                     "frac": achieved / peak if peak else None, "traffic": traffic,
                     "kernel": tier_names[top], "ops_per_cell": ALG_OPS_PER_CELL,
                     "peak_basis": f"{props.multi_processor_count} SMs x {ALU_LANES_PER_SM} integer ALU-pipe "
-                                  f"lanes x {sm_max:.0f} MHz (max SM clock)",
+                                  f"lanes x {width} ({'16-bit halves' if packed else '32-bit'}) x "
+                                  f"{sm_max:.0f} MHz (max SM clock)",
+                    "op_width_bits": 16 if packed else 32,
                     "kernel_ms": tier_ms[top],
                     "measured_alu_peak": alu_meas, "frac_of_measured_alu": achieved / alu_meas,
                     "cell_probe_gcups": cell_probe / 1e9,
@@ -513,7 +530,8 @@ def main():
             line = {"metric": "GCUPS", "value": value, "unit": "GCUPS", "n_gpus": world,
                     "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
                     "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                    "dtype": "int32", "data": "synthetic", "config": workload_config(a, b),
+                    "dtype": "int16" if packed_scores(b) else "int32", "data": "synthetic",
+                    "config": workload_config(a, b),
                     "pairs_per_s": b.n_pairs * world / (ms * 1e-3),
                     "paper_gcups": cells_paper * world / (ms * 1e-3) / 1e9,
                     "cells_per_step": cells,

@@ -254,10 +254,10 @@ xd_status xd_get_timing(xd_ctx* ctx, xd_timing* out);
  *   6 compare + select (two instructions), 7 byte permute, 8 DPX add-max on 16x2,
  *   9 DPX 3-way max on 16x2, 10 max on 16x2,
  * or op 100 / 101: the register tiers' own cell update on 32 in-register slots for DNA /
- * protein scoring (every slot in the band, no band bookkeeping); op 102: the DNA update
- * with 16-bit packed scores (two cells per register) including its dead mask, maximum and
- * first-maximum search.
- * *rate receives operations (ops 100-102: cells) per second for the whole GPU.  Synchronous;
+ * protein scoring (every slot in the band, no band bookkeeping); op 102 / 103: the DNA /
+ * protein update with 16-bit packed scores (two cells per register) including its dead
+ * mask and best-cell key.
+ * *rate receives operations (ops 100-103: cells) per second for the whole GPU.  Synchronous;
  * runs for a few tens of milliseconds.  Errors: XD_EINVAL (unknown op), XD_EDEVICE. */
 xd_status xd_probe(xd_ctx* ctx, int32_t op, double* rate);
 

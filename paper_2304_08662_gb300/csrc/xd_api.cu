@@ -563,6 +563,8 @@ xd_status run_pipeline(xd_ctx* c, Scratch& s, const BatchView& b, xd_result* d_o
     P.n_words = b.packed ? std::max<uint64_t>(1, b.packed_words)
                          : std::max<uint64_t>(1, (b.n_codes + (b.alpha == 4 ? 15 : 5)) / (b.alpha == 4 ? 16 : 6));
     P.max_abs = b.max_abs;
+    P.s_max = 0;
+    for (int e = 0; e < (b.alpha == 4 ? 16 : 400); e++) P.s_max = std::max<int32_t>(P.s_max, b.sim[e]);
     P.units = static_cast<const Unit*>(s.units.p);
     P.results = d_out;
     P.err = err;
@@ -604,7 +606,7 @@ xd_status run_pipeline(xd_ctx* c, Scratch& s, const BatchView& b, xd_result* d_o
         } else {
             const TierConfig& tc = tiers_for(c, b);
             int lv = 0;
-            if (tc.fused && fused_supported(tc, b.alpha) && (b.alpha == 20 || dna16_batch(P))) {
+            if (tc.fused && fused_supported(tc, b.alpha) && packed_batch(P)) {
                 // the live queues' slots start unpublished
                 XD_CUDA(c, cudaMemsetAsync(Q.q[0], 0xff, sizeof(uint32_t) * size_t(Q.n_units), st));
                 XD_CUDA(c, cudaMemsetAsync(Q.q[1], 0xff, sizeof(uint32_t) * size_t(Q.n_units), st));
@@ -1589,7 +1591,7 @@ xd_status xd_get_timing(xd_ctx* c, xd_timing* out) {
 
 xd_status xd_probe(xd_ctx* c, int32_t op, double* rate) {
     if (!c || !rate) return XD_EINVAL;
-    if (!((op >= 0 && op <= 10) || (op >= 100 && op <= 102))) return fail(c, XD_EINVAL, "unknown probe op");
+    if (!((op >= 0 && op <= 10) || (op >= 100 && op <= 103))) return fail(c, XD_EINVAL, "unknown probe op");
     std::lock_guard<std::mutex> lk(c->mu);
     XD_CUDA(c, cudaSetDevice(c->device));
     XD_CUDA(c, cudaDeviceSynchronize());

@@ -48,6 +48,7 @@ struct Problem {
     int32_t X;
     uint32_t delta;             // 0 = unrestricted
     int32_t max_abs;            // largest |score| of one step (similarity or gap)
+    int32_t s_max;              // largest similarity, at least 0
     // Escalation records: a side that outgrows a register level's window saves its two
     // anti-diagonals and band state so that the next level continues instead of restarting.
     int32_t* rec;               // record pool of rec_cap ints

@@ -42,8 +42,8 @@ constexpr int32_t kDeadR = -(1 << 23);
 constexpr int64_t kRegLimit = int64_t(1) << 23;
 
 // ---------------------------------------------------------------------------------------
-// DNA with 16-bit packed scores: representation kDna16 of the group kernels (template
-// argument A; the alphabet is DNA).
+// 16-bit packed scores: representations kDna16 (DNA) and kProt16 (protein) of the group
+// kernels (template argument A).
 //
 // Register p of a lane holds slot p in its low half and slot p + CG/2 in its high half, so
 // one 16x2 DPX instruction updates two cells.  A score S of anti-diagonal d is kept as 32 z
@@ -60,23 +60,24 @@ constexpr int64_t kRegLimit = int64_t(1) << 23;
 //   theta0 = 2 (|gap| + s_max) + 1: a dead slot plus 32 (Sim - 2 gap) stays below
 //            32 theta, and live slots stay positive across a rebase;
 //   theta1 = 1022 - X - s_max: live z <= theta + X + s_max, so 32 z + 31 < 2^15.
-// A batch takes these levels when theta1 - theta0 >= 64 and -127 <= gap <= 0 (for scores
-// 1 / -1 / -1: X <= 952); other DNA batches take the 32-bit levels.
+// A batch takes these levels when theta1 - theta0 >= 64 and -127 <= gap <= 0 (DNA scores
+// 1 / -1 / -1: X <= 952; BLOSUM62 with gap -2: X <= 920); other batches take the 32-bit
+// levels.
 constexpr int kDna16 = 2;
+constexpr int kProt16 = 3;
 constexpr uint32_t kDead2 = 0xffffffffu;
 
-__host__ __device__ constexpr int alpha_of(int A) { return A == kDna16 ? 4 : A; }
+__host__ __device__ constexpr int alpha_of(int A) { return A == kDna16 ? 4 : A == kProt16 ? 20 : A; }
+__host__ __device__ constexpr bool packed_rep(int A) { return A == kDna16 || A == kProt16; }
 
 struct Z16 {
     int32_t th0, th1;
 };
 __host__ __device__ inline Z16 z16_of(const Problem& P) {
-    const int32_t a = P.sim[0], b = P.sim[1];
-    const int32_t sm = a > b ? (a > 0 ? a : 0) : (b > 0 ? b : 0);
-    return Z16{2 * (sm - P.gap) + 1, 1022 - P.X - sm};
+    return Z16{2 * (P.s_max - P.gap) + 1, 1022 - P.X - P.s_max};
 }
-__host__ __device__ inline bool dna16_ok(const Problem& P) {
-    if (P.alpha != 4 || P.gap > 0 || P.gap < -127 || P.X < 0 || P.X > 1022) return false;
+__host__ __device__ inline bool packed_ok(const Problem& P) {
+    if (P.gap > 0 || P.gap < -127 || P.X < 0 || P.X > 1022 || P.s_max < 0 || P.s_max > 127) return false;
     const Z16 z = z16_of(P);
     return z.th1 - z.th0 >= 64;
 }
@@ -348,11 +349,15 @@ __device__ __forceinline__ void cells_of(int32_t (&P1)[CG], int32_t (&P2)[CG], i
 // major.  Entries past the 20 x 20 matrix are zero (offsets of codes >= 20 land there; only
 // cells outside the band can carry such codes).
 __device__ __forceinline__ void build_table16(int32_t* tab, const Problem& P);
+__device__ __forceinline__ void build_table_p16(int32_t* tab, const Problem& P);
 
 template <int A>
 __device__ __forceinline__ void build_table(int32_t* tab, const Problem& P) {
     if constexpr (A == kDna16) {
         build_table16(tab, P);
+        return;
+    } else if constexpr (A == kProt16) {
+        build_table_p16(tab, P);
         return;
     } else if constexpr (A == 4) {
         const int32_t mat = P.sim[0], mis = P.sim[1];
@@ -444,25 +449,93 @@ __device__ __forceinline__ void build_table16(int32_t* tab, const Problem& P) {
     __syncthreads();
 }
 
-// The lane's CG cells in kDna16.  P1 holds d-1, P2 holds d-2 and receives d; upb / lfb are
+// Protein residue slices in the register order of kProt16: byte offsets into the block's
+// 20 x 20 table, slot p in the low half and slot CG/2 + p in the high half (H codes scaled
+// by 80, V codes by 4); the sum of an H and a V register addresses both slots' cells.
+template <int CG>
+struct Res<CG, kProt16> {
+    static constexpr int H = CG / 2;
+    uint32_t hx[H], vx[H];
+    Stream5 sh, sv;
+
+    __device__ __forceinline__ void load(const Problem& P, const SideState& s, int64_t hb, int64_t vb) {
+        Stream5 t;
+        // slot u pairs H_side[hb + u] with V_side[vb - u]
+        stream5_init(t, P.store, P.n_words, s.h0 + s.dir * hb, s.dir);
+#pragma unroll
+        for (int u = 0; u < CG; u++) {
+            const uint32_t c = stream5_next(t, P.store, P.n_words) * 80u;
+            if (u < H) hx[u] = c;
+            else hx[u - H] |= c << 16;
+        }
+        stream5_init(t, P.store, P.n_words, s.v0 + s.dir * (vb - CG + 1), s.dir);
+#pragma unroll
+        for (int u = CG - 1; u >= 0; u--) {
+            const uint32_t c = stream5_next(t, P.store, P.n_words) * 4u;
+            if (u >= H) vx[u - H] = c << 16;
+            else vx[u] |= c;
+        }
+        stream5_init(sh, P.store, P.n_words, s.h0 + s.dir * (hb + CG), s.dir);
+        stream5_init(sv, P.store, P.n_words, s.v0 + s.dir * (vb + 1), s.dir);
+    }
+    // slots move down by one, the new residue enters slot CG - 1
+    __device__ __forceinline__ void push_h(const Problem& P) {
+        const uint32_t c = stream5_next(sh, P.store, P.n_words) * 80u;
+        const uint32_t s0 = hx[0] >> 16;
+#pragma unroll
+        for (int p = 0; p < H - 1; p++) hx[p] = hx[p + 1];
+        hx[H - 1] = s0 | (c << 16);
+    }
+    // slots move up by one, the new residue enters slot 0
+    __device__ __forceinline__ void push_v(const Problem& P) {
+        const uint32_t c = stream5_next(sv, P.store, P.n_words) * 4u;
+        const uint32_t sh1 = vx[H - 1] & 0xffffu;
+#pragma unroll
+        for (int p = H - 1; p > 0; p--) vx[p] = vx[p - 1];
+        vx[0] = c | (sh1 << 16);
+    }
+};
+
+// The block's table for kProt16: 32 (Sim - 2 gap) row-major, H code major (byte offset
+// 80 h + 4 v); entries past the 20 x 20 matrix are zero (only cells outside the band can
+// carry codes >= 20).
+__device__ __forceinline__ void build_table_p16(int32_t* tab, const Problem& P) {
+    for (int e = threadIdx.x; e < 1024; e += blockDim.x) tab[e] = e < 400 ? 32 * (int32_t(P.sim[e]) - 2 * P.gap) : 0;
+    __syncthreads();
+}
+
+// The lane's CG cells in kDna16 / kProt16.  P1 holds d-1, P2 holds d-2 and receives d; upb / lfb are
 // the neighbouring lanes' registers holding the slot before the first / after the last
 // (kDead2 at the group's ends).  nbv: slots outside the band, slot p at bit p and slot
 // CG/2 + p at bit 16 + p.  nth2: -32 theta in both halves.  Returns the packed maximum of
 // slot + 31 - lane slot over the new slots (the lane's best cell and its lowest slot; at
 // most 30 when none is live) and the dead mask in the layout of nbv.
-template <int CG, bool ODD>
+template <int CG, bool ODD, int A>
 __device__ __forceinline__ void cells16(uint32_t (&P1)[CG / 2], uint32_t (&P2)[CG / 2], uint32_t upb,
-                                        uint32_t lfb, const Res<CG, kDna16>& res, uint32_t nbv, uint32_t nth2,
+                                        uint32_t lfb, const Res<CG, A>& res, uint32_t nbv, uint32_t nth2,
                                         const int32_t* tab, uint32_t& mk, uint32_t& dacc) {
     constexpr int H = CG / 2;
     static_assert(CG % 4 == 0 && H <= 16, "slots come in pairs of registers");
-    const uint64_t x = res.hs ^ res.vs;
-    const int2* t2 = reinterpret_cast<const int2*>(tab);
     mk = kDead2;
     dacc = 0;
 #pragma unroll
     for (int q = 0; q < H / 2; q++) {
-        const int2 s2 = t2[uint32_t(x >> (8 * q)) & 0xffu];
+        uint32_t sp[2];
+        if constexpr (A == kDna16) {
+            const uint64_t x = res.hs ^ res.vs;
+            const int2 s2 = reinterpret_cast<const int2*>(tab)[uint32_t(x >> (8 * q)) & 0xffu];
+            sp[0] = uint32_t(s2.x);
+            sp[1] = uint32_t(s2.y);
+        } else {
+            const char* tb = reinterpret_cast<const char*>(tab);
+#pragma unroll
+            for (int r = 0; r < 2; r++) {
+                const uint32_t ix = res.hx[2 * q + r] + res.vx[2 * q + r];
+                const uint32_t a = *reinterpret_cast<const uint32_t*>(tb + (ix & 0xffffu));
+                const uint32_t b = *reinterpret_cast<const uint32_t*>(tb + (ix >> 16));
+                sp[r] = __byte_perm(a, b, 0x5410);
+            }
+        }
 #pragma unroll
         for (int r = 0; r < 2; r++) {
             const int p = 2 * q + r;
@@ -474,7 +547,7 @@ __device__ __forceinline__ void cells16(uint32_t (&P1)[CG / 2], uint32_t (&P2)[C
                 up = P1[p];
                 lf = p < H - 1 ? P1[p + 1] : __byte_perm(P1[0], lfb, 0x5432);
             }
-            const uint32_t raw = __viaddmax_s16x2(P2[p], uint32_t(r ? s2.y : s2.x), __vmaxs2(up, lf));
+            const uint32_t raw = __viaddmax_s16x2(P2[p], sp[r], __vmaxs2(up, lf));
             uint32_t u = __viaddmax_s16x2(raw, nth2, 0x80008000u);   // raw - 32 theta
             u |= (nbv << (15 - p)) & 0x80008000u;                   // outside the band: negative
             const uint32_t M = sign_spread(u);
@@ -593,10 +666,10 @@ __device__ __forceinline__ int group_step(SideState& s, Res<CG, A>& res, int32_t
     return d == s.m + s.n ? kDone : kCont;
 }
 
-// One anti-diagonal of the group's side extension in kDna16 (the steps of group_step, on
-// packed scores).
-template <int G, int CG, bool ODD>
-__device__ __forceinline__ int group_step16(SideState& s, Res<CG, kDna16>& res, uint32_t (&P1)[CG / 2],
+// One anti-diagonal of the group's side extension in kDna16 / kProt16 (the steps of
+// group_step, on packed scores).
+template <int G, int CG, bool ODD, int A>
+__device__ __forceinline__ int group_step16(SideState& s, Res<CG, A>& res, uint32_t (&P1)[CG / 2],
                                             uint32_t (&P2)[CG / 2], const Problem& P, const Z16& zc,
                                             const int32_t* tab, int gl, uint32_t gm, int32_t* gsm) {
     constexpr int W = G * CG, H = CG / 2;
@@ -634,7 +707,7 @@ __device__ __forceinline__ int group_step16(SideState& s, Res<CG, kDna16>& res, 
         if (gl == 0) atomicAdd(&P.stats[8], 1ull);
     }
     const int32_t sb = gl * CG;
-    update_slices<CG, ODD, kDna16>(s, res, P, int64_t(ib) - 1 + sb, int64_t(d) - ib - 1 - sb);
+    update_slices<CG, ODD, A>(s, res, P, int64_t(ib) - 1 + sb, int64_t(d) - ib - 1 - sb);
     const uint32_t nb = ~slot_mask(slo - sb, shi - sb, CG);
     const uint32_t nbv = H == 16 ? nb : ((nb & ((1u << H) - 1u)) | ((nb >> H) << 16));
     int32_t zb = s.B0 + P.gap * d;
@@ -664,7 +737,7 @@ __device__ __forceinline__ int group_step16(SideState& s, Res<CG, kDna16>& res, 
         }
     }
     uint32_t mk, dacc;
-    cells16<CG, ODD>(P1, P2, upb, lfb, res, nbv, nth2, tab, mk, dacc);
+    cells16<CG, ODD, A>(P1, P2, upb, lfb, res, nbv, nth2, tab, mk, dacc);
     s.cells += uint64_t(hi - lo + 1);
     const uint32_t hm = (1u << H) - 1u;
     const uint32_t lv = ~dacc & (hm * 0x10001u);
@@ -946,7 +1019,7 @@ __device__ __forceinline__ void group_loop(const Problem& P, const Queues& Q, co
     const int32_t* tab = smem;
     int32_t* gsm = smem + kLutInts + (threadIdx.x >> 5) * warp_ints + ((threadIdx.x & 31) / G) * 2 * W;
     // kDna16: CG/2 registers of two 16-bit slots each, else CG int32 slots
-    constexpr bool PK = A == kDna16;
+    constexpr bool PK = packed_rep(A);
     constexpr int NR = PK ? CG / 2 : CG;
     const Z16 zc = z16_of(P);
     using Reg = std::conditional_t<PK, uint32_t, int32_t>;
@@ -963,7 +1036,7 @@ __device__ __forceinline__ void group_loop(const Problem& P, const Queues& Q, co
             while (next_unit<G>(S, gl, lane, gm, chunk, next, end, uidx, P.err)) {
                 const Unit u = P.units[uidx];
                 if ((int64_t(u.m) + u.n) * P.max_abs >= kRegLimit || P.alpha != alpha_of(A) ||
-                    (PK && !dna16_ok(P))) {
+                    (PK && !packed_ok(P))) {
                     if (gl == 0) push_unit(Q, kBandQ, uidx);
                     continue;
                 }
@@ -1015,9 +1088,9 @@ __device__ __forceinline__ void group_loop(const Problem& P, const Queues& Q, co
         }
         int r = kCont;
         if constexpr (PK) {
-            if (!skip_odd) r = group_step16<G, CG, true>(s, res, R0, R1, P, zc, tab, gl, gm, gsm);
+            if (!skip_odd) r = group_step16<G, CG, true, A>(s, res, R0, R1, P, zc, tab, gl, gm, gsm);
             skip_odd = false;
-            if (r == kCont) r = group_step16<G, CG, false>(s, res, R1, R0, P, zc, tab, gl, gm, gsm);
+            if (r == kCont) r = group_step16<G, CG, false, A>(s, res, R1, R0, P, zc, tab, gl, gm, gsm);
         } else {
             if (!skip_odd) r = group_step<G, CG, true, A>(s, res, R0, R1, P, tab, gl, gm, gsm);
             skip_odd = false;

@@ -73,9 +73,11 @@ cudaError_t launch_level_dna(const Problem& P, const Queues& Q, int variant, int
                              int blocks, int chunk, cudaStream_t st);
 cudaError_t launch_level_dna16(const Problem& P, const Queues& Q, int variant, int in_q, int out_q,
                                int blocks, int chunk, cudaStream_t st);
-// DNA batches whose scores fit the packed 16-bit levels (fused grids are compiled for these
-// only; other DNA batches run one launch per level).
-bool dna16_batch(const Problem& P);
+cudaError_t launch_level_prot16(const Problem& P, const Queues& Q, int variant, int in_q, int out_q,
+                                int blocks, int chunk, cudaStream_t st);
+// Batches whose scores fit the packed 16-bit levels (fused grids are compiled for these
+// only; other batches run one launch per level).
+bool packed_batch(const Problem& P);
 cudaError_t launch_level_prot(const Problem& P, const Queues& Q, int variant, int in_q, int out_q,
                               int blocks, int chunk, cudaStream_t st);
 bool fused_supported_prot(int a, int b, int d);

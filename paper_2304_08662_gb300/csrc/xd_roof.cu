@@ -26,7 +26,8 @@ enum ProbeOp {
     kProbeVmax16 = 10,     // 16x2: x = max(x, y) per half
     kProbeCellDna = 100,   // the register tiers' cell update (cells_of), DNA, 32 slots
     kProbeCellProt = 101,  // the same, protein (similarity-table offsets), 32 slots
-    kProbeCellDna16 = 102, // the 16-bit packed DNA update (cells16 + first-maximum search)
+    kProbeCellDna16 = 102, // the 16-bit packed DNA update (cells16 with its best-cell key)
+    kProbeCellProt16 = 103, // the same, protein
 };
 
 template <int OP>
@@ -117,40 +118,61 @@ __global__ void __launch_bounds__(128, 2) k_probe_cells(int32_t* out, int iters,
     if (acc == uint32_t(seed) && kmax == seed) out[blockIdx.x] = int32_t(acc);
 }
 
-// The packed DNA update of the group kernels (cells16 with its best-cell key) on 32 slots
-// held in 16 registers, alternating odd / even anti-diagonals, every slot inside the band
-// (the band mask is a run-time zero, so its instructions stay).
+// The packed update of the group kernels (cells16 with its best-cell key; A = kDna16 or
+// kProt16) on 32 slots held in 16 registers, alternating odd / even anti-diagonals, every
+// slot inside the band (the band mask is a run-time zero, so its instructions stay).
+template <int A>
 __global__ void __launch_bounds__(128, 2) k_probe_cells16(int32_t* out, int iters, int32_t seed) {
     __shared__ __align__(16) int32_t tab[kLutInts];
     Problem P{};
-    P.sim[0] = 1;
-    P.sim[1] = -1;
-    P.gap = -1;
-    build_table16(tab, P);
+    if (A == kDna16) {
+        P.sim[0] = 1;
+        P.sim[1] = -1;
+        P.gap = -1;
+    } else {
+        for (int t = 0; t < 400; t++) P.sim[t] = int8_t((t * 7 + 3) % 15 - 7);
+        P.gap = -2;
+    }
+    build_table<A>(tab, P);
     uint32_t R0[16], R1[16];
 #pragma unroll
     for (int t = 0; t < 16; t++) {
         R0[t] = pack2(32 * (200 + ((t * 7 + seed) & 15)), 32 * (200 + ((t * 5 + seed) & 15)));
         R1[t] = pack2(32 * (200 + ((t * 3 + seed) & 15)), 32 * (200 + ((t * 11 + seed) & 15)));
     }
-    Res<32, kDna16> res;
+    Res<32, A> res;
     uint64_t x = 0x9E3779B97F4A7C15ull ^ uint64_t(threadIdx.x) * 0xBF58476D1CE4E5B9ull;
-    res.hs = x;
-    res.vs = x * 0x94D049BB133111EBull;
+    if constexpr (A == kDna16) {
+        res.hs = x;
+        res.vs = x * 0x94D049BB133111EBull;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+            res.hx[k] = uint32_t((x >> (k & 7)) % 20) * 80u | (uint32_t((x >> (k + 9)) % 20) * 80u << 16);
+            res.vx[k] = uint32_t((x >> (k + 3)) % 20) * 4u | (uint32_t((x >> (k + 17)) % 20) * 4u << 16);
+        }
+    }
     const uint32_t nbv = uint32_t(seed) >> 30;   // zero, unknown to the compiler
     uint32_t nth2 = (uint32_t(-32 * 190) & 0xffffu) * 0x10001u, acc = 0;
     int32_t k = 0;
     for (int it = 0; it < iters; it++) {
         uint32_t mk, dacc;
-        cells16<32, true>(R0, R1, kDead2, kDead2, res, nbv, nth2, tab, mk, dacc);
+        cells16<32, true, A>(R0, R1, kDead2, kDead2, res, nbv, nth2, tab, mk, dacc);
         k = max(lo16(mk), hi16(mk));
         acc ^= dacc;
         nth2 = (uint32_t(32 * 20 - (k & ~31)) & 0xffffu) * 0x10001u;
-        cells16<32, false>(R1, R0, kDead2, kDead2, res, nbv, nth2, tab, mk, dacc);
+        cells16<32, false, A>(R1, R0, kDead2, kDead2, res, nbv, nth2, tab, mk, dacc);
         k = max(lo16(mk), hi16(mk));
         acc ^= dacc;
         nth2 = (uint32_t(32 * 20 - (k & ~31)) & 0xffffu) * 0x10001u;
-        res.hs = (res.hs << 2) | (res.hs >> 62);
+        if constexpr (A == kDna16) {
+            res.hs = (res.hs << 2) | (res.hs >> 62);
+        } else {
+            const uint32_t t0 = res.hx[0];
+#pragma unroll
+            for (int q = 0; q < 15; q++) res.hx[q] = res.hx[q + 1];
+            res.hx[15] = t0;
+        }
     }
     if (acc == uint32_t(seed) && k == seed) out[blockIdx.x] = int32_t(acc);
 }
@@ -170,7 +192,8 @@ cudaError_t probe_rate(int op, int n_sm, double* rate, float* ms_out) {
     cudaEventCreate(&a);
     cudaEventCreate(&b);
     const int blocks = n_sm * 8;
-    const bool cells = op == kProbeCellDna || op == kProbeCellProt || op == kProbeCellDna16;
+    const bool cells = op == kProbeCellDna || op == kProbeCellProt || op == kProbeCellDna16 ||
+                       op == kProbeCellProt16;
     int iters = cells ? 4000 : 20000;
     double per_thread = 0;
     int threads = 256;
@@ -194,7 +217,10 @@ cudaError_t probe_rate(int op, int n_sm, double* rate, float* ms_out) {
                 k_probe_cells<20><<<n_sm * 2, 128, 0, 0>>>(out, iters, 12345);
                 return cudaGetLastError();
             case kProbeCellDna16:
-                k_probe_cells16<<<n_sm * 2, 128, 0, 0>>>(out, iters, 12345);
+                k_probe_cells16<kDna16><<<n_sm * 2, 128, 0, 0>>>(out, iters, 12345);
+                return cudaGetLastError();
+            case kProbeCellProt16:
+                k_probe_cells16<kProt16><<<n_sm * 2, 128, 0, 0>>>(out, iters, 12345);
                 return cudaGetLastError();
             default: return cudaErrorInvalidValue;
         }

@@ -1,5 +1,5 @@
 // Register tiers: the fused DNA grids (16-bit packed scores, A = kDna16) and the dispatch
-// of register levels to the DNA (packed or 32-bit) or protein kernels.  The kernels
+// of register levels to the DNA or protein kernels (packed or 32-bit).  The kernels
 // themselves are the templates of xd_group.cuh.
 #include "xd_group.cuh"
 
@@ -35,12 +35,14 @@ cudaError_t launch_level(const Problem& P, const Queues& Q, const TierConfig& cf
     const int in_q = level == 0 ? -1 : level - 1;
     const int out_q = level == cfg.n_levels - 1 ? kBandQ : level;
     const int blocks = n_sm * cfg.blocks_per_sm[v];
-    if (P.alpha == 20) return launch_level_prot(P, Q, v, in_q, out_q, blocks, cfg.chunk, st);
-    if (dna16_ok(P)) return launch_level_dna16(P, Q, v, in_q, out_q, blocks, cfg.chunk, st);
+    if (P.alpha == 20)
+        return packed_ok(P) ? launch_level_prot16(P, Q, v, in_q, out_q, blocks, cfg.chunk, st)
+                            : launch_level_prot(P, Q, v, in_q, out_q, blocks, cfg.chunk, st);
+    if (packed_ok(P)) return launch_level_dna16(P, Q, v, in_q, out_q, blocks, cfg.chunk, st);
     return launch_level_dna(P, Q, v, in_q, out_q, blocks, cfg.chunk, st);
 }
 
-bool dna16_batch(const Problem& P) { return dna16_ok(P);
+bool packed_batch(const Problem& P) { return packed_ok(P);
 }
 
 bool fused_supported(const TierConfig& c, int alpha) {
@@ -60,7 +62,7 @@ cudaError_t launch_fused_levels(const Problem& P, const Queues& Q, const TierCon
                                 cudaStream_t st) {
     const int a = cfg.variant[0], b = cfg.variant[1], d = cfg.variant[2];
     if (P.alpha == 20) return launch_fused_levels_prot(P, Q, cfg, n_sm, st);
-    if (!dna16_ok(P)) return cudaErrorInvalidValue;   // DNA grids are compiled packed only
+    if (!packed_ok(P)) return cudaErrorInvalidValue;   // DNA grids are compiled packed only
     if (a == kG1C32 && b == kG4C32 && d == kG8C32) return launch_fused<1, 32, 4, 32, 8, 32, 2, kDna16>(P, Q, cfg, n_sm, st);
     if (a == kG1C32 && b == kG8C16 && d == kG16C16) return launch_fused<1, 32, 8, 16, 16, 16, 2, kDna16>(P, Q, cfg, n_sm, st);
     if (a == kG1C32 && b == kG16C16 && d == kG32C16)

@@ -1,6 +1,6 @@
 // Register tiers, DNA level kernels with 32-bit scores (A = 4): the group kernels of
 // xd_group.cuh, one launch per register level, for DNA batches outside the packed range
-// (dna16_ok false: X too large for 16-bit scores, X = infinity, or gap outside [-127, 0]).
+// (packed_ok false: X too large for 16-bit scores, X = infinity, or gap outside [-127, 0]).
 #include "xd_group.cuh"
 
 namespace xd {

@@ -1,12 +1,13 @@
 // Register tiers, DNA level kernels with 16-bit packed scores (A = kDna16): the group
-// kernels of xd_group.cuh, one launch per register level.  Used when dna16_ok holds for
-// the batch (X, gap within the packed range); other DNA batches take xd_tiers_dna.cu.
+// kernels of xd_group.cuh, one launch per register level.  Used when packed_ok holds for
+// the batch (X, gap and scores within the packed range); other DNA batches take the
+// 32-bit levels of xd_tiers_dna.cu.
 #include "xd_group.cuh"
 
 namespace xd {
 
 cudaError_t launch_level_dna16(const Problem& P, const Queues& Q, int variant, int in_q, int out_q,
-                             int blocks, int chunk, cudaStream_t st) {
+                               int blocks, int chunk, cudaStream_t st) {
     switch (variant) {
         case kG1C16: return launch_group<1, 16, 3, kDna16>(P, Q, in_q, out_q, blocks, chunk, st);
         case kG1C32: return launch_group<1, 32, 2, kDna16>(P, Q, in_q, out_q, blocks, chunk, st);

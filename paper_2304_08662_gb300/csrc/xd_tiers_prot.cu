@@ -1,5 +1,6 @@
-// Register tiers, protein instantiations (A = 20): the group kernels of xd_group.cuh with
-// 16-bit similarity-table offsets as residue slices.
+// Register tiers, protein instantiations: the 32-bit level kernels (A = 20, for batches
+// outside the packed range) and the fused grids (16-bit packed scores, A = kProt16), the
+// group kernels of xd_group.cuh with 16-bit similarity-table offsets as residue slices.
 #include "xd_group.cuh"
 
 namespace xd {
@@ -31,8 +32,9 @@ bool fused_supported_prot(int a, int b, int d) {
 cudaError_t launch_fused_levels_prot(const Problem& P, const Queues& Q, const TierConfig& cfg, int n_sm,
                                      cudaStream_t st) {
     const int a = cfg.variant[0], b = cfg.variant[1], d = cfg.variant[2];
-    if (a == kG4C16 && b == kG16C16 && d == kG32C32) return launch_fused<4, 16, 16, 16, 32, 32, 2, 20>(P, Q, cfg, n_sm, st);
-    if (a == kG1C16 && b == kG4C16 && d == kG16C16) return launch_fused<1, 16, 4, 16, 16, 16, 3, 20>(P, Q, cfg, n_sm, st);
+    if (!packed_ok(P)) return cudaErrorInvalidValue;   // protein grids are compiled packed only
+    if (a == kG4C16 && b == kG16C16 && d == kG32C32) return launch_fused<4, 16, 16, 16, 32, 32, 2, kProt16>(P, Q, cfg, n_sm, st);
+    if (a == kG1C16 && b == kG4C16 && d == kG16C16) return launch_fused<1, 16, 4, 16, 16, 16, 3, kProt16>(P, Q, cfg, n_sm, st);
     return cudaErrorInvalidValue;
 }
 

@@ -240,7 +240,7 @@ def xd_get_timing(ctx):
 
 PROBE_OPS = {"add": 0, "max": 1, "dpx_addmax": 2, "dpx_max3": 3, "lop3": 4, "imad": 5,
              "cmp_sel": 6, "prmt": 7, "dpx_addmax_16x2": 8, "dpx_max3_16x2": 9, "max_16x2": 10,
-             "cell_dna": 100, "cell_prot": 101, "cell_dna16": 102}
+             "cell_dna": 100, "cell_prot": 101, "cell_dna16": 102, "cell_prot16": 103}
 
 
 def xd_probe(ctx, op):

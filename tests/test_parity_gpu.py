@@ -141,6 +141,15 @@ def test_score_ranges(ctx, X, gap, match, mismatch):
     assert_parity(xdrop.extend_host(ctx, b), b)
 
 
+@pytest.mark.parametrize("X", [500, 920, 921])
+def test_protein_score_ranges(ctx, X):
+    """BLOSUM62 with gap -2: packed levels up to X = 920, 32-bit beyond."""
+    rng = np.random.default_rng(11 + X)
+    rows = random_pairs(rng, 60, "protein", 400)
+    b = synth.from_strings(rows, alphabet="protein", gap=-2, X=X)
+    assert_parity(xdrop.extend_host(ctx, b), b)
+
+
 @pytest.mark.parametrize("delta", [1, 2, 3, 7, 32, 33, 100])
 def test_random_restricted(ctx, delta):
     rng = np.random.default_rng(delta)
