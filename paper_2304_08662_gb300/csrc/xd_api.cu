@@ -454,8 +454,10 @@ void default_tiers(xd_ctx* c) {
     t.fused = env_int("XD_FUSED", 1) != 0;
     t.every1 = std::max(0, env_int("XD_EVERY1", 8));
     t.every2 = std::max(0, env_int("XD_EVERY2", 32));
+    t.every3 = std::max(0, env_int("XD_EVERY3", 64));
     if (t.every1 == 1) t.every1 = 2;   // every warp in role 1 would leave the ordered units to nobody
     if (t.every2 == 1) t.every2 = 2;
+    if (t.every3 == 1) t.every3 = 2;
     t.fused_minb = env_int("XD_FUSED_MINB", 2);
     // the longest 0.2% of the sides first, with 8 lanes x 4 slots (measured +3-4% at X = 20)
     t.long_permille = std::max(0, std::min(250, env_int("XD_LONG_PERMILLE", 2)));
@@ -606,15 +608,16 @@ xd_status run_pipeline(xd_ctx* c, Scratch& s, const BatchView& b, xd_result* d_o
         } else {
             const TierConfig& tc = tiers_for(c, b);
             int lv = 0;
-            if (tc.fused && fused_supported(tc, b.alpha) && packed_batch(P)) {
+            const int roles = packed_batch(P) ? fused_roles(tc, b.alpha) : 0;
+            if (roles) {
                 // the live queues' slots start unpublished
-                XD_CUDA(c, cudaMemsetAsync(Q.q[0], 0xff, sizeof(uint32_t) * size_t(Q.n_units), st));
-                XD_CUDA(c, cudaMemsetAsync(Q.q[1], 0xff, sizeof(uint32_t) * size_t(Q.n_units), st));
+                for (int k = 0; k < roles - 1; k++)
+                    XD_CUDA(c, cudaMemsetAsync(Q.q[k], 0xff, sizeof(uint32_t) * size_t(Q.n_units), st));
                 if (chain) XD_CUDA(c, cudaStreamWaitEvent(st, chain, 0));
                 XD_CUDA(c, launch_fused_levels(P, Q, tc, c->n_sm, st));
                 if (chain) XD_CUDA(c, cudaEventRecord(chain, st));
                 XD_CUDA(c, mark(4));
-                lv = 3;
+                lv = roles;
                 launches += 1;
             }
             for (; lv < tc.n_levels; lv++) {
@@ -908,15 +911,16 @@ void dispatch_loop(xd_ctx* c) {
 
 // ---------------------------------------------------------------- tuning table
 
-// One line per entry:  alpha=4 xb=1 lb=1 chain=1,4,5,6 chunk=1 fused=1 every1=4 every2=16 minb=2 ms=63.2
+// One line per entry:  alpha=4 xb=1 lb=1 chain=1,4,5,6 chunk=1 fused=1 every1=4 every2=16 every3=0 minb=2 ms=63.2
 std::string format_entry(const TuneEntry& t) {
     std::string chain;
     for (int k = 0; k < t.cfg.n_levels; k++) chain += (k ? "," : "") + std::to_string(t.cfg.variant[k]);
     char buf[256];
     std::snprintf(buf, sizeof(buf),
-                  "alpha=%d xb=%d lb=%d sb=%d chain=%s chunk=%d fused=%d every1=%d every2=%d minb=%d long=%d ms=%.4f",
+                  "alpha=%d xb=%d lb=%d sb=%d chain=%s chunk=%d fused=%d every1=%d every2=%d every3=%d minb=%d long=%d "
+                  "ms=%.4f",
                   t.alpha, t.xb, t.lb, t.sb, chain.c_str(), t.cfg.chunk, t.cfg.fused ? 1 : 0, t.cfg.every1,
-                  t.cfg.every2, t.cfg.fused_minb, t.cfg.long_permille, double(t.ms));
+                  t.cfg.every2, t.cfg.every3, t.cfg.fused_minb, t.cfg.long_permille, double(t.ms));
     return buf;
 }
 
@@ -957,6 +961,7 @@ bool parse_entry(const std::string& line, const TierConfig& base, TuneEntry& out
             else if (k == "fused") out.cfg.fused = x != 0;
             else if (k == "every1") out.cfg.every1 = x == 1 ? 2 : std::max(0, x);   // 1: no warp in role 0
             else if (k == "every2") out.cfg.every2 = x == 1 ? 2 : std::max(0, x);
+            else if (k == "every3") out.cfg.every3 = x == 1 ? 2 : std::max(0, x);
             else if (k == "minb") out.cfg.fused_minb = x;
             else if (k == "long") out.cfg.long_permille = std::max(0, std::min(250, x));
             else if (k == "ms") out.ms = float(std::atof(v.c_str()));
@@ -978,7 +983,7 @@ bool parse_entry(const std::string& line, const TierConfig& base, TuneEntry& out
                 return false;
             }
         }
-    if (out.cfg.fused && !fused_supported(out.cfg, out.alpha)) out.cfg.fused = false;
+    if (out.cfg.fused && fused_roles(out.cfg, out.alpha) == 0) out.cfg.fused = false;
     return true;
 }
 
@@ -1051,7 +1056,7 @@ std::vector<TierConfig> chain_candidates(const TierConfig& base, int alpha) {
             t.n_levels = 0;
             for (int v : ch) t.variant[t.n_levels++] = v;
             t.fused = fused != 0;
-            if (t.fused && !fused_supported(t, alpha)) continue;
+            if (t.fused && fused_roles(t, alpha) == 0) continue;
             out.push_back(t);
         }
     return out;

@@ -792,74 +792,98 @@ struct Source {
     uint64_t wait_limit_ns;     // live: give up after this long without progress
 };
 
-// Next unit for the group (group-uniform result).  Returns false when the source is
-// exhausted.  Waits on a live source are bounded; a wait that gives up raises kErrWait.
-template <int G>
-__device__ __forceinline__ bool next_unit(const Source& S, int gl, int lane, uint32_t gm, int chunk,
-                                          uint32_t& next, uint32_t& end, uint32_t& uidx, uint32_t* err) {
-    if (!S.live) {
+// A consumer's wait on a live source (lane 0 of the group keeps it): its ticket, the queue
+// words loaded by the previous poll, and the clock of its wait.  An idle group shares its
+// warp's instruction stream with groups that still compute, so a poll never waits on
+// memory: it decides on the values loaded by the poll before and issues the loads for the
+// next.  (The zero start is a valid, if stale, snapshot.)
+struct LiveWait {
+    uint32_t ticket = kNoUnit;      // taken ticket (slot index of the queue), or kNoUnit
+    uint32_t res = 0, pull = 0, fin = 0, slot = kNoUnit;
+    uint32_t sig = 0xffffffffu;     // queue length and finished producers when last changed
+    uint32_t t_us = 0;              // globaltimer (microseconds) of that change, 0 = not waiting
+};
+
+// Takes the group's next side extension from S without blocking (group-uniform result):
+// 1 = uidx holds a unit, 0 = none yet (a live source whose producers still run, or a poll
+// in progress), -1 = S is exhausted, or a live wait gave up after S.wait_limit_ns without
+// progress (kErrWait).  `progress` is set when the poll took a ticket (the caller then does
+// not back off).  LIVE: S is a live queue (else a finished list).
+template <int G, bool LIVE>
+__device__ __forceinline__ int take_unit(const Source& S, int gl, int lane, uint32_t gm, int chunk,
+                                         uint32_t& next, uint32_t& end, uint32_t& uidx, LiveWait& lw,
+                                         uint32_t* err, bool& progress) {
+    if constexpr (!LIVE) {
         if (next >= end) {
             uint32_t base = 0;
             const uint32_t take = G == 1 ? uint32_t(chunk) : 1u;
             if (gl == 0) base = atomicAdd(S.pull, take);
             if (G > 1) base = __shfl_sync(gm, base, lane - gl);
-            if (base >= S.n) return false;
+            if (base >= S.n) return -1;
             next = base;
             end = min(base + take, S.n);
         }
         uidx = S.list[next++];
-        return true;
+        return 1;
     }
+    int st = 0;
     uint32_t u = kNoUnit;
-    int got = 0;
     if (gl == 0) {
-        // Poll with plain coherent loads and exponential back-off (an idle consumer must not
-        // load L2 with atomics).  The wait gives up, raising kErrWait, once neither the
-        // queue length nor the finished-producer count has changed for S.wait_limit_ns.
+        // plain coherent loads (an idle consumer must not load L2 with atomics); a ticket is
+        // taken only when the queue holds a slot nobody has taken
         const volatile uint32_t* reserve = S.reserve;
+        const volatile uint32_t* pull = S.pull;
         const volatile uint32_t* done = S.producers_done;
-        const uint32_t ticket = atomicAdd(S.pull, 1u);
-        uint32_t last_res = 0xffffffffu, last_done = 0xffffffffu, pause = 128;
-        uint64_t t_change = globaltimer_ns();
-        for (;;) {
-            const uint32_t res = *reserve;
-            if (ticket < res) {
-                const volatile uint32_t* slot = S.list + ticket;
-                uint32_t v = *slot;
-                for (uint32_t w = 0; v == kNoUnit && w < kMaxSpin; w++) {
-                    __nanosleep(64);
-                    v = *slot;
-                }
-                if (v == kNoUnit) atomicOr(err, kErrWait);
-                else { u = v; got = 1; }
-                break;
+        const volatile uint32_t* list = S.list;
+        const uint32_t res = lw.res, fin = lw.fin;   // queue length known to this poll
+        bool took = false;
+        if (lw.ticket == kNoUnit) {
+            if (lw.pull < res) {
+                lw.ticket = atomicAdd(S.pull, 1u);   // its slot is loaded by the next poll
+                took = true;
             }
-            const uint32_t fin = *done;
-            if (fin >= S.n_producers) {
-                __threadfence();
-                if (ticket < *reserve) continue;   // a final push landed meanwhile
-                break;
-            }
-            const uint64_t now = globaltimer_ns();
-            if (res != last_res || fin != last_done) {
-                last_res = res;
-                last_done = fin;
-                t_change = now;
-                pause = 128;
-            } else if (now - t_change > S.wait_limit_ns) {
-                atomicOr(err, kErrWait);
-                break;
-            }
-            __nanosleep(pause);
-            pause = min(pause * 2u, 8192u);
+        } else if (lw.ticket < res && lw.slot != kNoUnit) {
+            u = lw.slot;   // the slot loaded by the previous poll, published
+            st = 1;
+            lw.ticket = kNoUnit;
+            lw.t_us = 0;
         }
+        if (st == 0 && !took) {
+            if (fin >= S.n_producers) {
+                // every producer has counted itself: the queue's length is final
+                __threadfence();
+                const uint32_t r2 = *reserve;
+                if (lw.ticket == kNoUnit ? *pull >= r2 : lw.ticket >= r2) st = -1;
+            }
+            if (st == 0) {
+                const uint32_t now = uint32_t(globaltimer_ns() >> 10);
+                const uint32_t sig = res ^ (fin << 20);
+                if (lw.t_us == 0 || sig != lw.sig) {
+                    lw.sig = sig;
+                    lw.t_us = now;
+                } else if (uint64_t(now - lw.t_us) << 10 > S.wait_limit_ns) {
+                    atomicOr(err, kErrWait);
+                    st = -1;
+                }
+            }
+        }
+        if (took) lw.t_us = 0;
+        progress = took;
+        // loads for the next poll; the slot of a held ticket only once the ticket is below
+        // a known queue length (tickets past it may lie beyond the queue)
+        lw.slot = kNoUnit;
+        if (!took && lw.ticket < res) lw.slot = list[lw.ticket];
+        lw.res = *reserve;
+        lw.pull = *pull;
+        lw.fin = *done;
     }
     if (G > 1) {
-        got = __shfl_sync(gm, got, lane - gl);
+        st = __shfl_sync(gm, st, lane - gl);
         u = __shfl_sync(gm, u, lane - gl);
+        progress = __shfl_sync(gm, progress ? 1 : 0, lane - gl) != 0;
     }
     uidx = u;
-    return got != 0;
+    return st;
 }
 
 // Record layout: 16 header ints (window, d, rb, L, U, T, best, bi, bj, barg, flags,
@@ -1009,7 +1033,7 @@ __device__ __forceinline__ bool load_record16(const Problem& P, const Z16& zc, u
 // least 64 * CG: 2W ints for each of the warp's 32 / G groups).  The areas belong to warps,
 // not to groups, so that warps of one block may run groups of different shapes at the same
 // time (the roles of the fused grid) without sharing shift buffers.
-template <int G, int CG, int A>
+template <int G, int CG, int A, bool LIVE>
 __device__ __forceinline__ void group_loop(const Problem& P, const Queues& Q, const Source& S, int out_q,
                                            int chunk, int32_t* smem, int stage, int warp_ints) {
     constexpr int W = G * CG;
@@ -1027,123 +1051,145 @@ __device__ __forceinline__ void group_loop(const Problem& P, const Queues& Q, co
     SideState s{};
     Res<CG, A> res;
     uint32_t uidx = 0, pair = 0, next = 0, end = 0;
-    bool active = false, skip_odd = false;
+    bool active = false, done = false, skip_odd = false;
     int32_t d_start = 0;
     uint64_t cells_start = 0;
+    LiveWait lw;   // unused (optimised away) for a finished list
+    uint32_t pause = 128;
     for (;;) {
-        if (!active) {
-            bool got = false;
-            while (next_unit<G>(S, gl, lane, gm, chunk, next, end, uidx, P.err)) {
+        bool took = false;
+        if (!active && !done) {
+            const int st = take_unit<G, LIVE>(S, gl, lane, gm, chunk, next, end, uidx, lw, P.err, took);
+            if (st < 0) done = true;
+            if (st > 0) {
+                took = true;
                 const Unit u = P.units[uidx];
                 if ((int64_t(u.m) + u.n) * P.max_abs >= kRegLimit || P.alpha != alpha_of(A) ||
                     (PK && !packed_ok(P))) {
                     if (gl == 0) push_unit(Q, kBandQ, uidx);
-                    continue;
+                } else {
+                    init_side(s, u, -W / 2);
+                    pair = u.pair;
+                    if (s.m + s.n == 0) {
+                        if (gl == 0) {
+                            write_side(P.results, pair, s.side, 0, 0, 0, 0, 1);
+                            atomicAdd(&P.stats[stage], 1ull);
+                            atomicAdd(&P.stats[4 + stage], 1ull);
+                        }
+                    } else {
+                        const uint32_t ri = P.rec_of ? __ldcg(P.rec_of + uidx) : kNoUnit;
+                        bool resumed = false;
+                        if (ri != kNoUnit) {
+                            if constexpr (PK) resumed = load_record16<G, CG>(P, zc, ri, s, R0, R1, gl);
+                            else resumed = load_record<G, CG>(P, ri, s, R0, R1, gl);
+                        }
+                        if (!resumed) {
+                            // S(0,0) = 0 in the middle of the window, every other cell -inf (Sec. 2.2)
+                            if constexpr (PK) {
+                                constexpr int t0 = (W / 2) % CG, p0 = t0 % (CG / 2);
+                                s.B0 = -P.X - P.gap - zc.th0;   // theta of d = 1 at theta0
+                                const int32_t z0 = -32 * s.B0;
+#pragma unroll
+                                for (int p = 0; p < NR; p++) {
+                                    R0[p] = kDead2;
+                                    R1[p] = kDead2;
+                                }
+                                if (gl == (W / 2) / CG) R0[p0] = t0 < CG / 2 ? pack2(z0, -1) : pack2(-1, z0);
+                            } else {
+#pragma unroll
+                                for (int t = 0; t < CG; t++) {
+                                    R0[t] = kNegR;
+                                    R1[t] = kNegR;
+                                }
+                                if (gl == (W / 2) / CG) R0[(W / 2) % CG] = 0;
+                            }
+                        }
+                        skip_odd = (s.d & 1) == 0;   // a side continued on an even anti-diagonal
+                        active = true;
+                        d_start = s.d;
+                        cells_start = s.cells;
+                    }
                 }
-                init_side(s, u, -W / 2);
-                pair = u.pair;
-                got = true;
-                break;
             }
-            if (!got) break;
-            if (s.m + s.n == 0) {
+        }
+        if (active) {
+            int r = kCont;
+            if constexpr (PK) {
+                if (!skip_odd) r = group_step16<G, CG, true, A>(s, res, R0, R1, P, zc, tab, gl, gm, gsm);
+                skip_odd = false;
+                if (r == kCont) r = group_step16<G, CG, false, A>(s, res, R1, R0, P, zc, tab, gl, gm, gsm);
+            } else {
+                if (!skip_odd) r = group_step<G, CG, true, A>(s, res, R0, R1, P, tab, gl, gm, gsm);
+                skip_odd = false;
+                if (r == kCont) r = group_step<G, CG, false, A>(s, res, R1, R0, P, tab, gl, gm, gsm);
+            }
+            if (r != kCont) {
+                active = false;
                 if (gl == 0) {
-                    write_side(P.results, pair, s.side, 0, 0, 0, 0, 1);
-                    atomicAdd(&P.stats[stage], 1ull);
-                    atomicAdd(&P.stats[4 + stage], 1ull);
+                    // window fill of this level: in-band cells against the slots evaluated
+                    atomicAdd(&P.stats[9], (unsigned long long)(s.cells - cells_start));
+                    atomicAdd(&P.stats[10], (unsigned long long)(s.d + 1 - d_start) * (unsigned long long)W);
                 }
-                continue;
-            }
-            const uint32_t ri = P.rec_of ? __ldcg(P.rec_of + uidx) : kNoUnit;
-            bool resumed = false;
-            if (ri != kNoUnit) {
-                if constexpr (PK) resumed = load_record16<G, CG>(P, zc, ri, s, R0, R1, gl);
-                else resumed = load_record<G, CG>(P, ri, s, R0, R1, gl);
-            }
-            if (!resumed) {
-                // S(0,0) = 0 in the middle of the window, every other cell -inf (Sec. 2.2)
-                if constexpr (PK) {
-                    constexpr int t0 = (W / 2) % CG, p0 = t0 % (CG / 2);
-                    s.B0 = -P.X - P.gap - zc.th0;   // theta of d = 1 at theta0
-                    const int32_t z0 = -32 * s.B0;
-#pragma unroll
-                    for (int p = 0; p < NR; p++) {
-                        R0[p] = kDead2;
-                        R1[p] = kDead2;
+                if (r == kDone) {
+                    if (gl == 0) {
+                        write_side(P.results, pair, s.side, s.best, uint32_t(s.bi), uint32_t(s.bj), s.flags,
+                                   s.cells);
+                        atomicAdd(&P.stats[stage], 1ull);
+                        atomicAdd(&P.stats[4 + stage], (unsigned long long)s.cells);
                     }
-                    if (gl == (W / 2) / CG) R0[p0] = t0 < CG / 2 ? pack2(z0, -1) : pack2(-1, z0);
                 } else {
-#pragma unroll
-                    for (int t = 0; t < CG; t++) {
-                        R0[t] = kNegR;
-                        R1[t] = kNegR;
+                    // overflow: hand the side to the next level, with its state when that level
+                    // can take it
+                    uint32_t ri = kNoUnit;
+                    if (out_q <= kBandQ && P.rec) {
+                        // bump-allocate kRecHeader + 2W ints of the record pool
+                        const uint32_t need = uint32_t(kRecHeader + 2 * W);
+                        if (gl == 0) ri = atomicAdd(P.rec_ctr, need);
+                        if (G > 1) ri = __shfl_sync(gm, ri, lane - gl);
+                        if (ri <= P.rec_cap && P.rec_cap - ri >= need) {
+                            if constexpr (PK) {
+                                if (s.d & 1) save_record16<G, CG>(P, ri, s, R0, R1, gl);
+                                else save_record16<G, CG>(P, ri, s, R1, R0, gl);
+                            } else {
+                                if (s.d & 1) save_record<G, CG>(P, ri, s, R0, R1, gl);
+                                else save_record<G, CG>(P, ri, s, R1, R0, gl);
+                            }
+                            if (G > 1) __syncwarp(gm);
+                        } else {
+                            ri = kNoUnit;
+                        }
                     }
-                    if (gl == (W / 2) / CG) R0[(W / 2) % CG] = 0;
+                    if (gl == 0) {
+                        if (ri != kNoUnit) {
+                            __threadfence();
+                            __stcg(P.rec_of + uidx, ri);
+                            __threadfence();
+                        } else {
+                            atomicAdd(&P.stats[7], (unsigned long long)s.cells);
+                        }
+                        push_unit(Q, out_q, uidx);
+                        atomicAdd(&P.stats[3], 1ull);
+                    }
                 }
             }
-            skip_odd = (s.d & 1) == 0;   // a side continued on an even anti-diagonal
-            active = true;
-            d_start = s.d;
-            cells_start = s.cells;
         }
-        int r = kCont;
-        if constexpr (PK) {
-            if (!skip_odd) r = group_step16<G, CG, true, A>(s, res, R0, R1, P, zc, tab, gl, gm, gsm);
-            skip_odd = false;
-            if (r == kCont) r = group_step16<G, CG, false, A>(s, res, R1, R0, P, zc, tab, gl, gm, gsm);
+        // a finished list: each group leaves when it is exhausted.  A live source: the warp
+        // leaves once every group is done, and backs off before polling again when no group
+        // is at work and none took a ticket
+        if constexpr (LIVE) {
+            if (__all_sync(0xffffffffu, done)) break;
+            if (__any_sync(0xffffffffu, active || took)) {
+                pause = 128;
+            } else {
+                __nanosleep(pause);
+                pause = min(pause * 2u, 8192u);
+            }
         } else {
-            if (!skip_odd) r = group_step<G, CG, true, A>(s, res, R0, R1, P, tab, gl, gm, gsm);
-            skip_odd = false;
-            if (r == kCont) r = group_step<G, CG, false, A>(s, res, R1, R0, P, tab, gl, gm, gsm);
-        }
-        if (r == kCont) continue;
-        active = false;
-        if (gl == 0) {
-            // window fill of this level: in-band cells against the slots evaluated
-            atomicAdd(&P.stats[9], (unsigned long long)(s.cells - cells_start));
-            atomicAdd(&P.stats[10], (unsigned long long)(s.d + 1 - d_start) * (unsigned long long)W);
-        }
-        if (r == kDone) {
-            if (gl == 0) {
-                write_side(P.results, pair, s.side, s.best, uint32_t(s.bi), uint32_t(s.bj), s.flags, s.cells);
-                atomicAdd(&P.stats[stage], 1ull);
-                atomicAdd(&P.stats[4 + stage], (unsigned long long)s.cells);
-            }
-            continue;
-        }
-        // overflow: hand the side to the next level, with its state when that level can take it
-        uint32_t ri = kNoUnit;
-        if (out_q <= kBandQ && P.rec) {
-            // bump-allocate kRecHeader + 2W ints of the record pool
-            const uint32_t need = uint32_t(kRecHeader + 2 * W);
-            if (gl == 0) ri = atomicAdd(P.rec_ctr, need);
-            if (G > 1) ri = __shfl_sync(gm, ri, lane - gl);
-            if (ri <= P.rec_cap && P.rec_cap - ri >= need) {
-                if constexpr (PK) {
-                    if (s.d & 1) save_record16<G, CG>(P, ri, s, R0, R1, gl);
-                    else save_record16<G, CG>(P, ri, s, R1, R0, gl);
-                } else {
-                    if (s.d & 1) save_record<G, CG>(P, ri, s, R0, R1, gl);
-                    else save_record<G, CG>(P, ri, s, R1, R0, gl);
-                }
-                if (G > 1) __syncwarp(gm);
-            } else {
-                ri = kNoUnit;
-            }
-        }
-        if (gl == 0) {
-            if (ri != kNoUnit) {
-                __threadfence();
-                __stcg(P.rec_of + uidx, ri);
-                __threadfence();
-            } else {
-                atomicAdd(&P.stats[7], (unsigned long long)s.cells);
-            }
-            push_unit(Q, out_q, uidx);
-            atomicAdd(&P.stats[3], 1ull);
+            if (done) break;
         }
     }
 }
+
 
 __device__ __forceinline__ Source static_source(const Queues& Q, int in_q) {
     Source S{};
@@ -1159,7 +1205,8 @@ template <int G, int CG, int MINB, int A>
 __global__ void __launch_bounds__(128, MINB) k_group(Problem P, Queues Q, int in_q, int out_q, int chunk) {
     extern __shared__ __align__(16) int32_t group_smem[];
     build_table<A>(group_smem, P);
-    group_loop<G, CG, A>(P, Q, static_source(Q, in_q), out_q, chunk, group_smem, in_q < 0 ? 0 : 1, 64 * CG);
+    group_loop<G, CG, A, false>(P, Q, static_source(Q, in_q), out_q, chunk, group_smem, in_q < 0 ? 0 : 1,
+                                64 * CG);
 }
 
 // The first register levels fused into one persistent, cooperatively launched grid.
@@ -1182,9 +1229,13 @@ struct RolePlan {
                                 // follow the grid, else the band tier's queue
     uint64_t wait_limit_ns;     // live-queue waits give up (kErrWait) after this long without
                                 // progress
+    int every3;                 // four-role grids: warp gw starts in role 3 if
+                                // gw % every3 == every3 - 1 (checked first)
+    uint32_t producers2;        // four-role grids: warps that run role 0, 1 or 2
 };
 
-__host__ __device__ __forceinline__ int start_role(uint32_t gw, int every1, int every2) {
+__host__ __device__ __forceinline__ int start_role(uint32_t gw, int every1, int every2, int every3 = 0) {
+    if (every3 > 0 && gw % uint32_t(every3) == uint32_t(every3 - 1)) return 3;
     if (every2 > 0 && gw % uint32_t(every2) == uint32_t(every2 - 1)) return 2;
     if (every1 > 0 && gw % uint32_t(every1) == 0) return 1;
     return 0;
@@ -1240,22 +1291,67 @@ __global__ void __launch_bounds__(128, MINB) k_fused(Problem P, Queues Q, RolePl
             Source SL = static_source(Q, -1);
             SL.pull = &Q.ctr[kLongPull];
             SL.n = R.n_long;
-            group_loop<GL, CL, A>(P, Q, SL, 0, 1, group_smem, 0, kWarpInts);
+            group_loop<GL, CL, A, false>(P, Q, SL, 0, 1, group_smem, 0, kWarpInts);
         }
     }
     if (role == 0) {
         Source S0 = static_source(Q, -1);
         S0.list = Q.order + R.n_long;
         S0.n = Q.n_units - R.n_long;
-        group_loop<G0, C0, A>(P, Q, S0, 0, chunk, group_smem, 0, kWarpInts);
+        group_loop<G0, C0, A, false>(P, Q, S0, 0, chunk, group_smem, 0, kWarpInts);
         signal_done(done0);
     }
     if (role <= 1) {
-        group_loop<G1, C1, A>(P, Q, live_source(Q, 0, done0, R.producers0, R.wait_limit_ns), 1, 1, group_smem, 0,
+        group_loop<G1, C1, A, true>(P, Q, live_source(Q, 0, done0, R.producers0, R.wait_limit_ns), 1, 1, group_smem, 0,
                               kWarpInts);
         signal_done(done1);
     }
-    group_loop<G2, C2, A>(P, Q, live_source(Q, 1, done1, R.producers1, R.wait_limit_ns), R.out2, 1, group_smem, 0,
+    group_loop<G2, C2, A, true>(P, Q, live_source(Q, 1, done1, R.producers1, R.wait_limit_ns), R.out2, 1, group_smem, 0,
+                          kWarpInts);
+}
+
+// Four roles: k_fused with a fourth level.  Role 2 appends its overflows to the live queue
+// q[2], which role 3 consumes; role 3's overflows go to R.out2 (q[3] when later register
+// levels follow the grid, else the band tier).  A warp that leaves role 2 counts itself in
+// done[2].
+template <int G0, int C0, int G1, int C1, int G2, int C2, int G3, int C3, int MINB, int A, int GL, int CL>
+__global__ void __launch_bounds__(128, MINB) k_fused4(Problem P, Queues Q, RolePlan R, int chunk) {
+    constexpr int kC13 = C1 > C3 ? C1 : C3;
+    constexpr int kWarpInts = fused_warp_ints<C0, kC13, C2, CL>();
+    extern __shared__ __align__(16) int32_t group_smem[];
+    build_table<A>(group_smem, P);
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    uint32_t* done0 = &Q.ctr[1 + 2 * kLevels];
+    uint32_t* done1 = &Q.ctr[2 + 2 * kLevels];
+    uint32_t* done2 = &Q.ctr[kDone2];
+    const bool long_role = GL > 0 && gw < R.long_warps;
+    const int role = long_role ? 0 : start_role(gw, R.every1, R.every2, R.every3);
+    if constexpr (GL > 0) {
+        if (long_role) {
+            Source SL = static_source(Q, -1);
+            SL.pull = &Q.ctr[kLongPull];
+            SL.n = R.n_long;
+            group_loop<GL, CL, A, false>(P, Q, SL, 0, 1, group_smem, 0, kWarpInts);
+        }
+    }
+    if (role == 0) {
+        Source S0 = static_source(Q, -1);
+        S0.list = Q.order + R.n_long;
+        S0.n = Q.n_units - R.n_long;
+        group_loop<G0, C0, A, false>(P, Q, S0, 0, chunk, group_smem, 0, kWarpInts);
+        signal_done(done0);
+    }
+    if (role <= 1) {
+        group_loop<G1, C1, A, true>(P, Q, live_source(Q, 0, done0, R.producers0, R.wait_limit_ns), 1, 1, group_smem, 0,
+                              kWarpInts);
+        signal_done(done1);
+    }
+    if (role <= 2) {
+        group_loop<G2, C2, A, true>(P, Q, live_source(Q, 1, done1, R.producers1, R.wait_limit_ns), 2, 1, group_smem, 0,
+                              kWarpInts);
+        signal_done(done2);
+    }
+    group_loop<G3, C3, A, true>(P, Q, live_source(Q, 2, done2, R.producers2, R.wait_limit_ns), R.out2, 1, group_smem, 0,
                           kWarpInts);
 }
 
@@ -1316,6 +1412,49 @@ static cudaError_t launch_fused(const Problem& P, const Queues& Q, const TierCon
     // consumers' waits run out (bounded) and the batch reports kErrWait
     R.producers0 += cfg.phantom_producer ? 1u : 0u;
     R.producers1 += cfg.phantom_producer ? 1u : 0u;
+    Problem p = P;
+    Queues q = Q;
+    int ch = cfg.chunk;
+    void* args[] = {&p, &q, &R, &ch};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(fn), dim3(blocks), dim3(128), args, smem, st);
+}
+
+template <int G0, int C0, int G1, int C1, int G2, int C2, int G3, int C3, int MINB, int A, int GL, int CL>
+static cudaError_t launch_fused4(const Problem& P, const Queues& Q, const TierConfig& cfg, int n_sm,
+                                 cudaStream_t st) {
+    constexpr int kC13 = C1 > C3 ? C1 : C3;
+    const size_t smem = (size_t(kLutInts) + 4 * size_t(fused_warp_ints<C0, kC13, C2, CL>())) * sizeof(int32_t);
+    auto fn = k_fused4<G0, C0, G1, C1, G2, C2, G3, C3, MINB, A, GL, CL>;
+    static int occ = 0;
+    if (occ == 0) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 128, smem);
+        if (e != cudaSuccess) return e;
+        if (occ < 1) return cudaErrorInvalidConfiguration;
+    }
+    // every block must be resident at once: consumers wait for producers of the same grid
+    const int blocks = n_sm * occ;
+    const uint32_t n_warps = uint32_t(blocks) * 4;
+    RolePlan R{cfg.every1, cfg.every2, 0, 0, 0, 0, cfg.n_levels > 4 ? 3 : kBandQ,
+               cfg.wait_limit_ms > 0 ? uint64_t(cfg.wait_limit_ms) * 1000000ull : kWaitLimitNs, cfg.every3, 0};
+    if (GL > 0 && cfg.long_permille > 0) {
+        R.n_long = uint32_t(uint64_t(Q.n_units) * uint32_t(cfg.long_permille) / 1000u);
+        R.long_warps = std::min(R.n_long, n_warps / 4);   // at most a quarter of the grid
+    }
+    for (uint32_t w = 0; w < n_warps; w++) {
+        const int r = w < R.long_warps ? 0 : start_role(w, R.every1, R.every2, R.every3);
+        R.producers0 += r == 0;
+        R.producers1 += r <= 1;
+        R.producers2 += r <= 2;
+    }
+    if (R.producers0 == 0) return cudaErrorInvalidValue;   // nobody would take the ordered units
+    // failure-detection test: a role-0 producer that never finishes
+    R.producers0 += cfg.phantom_producer ? 1u : 0u;
+    R.producers1 += cfg.phantom_producer ? 1u : 0u;
+    R.producers2 += cfg.phantom_producer ? 1u : 0u;
     Problem p = P;
     Queues q = Q;
     int ch = cfg.chunk;

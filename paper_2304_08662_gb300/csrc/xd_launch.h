@@ -6,9 +6,11 @@
 namespace xd {
 
 // queue counters: [0] order pull, [1 + 2k] / [2 + 2k] length / pull of q[k], then producer
-// warps finished (two), the record counter, and the pull counter of the long-side head
-constexpr int kNumCtr = 5 + 2 * kLevels;
+// warps finished (roles 0 and 1), the record counter, the pull counter of the long-side
+// head, and producer warps finished in role 2 (four-role grids)
+constexpr int kNumCtr = 6 + 2 * kLevels;
 constexpr int kLongPull = 4 + 2 * kLevels;
+constexpr int kDone2 = 5 + 2 * kLevels;
 
 cudaError_t launch_pack(int alpha, const uint8_t* codes, uint64_t n_codes, uint32_t* store,
                         uint32_t* err, int n_sm, cudaStream_t st);
@@ -46,7 +48,9 @@ struct TierConfig {
     int chunk;                          // units pulled per queue access (single-lane groups)
     bool fused;                         // fuse levels 0-2 into one persistent grid
     int every1, every2;                 // fused grid: warps starting in role 1 / role 2
-    int fused_minb;                     // fused grid register budget: resident blocks per SM
+    int every3;                         // four-role grid: warps starting in role 3 (0: three roles)
+    int fused_minb;                     // fused grid register budget: 3 = three resident blocks per SM
+                                        // (no long role), else the 128-register build (four)
     int long_permille;                  // fused grid: head of the cost order (per mille of the
                                         // units) run first by wider groups (0 = none)
     int long_shape;                     // their groups: 0 = 32 lanes x 4 slots, 1 = 8 x 4, 2 = 4 x 8
@@ -66,6 +70,9 @@ int variant_window(int variant);
 bool fused_supported(const TierConfig& cfg, int alpha);
 cudaError_t launch_fused_levels(const Problem& P, const Queues& Q, const TierConfig& cfg, int n_sm,
                                 cudaStream_t st);
+// Levels 0-3 in one grid (four roles); fused_roles(cfg, alpha) is 4 when the variant
+// quadruple is compiled and cfg asks for it, 3 for the triple, else 0.
+int fused_roles(const TierConfig& cfg, int alpha);
 
 // DNA levels (xd_tiers_dna.cu) and protein instantiations (xd_tiers_prot.cu), reached
 // through the launchers above.

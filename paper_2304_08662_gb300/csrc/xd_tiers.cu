@@ -58,19 +58,57 @@ bool fused_supported(const TierConfig& c, int alpha) {
            (a == kG1C32 && b == kG8C32 && d == kG32C16) || (a == kG1C32 && b == kG8C32 && d == kG16C32);
 }
 
+// Four-role grids compiled (packed scores only).
+static bool fused4_supported(const TierConfig& c, int alpha) {
+    if (c.n_levels < 4) return false;
+    const int a = c.variant[0], b = c.variant[1], d = c.variant[2], e = c.variant[3];
+    if (alpha == 20) return a == kG4C16 && b == kG8C16 && d == kG16C16 && e == kG32C32;
+    return (a == kG1C32 && b == kG8C16 && d == kG16C16 && e == kG32C16) ||
+           (a == kG1C24 && b == kG8C16 && d == kG16C16 && e == kG32C16) ||
+           (a == kG1C20 && b == kG8C16 && d == kG16C16 && e == kG32C16) ||
+           (a == kG1C32 && b == kG4C16 && d == kG8C16 && e == kG16C16);
+}
+
+int fused_roles(const TierConfig& c, int alpha) {
+    if (!c.fused) return 0;
+    if (fused4_supported(c, alpha)) return 4;
+    return fused_supported(c, alpha) ? 3 : 0;
+}
+
+static cudaError_t launch_fused4_levels(const Problem& P, const Queues& Q, const TierConfig& cfg, int n_sm,
+                                        cudaStream_t st) {
+    const int a = cfg.variant[0], b = cfg.variant[1], d = cfg.variant[2], e = cfg.variant[3];
+    if (!packed_ok(P)) return cudaErrorInvalidValue;
+    if (P.alpha == 20) {
+        if (a == kG4C16 && b == kG8C16 && d == kG16C16 && e == kG32C32)
+            return launch_fused4<4, 16, 8, 16, 16, 16, 32, 32, 2, kProt16, 0, 4>(P, Q, cfg, n_sm, st);
+        return cudaErrorInvalidValue;
+    }
+    if (a == kG1C32 && b == kG8C16 && d == kG16C16 && e == kG32C16)
+        return launch_fused4<1, 32, 8, 16, 16, 16, 32, 16, 4, kDna16, 8, 4>(P, Q, cfg, n_sm, st);
+    if (a == kG1C24 && b == kG8C16 && d == kG16C16 && e == kG32C16)
+        return launch_fused4<1, 24, 8, 16, 16, 16, 32, 16, 2, kDna16, 8, 4>(P, Q, cfg, n_sm, st);
+    if (a == kG1C20 && b == kG8C16 && d == kG16C16 && e == kG32C16)
+        return launch_fused4<1, 20, 8, 16, 16, 16, 32, 16, 2, kDna16, 8, 4>(P, Q, cfg, n_sm, st);
+    if (a == kG1C32 && b == kG4C16 && d == kG8C16 && e == kG16C16)
+        return launch_fused4<1, 32, 4, 16, 8, 16, 16, 16, 2, kDna16, 8, 4>(P, Q, cfg, n_sm, st);
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_fused_levels(const Problem& P, const Queues& Q, const TierConfig& cfg, int n_sm,
                                 cudaStream_t st) {
     const int a = cfg.variant[0], b = cfg.variant[1], d = cfg.variant[2];
+    if (fused_roles(cfg, P.alpha) == 4) return launch_fused4_levels(P, Q, cfg, n_sm, st);
     if (P.alpha == 20) return launch_fused_levels_prot(P, Q, cfg, n_sm, st);
     if (!packed_ok(P)) return cudaErrorInvalidValue;   // DNA grids are compiled packed only
     if (a == kG1C32 && b == kG4C32 && d == kG8C32) return launch_fused<1, 32, 4, 32, 8, 32, 2, kDna16>(P, Q, cfg, n_sm, st);
     if (a == kG1C32 && b == kG8C16 && d == kG16C16) return launch_fused<1, 32, 8, 16, 16, 16, 2, kDna16>(P, Q, cfg, n_sm, st);
+    // 128 registers (four blocks per SM, no spills) unless fused_minb asks for three blocks
     if (a == kG1C32 && b == kG16C16 && d == kG32C16)
-        return cfg.fused_minb == 4   ? launch_fused<1, 32, 16, 16, 32, 16, 4, kDna16>(P, Q, cfg, n_sm, st)
-               : cfg.fused_minb == 3 ? launch_fused<1, 32, 16, 16, 32, 16, 3, kDna16>(P, Q, cfg, n_sm, st)
-               : cfg.long_shape == 1 ? launch_fused<1, 32, 16, 16, 32, 16, 2, kDna16, 8, 4>(P, Q, cfg, n_sm, st)
-               : cfg.long_shape == 2 ? launch_fused<1, 32, 16, 16, 32, 16, 2, kDna16, 4, 8>(P, Q, cfg, n_sm, st)
-                                     : launch_fused<1, 32, 16, 16, 32, 16, 2, kDna16, 32, 4>(P, Q, cfg, n_sm, st);
+        return cfg.fused_minb == 3   ? launch_fused<1, 32, 16, 16, 32, 16, 3, kDna16>(P, Q, cfg, n_sm, st)
+               : cfg.long_shape == 2 ? launch_fused<1, 32, 16, 16, 32, 16, 4, kDna16, 4, 8>(P, Q, cfg, n_sm, st)
+               : cfg.long_shape == 0 ? launch_fused<1, 32, 16, 16, 32, 16, 4, kDna16, 32, 4>(P, Q, cfg, n_sm, st)
+                                     : launch_fused<1, 32, 16, 16, 32, 16, 4, kDna16, 8, 4>(P, Q, cfg, n_sm, st);
     if (a == kG1C32 && b == kG8C16 && d == kG32C16) return launch_fused<1, 32, 8, 16, 32, 16, 2, kDna16>(P, Q, cfg, n_sm, st);
     if (a == kG1C32 && b == kG32C8 && d == kG32C16) return launch_fused<1, 32, 32, 8, 32, 16, 2, kDna16, 32, 4>(P, Q, cfg, n_sm, st);
     if (a == kG1C16 && b == kG32C8 && d == kG32C16) return launch_fused<1, 16, 32, 8, 32, 16, 2, kDna16, 32, 4>(P, Q, cfg, n_sm, st);
