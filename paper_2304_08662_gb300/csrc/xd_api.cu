@@ -1043,7 +1043,8 @@ std::vector<TierConfig> chain_candidates(const TierConfig& base, int alpha) {
                   {kG4C16, kG16C16, kG32C32},         {kG1C16, kG8C16, kG32C16, kG32C32},
                   {kG1C32, kG8C16, kG16C16, kG32C32}, {kG32C16, kG32C32},
                   {kG32C8, kG32C32},                  {kG16C8, kG32C16, kG32C32},
-                  {kG8C16, kG32C32},                  {kG1C24, kG16C16, kG32C16, kG32C32}};
+                  {kG8C16, kG32C32},                  {kG1C24, kG16C16, kG32C16, kG32C32},
+                  {kG1C32, kG8C16, kG16C16, kG32C16, kG32C32}};
     else
         chains = {{kG4C16, kG16C16, kG32C32}, {kG1C16, kG4C16, kG16C16, kG32C32},
                   {kG8C16, kG32C16, kG32C32}, {kG4C16, kG8C16, kG32C16, kG32C32},

@@ -1173,19 +1173,17 @@ __device__ __forceinline__ void group_loop(const Problem& P, const Queues& Q, co
                 }
             }
         }
-        // a finished list: each group leaves when it is exhausted.  A live source: the warp
-        // leaves once every group is done, and backs off before polling again when no group
-        // is at work and none took a ticket
+        // the warp leaves once every group is done (measured faster than leaving group by
+        // group); a warp of a live source with no group at work and none that took a ticket
+        // backs off before polling again
+        if (__all_sync(0xffffffffu, done)) break;
         if constexpr (LIVE) {
-            if (__all_sync(0xffffffffu, done)) break;
             if (__any_sync(0xffffffffu, active || took)) {
                 pause = 128;
             } else {
                 __nanosleep(pause);
                 pause = min(pause * 2u, 8192u);
             }
-        } else {
-            if (done) break;
         }
     }
 }

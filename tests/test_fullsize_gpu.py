@@ -125,7 +125,7 @@ def test_full_size_uneven_restricted(ctx, uneven, uneven_unrestricted, delta):
 
 
 def _ctx_env(env):
-    keys = ("XD_FUSED", "XD_FUSED_PROT", "XD_EVERY1", "XD_EVERY2", "XD_LONG_PERMILLE")
+    keys = ("XD_FUSED", "XD_FUSED_PROT", "XD_EVERY1", "XD_EVERY2", "XD_EVERY3", "XD_LONG_PERMILLE", "XD_CHAIN")
     old = {k: os.environ.get(k) for k in keys}
     for k in keys:
         os.environ.pop(k, None)
@@ -140,14 +140,15 @@ def _ctx_env(env):
                 os.environ[k] = v
 
 
-@pytest.mark.parametrize("X", [10, 20, 50])
-def test_full_size_fused_grid_equals_level_launches(X):
+@pytest.mark.parametrize("X,chain", [(10, None), (20, None), (50, None), (20, "1,3,4,5,6")])
+def test_full_size_fused_grid_equals_level_launches(X, chain):
     """Every one of the 100,000 long-read pairs: the persistent grid whose warps run
     different group shapes at once (and the long-side role) must give exactly the results of
-    one launch per register level."""
+    one launch per register level; also the four-role grid (windows 32, 128, 256, 512)."""
     b = synth.dna_longread().with_params(X=X)
-    fused = _ctx_env({"XD_EVERY1": "2", "XD_EVERY2": "4", "XD_LONG_PERMILLE": "5"})
-    split = _ctx_env({"XD_FUSED": "0"})
+    extra = {"XD_CHAIN": chain, "XD_EVERY3": "8"} if chain else {}
+    fused = _ctx_env({"XD_EVERY1": "2", "XD_EVERY2": "4", "XD_LONG_PERMILLE": "5", **extra})
+    split = _ctx_env({"XD_FUSED": "0", **({"XD_CHAIN": chain} if chain else {})})
     try:
         a = _run_device(fused, b)
         c = _run_device(split, b)

@@ -29,9 +29,11 @@ FIELDS = ("score", "h_ext", "v_ext", "flags", "cells")
 # generic: every side in the generic tier
 MODES = {"tiered": {}, "generic": {"XD_TIERS": "generic"},
          "throughput": {"XD_LATENCY_UNITS": "0"},
-         "split": {"XD_LATENCY_UNITS": "0", "XD_FUSED": "0"}}
+         "split": {"XD_LATENCY_UNITS": "0", "XD_FUSED": "0"},
+         # DNA through the four-role fused grid (windows 32, 128, 256, 512)
+         "four_roles": {"XD_LATENCY_UNITS": "0", "XD_CHAIN": "1,3,4,5,6", "XD_EVERY1": "16"}}
 ENV_KEYS = ("XD_TIERS", "XD_FUSED", "XD_FUSED_PROT", "XD_LATENCY_UNITS", "XD_CHAIN", "XD_CHAIN_PROT",
-            "XD_CHAIN_SMALL")
+            "XD_CHAIN_SMALL", "XD_EVERY1")
 
 
 def _ctx(mode, env=None):
@@ -50,7 +52,7 @@ def _ctx(mode, env=None):
                 os.environ[k] = v
 
 
-@pytest.fixture(scope="module", params=["tiered", "throughput", "split", "generic"])
+@pytest.fixture(scope="module", params=["tiered", "throughput", "split", "generic", "four_roles"])
 def ctx(request):
     c = _ctx(request.param)
     yield c
