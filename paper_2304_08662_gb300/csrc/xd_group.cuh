@@ -745,9 +745,20 @@ __device__ __forceinline__ int group_step16(SideState& s, Res<CG, A>& res, uint3
     const bool any = lm != 0;
     int32_t first = any ? sb + __ffs(lm) - 1 : INT32_MAX;
     int32_t last = any ? sb + 31 - __clz(lm) : -1;
-    first = gmin<G>(first, gm);
-    if (first == INT32_MAX) return kDone;
-    last = gmax<G>(last, gm);
+    if constexpr (G > 1 && G < 32) {
+        // first and last live slot of the group in one shuffle tree of 16x2 maxima:
+        // (last + 1, 0xffff - first), a lane without live slots contributing (0, 0)
+        uint32_t fl = any ? (uint32_t(last + 1) << 16) | uint32_t(0xffff - first) : 0u;
+#pragma unroll
+        for (int k = G / 2; k >= 1; k >>= 1) fl = __vmaxu2(fl, __shfl_xor_sync(gm, fl, k));
+        if ((fl & 0xffffu) == 0) return kDone;
+        first = 0xffff - int32_t(fl & 0xffffu);
+        last = int32_t(fl >> 16) - 1;
+    } else {
+        first = gmin<G>(first, gm);
+        if (first == INT32_MAX) return kDone;
+        last = gmax<G>(last, gm);
+    }
     // best cell of the group: z, then 1023 - window slot (the lowest slot wins ties); a lane
     // without live slots has a lane key <= 30 and loses to every live one (z >= theta0 > 0)
     const int32_t kl = max(lo16(mk), hi16(mk));
