@@ -449,7 +449,10 @@ void default_tiers(xd_ctx* c) {
     TierConfig& t = c->tiers;
     for (int v = 0; v < kNumGroupVariants; v++) t.blocks_per_sm[v] = 3;
     for (int v : {kG1C32, kG32C32, kG4C32, kG8C32, kG16C32, kG2C32}) t.blocks_per_sm[v] = 2;
-    for (int v : {kG4C8, kG8C8, kG16C8, kG32C8}) t.blocks_per_sm[v] = 4;
+    // 8- and 16-slot levels: 128 registers (four blocks per SM) in the packed builds; the
+    // 32-bit builds of the 16-slot levels hold three, the rest of their grid runs after
+    for (int v : {kG4C8, kG8C8, kG16C8, kG32C8, kG1C16, kG2C16, kG4C16, kG8C16, kG16C16, kG32C16})
+        t.blocks_per_sm[v] = 4;
     t.chunk = std::max(1, env_int("XD_CHUNK", 1));
     t.fused = env_int("XD_FUSED", 1) != 0;
     t.every1 = std::max(0, env_int("XD_EVERY1", 8));
@@ -474,6 +477,8 @@ void default_tiers(xd_ctx* c) {
     set_chain(c->tiers_tiny_x, {kG1C20, kG16C16, kG32C16, kG32C32});
     c->tiers_large_x = t;
     set_chain(c->tiers_large_x, {kG4C16, kG16C16, kG32C32});
+    // measured at X = 50: three blocks per SM for its 16-slot levels ahead of four (~1%)
+    for (int v : {kG4C16, kG16C16}) c->tiers_large_x.blocks_per_sm[v] = 3;
     c->tiers_large_x.every1 = std::max(0, env_int("XD_EVERY1", 4));
     c->tiers_large_x.every2 = std::max(0, env_int("XD_EVERY2", 16));
     if (c->tiers_large_x.every1 == 1) c->tiers_large_x.every1 = 2;
