@@ -500,6 +500,9 @@ void default_tiers(xd_ctx* c) {
     set_chain(c->tiers_latency_mid, {kG16C8, kG32C16, kG32C32});
     c->tiers_latency_prot = c->tiers_latency;
     set_chain(c->tiers_latency_prot, {kG32C8, kG32C32});
+    // small batches: the 32 x 16 level with three blocks per SM, as measured for serving
+    for (TierConfig* tc : {&c->tiers_latency, &c->tiers_latency_mid, &c->tiers_latency_prot})
+        tc->blocks_per_sm[kG32C16] = 3;
     c->latency_units = uint32_t(std::max(0, env_int("XD_LATENCY_UNITS", int(kLatencyUnits))));
     // overrides for experiments: comma-separated variant ids
     if (const char* ch = std::getenv("XD_CHAIN_PROT")) parse_chain(ch, c->tiers_protein);
