@@ -14,7 +14,7 @@ cudaError_t launch_level_dna16(const Problem& P, const Queues& Q, int variant, i
         case kG4C16: return launch_group<4, 16, 4, kDna16>(P, Q, in_q, out_q, blocks, chunk, st);
         case kG8C16: return launch_group<8, 16, 4, kDna16>(P, Q, in_q, out_q, blocks, chunk, st);
         case kG16C16: return launch_group<16, 16, 4, kDna16>(P, Q, in_q, out_q, blocks, chunk, st);
-        case kG32C16: return launch_group<32, 16, 4, kDna16>(P, Q, in_q, out_q, blocks, chunk, st);
+        case kG32C16: return launch_group<32, 16, 3, kDna16>(P, Q, in_q, out_q, blocks, chunk, st);
         case kG32C32: return launch_group<32, 32, 2, kDna16>(P, Q, in_q, out_q, blocks, chunk, st);
         case kG4C32: return launch_group<4, 32, 2, kDna16>(P, Q, in_q, out_q, blocks, chunk, st);
         case kG8C32: return launch_group<8, 32, 2, kDna16>(P, Q, in_q, out_q, blocks, chunk, st);

@@ -12,7 +12,7 @@ cudaError_t launch_level_prot16(const Problem& P, const Queues& Q, int variant, 
         case kG4C16: return launch_group<4, 16, 4, kProt16>(P, Q, in_q, out_q, blocks, chunk, st);
         case kG8C16: return launch_group<8, 16, 4, kProt16>(P, Q, in_q, out_q, blocks, chunk, st);
         case kG16C16: return launch_group<16, 16, 4, kProt16>(P, Q, in_q, out_q, blocks, chunk, st);
-        case kG32C16: return launch_group<32, 16, 4, kProt16>(P, Q, in_q, out_q, blocks, chunk, st);
+        case kG32C16: return launch_group<32, 16, 3, kProt16>(P, Q, in_q, out_q, blocks, chunk, st);
         case kG32C32: return launch_group<32, 32, 2, kProt16>(P, Q, in_q, out_q, blocks, chunk, st);
         case kG8C8: return launch_group<8, 8, 4, kProt16>(P, Q, in_q, out_q, blocks, chunk, st);
         case kG32C8: return launch_group<32, 8, 4, kProt16>(P, Q, in_q, out_q, blocks, chunk, st);
