@@ -8,10 +8,10 @@
 // follows the main diagonal does not move in the window; it drifts only with the indels of
 // the alignment.  The window is re-centred through shared memory when the band nears its
 // edge (one guard slot on each side holds the gap predecessors of the band's end cells).
-// A side whose band outgrows the window is appended to the next level's queue and
-// restarted there with a wider window.  The two anti-diagonals are the paper's
-// memory-restricted pair (Gotoh's two-diagonal scheme, Sec. 3): the new anti-diagonal
-// overwrites d-2 slot by slot.
+// A side whose band outgrows the window is appended to the next level's queue with an
+// escalation record and continued there in a wider window.  The two anti-diagonals are
+// the paper's memory-restricted pair (Gotoh's two-diagonal scheme, Sec. 3): the new
+// anti-diagonal overwrites d-2 slot by slot.
 //
 // Per anti-diagonal (Sec. 3, Algorithm 1): band [first live, last live + 1] of d-1 clipped
 // to the matrix and, when restricted, to delta_b cells centred on d-1's best cell; per cell
@@ -19,13 +19,18 @@
 // the DPX add-max, the X-Drop test against T of the completed anti-diagonals; then group
 // reductions of the live range and of the best cell (lowest i on ties).
 //
+// Scores: the template argument A selects the representation, 32-bit slots (A = 4 DNA,
+// A = 20 protein: group_step, cells_of) or 16-bit packed slots, two per register (A =
+// kDna16, kProt16: group_step16, cells16), described with kDna16 below.
+//
 // Residues: each lane keeps slices of H and V for its slots (2-bit fields for DNA; for
 // protein, 16-bit table offsets, two slots per register).  On odd d the V slice gains one
 // residue, on even d the H slice does; residues come from two oriented streams per lane
 // whose next store word is always prefetched.
 //
-// This header holds the templates; xd_tiers.cu instantiates the DNA kernels (A = 4) and
-// xd_tiers_prot.cu the protein ones (A = 20).
+// This header holds the templates; xd_tiers.cu instantiates the fused grids,
+// xd_tiers_dna.cu / xd_tiers_dna16.cu the DNA level kernels (32-bit / packed) and
+// xd_tiers_prot.cu / xd_tiers_prot16.cu the protein ones.
 #pragma once
 #include <algorithm>
 #include <cstdint>
