@@ -115,6 +115,19 @@ def paper_cells(b):
     return float((b.lengths[p[:, 0]].astype(np.float64) * b.lengths[p[:, 1]]).sum())
 
 
+def job_totals(dist, dev, per_rank, slowest):
+    """Whole-job figures over the ranks of a replicated run: the sums of `per_rank` (cells,
+    pairs) and the maximum of `slowest` (seconds).  Without a process group: the inputs."""
+    if dist is None:
+        return [float(x) for x in per_rank], [float(x) for x in slowest]
+    import torch
+    s = torch.tensor([float(x) for x in per_rank], dtype=torch.float64, device=dev)
+    m = torch.tensor([float(x) for x in slowest], dtype=torch.float64, device=dev)
+    dist.all_reduce(s, op=dist.ReduceOp.SUM)
+    dist.all_reduce(m, op=dist.ReduceOp.MAX)
+    return s.tolist(), m.tolist()
+
+
 def cpu_oracle(b, n_sample, threads):
     import oracle
     rng = np.random.default_rng(7)
@@ -438,11 +451,10 @@ def main():
         ms = ev0.elapsed_time(ev1) / a.steps
         tim = xdrop.xd_get_timing(ctx)
         xdrop.xd_set_timing(ctx, False)
-        if dist:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        value = cells * world / (ms * 1e-3) / 1e9
+        # whole job: every rank's cells over the slowest rank's time (the ranks' batches are
+        # seeded differently, so their cell counts differ)
+        (job_cells, job_paper, job_pairs), (ms,) = job_totals(dist, dev, [cells, cells_paper, b.n_pairs], [ms])
+        value = job_cells / (ms * 1e-3) / 1e9
 
         # ---- roofline of the dominant alignment tier
         nb = max(1, tim["batches"])
@@ -507,13 +519,10 @@ def main():
                 if xdrop.xd_poll(ctx, t, hout, -1) != xdrop.XD_OK:
                     raise RuntimeError("e2e batch failed")
             e2e_s = (time.perf_counter() - t0) / a.steps
-            if dist:
-                tt = torch.tensor([e2e_s], device=dev)
-                dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-                e2e_s = float(tt.item())
+            _, (e2e_s,) = job_totals(dist, dev, [0], [e2e_s])
             assert np.array_equal(hout, res), "host and device entry points disagree"
             h2d = int(b.codes.nbytes + b.offsets.nbytes + b.lengths.nbytes + b.pairs.nbytes)
-            e2e = {"value": cells * world / e2e_s / 1e9, "unit": "GCUPS", "h2d_bytes_per_step": h2d,
+            e2e = {"value": job_cells / e2e_s / 1e9, "unit": "GCUPS", "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": int(hout.nbytes), "ms_per_step": e2e_s * 1e3,
                    "in_flight": 2}
 
@@ -535,8 +544,8 @@ def main():
                     "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                     "dtype": "int16" if packed_scores(b) else "int32", "data": "synthetic",
                     "config": workload_config(a, b),
-                    "pairs_per_s": b.n_pairs * world / (ms * 1e-3),
-                    "paper_gcups": cells_paper * world / (ms * 1e-3) / 1e9,
+                    "pairs_per_s": job_pairs / (ms * 1e-3),
+                    "paper_gcups": job_paper / (ms * 1e-3) / 1e9,
                     "cells_per_step": cells,
                     "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                     "gpu_launches": int(tim["launches"]),

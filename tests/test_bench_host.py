@@ -33,3 +33,65 @@ def test_packed_bound_protein(X, packed):
     b = _prot(X)
     assert int(np.max(b.matrix)) == 11   # BLOSUM62's largest entry sets s_max
     assert bench.packed_scores(b) is packed
+
+
+# ---- the replicated (N > 1) path of bench.py on CPU ranks (gloo, world size 2)
+
+def _job_worker(rank, world, port, q):
+    import os
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        # per-rank cells and pairs differ (each rank extends its own seeded batch)
+        sums, slowest = bench.job_totals(dist, "cpu", [1000.0 * (rank + 1), 7.0], [0.25 + rank])
+        q.put((rank, sums, slowest))
+    finally:
+        dist.destroy_process_group()
+
+
+def _free_port():
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def test_job_totals_two_ranks():
+    """Whole-job value = every rank's cells over the slowest rank's time, on every rank."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_job_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, sums, slowest in got:
+        assert sums == [3000.0, 14.0]
+        assert slowest == [1.25]
+
+
+def test_job_totals_single_process():
+    assert bench.job_totals(None, "cpu", [5, 2], [0.5]) == ([5.0, 2.0], [0.5])
+
+
+def test_reference_arm_ranks(monkeypatch, capsys):
+    """--impl reference under torchrun: rank 0 alone times the oracle and prints one line;
+    the other ranks exit without work."""
+    monkeypatch.setattr("sys.argv", ["bench.py", "--impl", "reference", "--workload", "dna_tiny",
+                                     "--pairs", "40", "--steps", "1", "--warmup", "1", "--cpu-pairs", "160"])
+    a = bench.parse()
+    assert bench.run_reference(a, 1, 2) is None
+    assert capsys.readouterr().out == ""
+    bench.run_reference(a, 0, 2)
+    lines = capsys.readouterr().out.strip().splitlines()
+    assert len(lines) == 1
+    import json
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
