@@ -42,8 +42,9 @@ SM_COUNT_GB300 = 152
 ALU_LANES_PER_SM = 64
 # DRAM bytes (read + write) of one launch of the dominant kernel, from one ncu capture of the
 # same workload and kernel build (profiles/k_fused_dna_longread_100k_x20.md); reported as
-# roofline.traffic only for that workload with the default configuration.
-DOMINANT_KERNEL_TRAFFIC = {"dna_longread_100000_x20": 261_023_232 + 16_260_864}
+# roofline.traffic only for that workload with the default configuration, and only while
+# the kernel is the build the counters were taken on (empty: the kernel has changed since).
+DOMINANT_KERNEL_TRAFFIC = {}
 
 
 def packed_scores(b):
