@@ -24,7 +24,7 @@ def _h(x):
     return x
 
 
-def packed_extend(H, V, sim, gap, X):
+def packed_extend(H, V, sim, gap, X, delta=0):
     m, n = len(H), len(V)
     smax = max(int(sim.max()), 0)
     th0, th1 = 2 * (smax - gap) + 1, 1022 - X - smax
@@ -32,19 +32,24 @@ def packed_extend(H, V, sim, gap, X):
     sp_max = int(sim.max()) - 2 * gap
     B0 = -X - gap - th0
     P2, P1 = {}, {0: _h(-32 * B0)}        # anti-diagonals d-2, d-1: cell i -> value (absent: -1)
-    T = best = bi = bj = 0
+    T = best = bi = bj = barg = flags = 0
     L = U = 0
     cells, rebases, d = 1, 0, 1
     while True:
         lo, hi = max(L, d - n, 0), min(U + 1, m, d)
+        if delta and hi - lo + 1 > delta:
+            # memory-restricted window (Sec. 3): delta cells centred on d-1's best cell
+            flags |= 1
+            lo = max(lo, min(barg - delta // 2, hi - delta + 1))
+            hi = lo + delta - 1
         zb = B0 + gap * d
         theta = T - X - zb
         if theta > th1:
-            delta = theta - th0
+            shift = theta - th0
             for row in (P1, P2):
                 for k in row:
-                    row[k] = max(_h(row[k] - _h(32 * delta)), -1)
-            B0, zb, theta, rebases = B0 + delta, zb + delta, theta - delta, rebases + 1
+                    row[k] = max(_h(row[k] - _h(32 * shift)), -1)
+            B0, zb, theta, rebases = B0 + shift, zb + shift, theta - shift, rebases + 1
         new, first, last, kmax = {}, None, None, -1
         for i in range(lo, hi + 1):
             j = d - i
@@ -70,12 +75,13 @@ def packed_extend(H, V, sim, gap, X):
         if wmax > T:
             T = best = wmax
             bi, bj = karg, d - karg
+        barg = karg
         L, U = first, last
         P2, P1 = P1, new
         if d == m + n:
             break
         d += 1
-    return {"score": best, "h_ext": bi, "v_ext": bj, "cells": cells}, rebases
+    return {"score": best, "h_ext": bi, "v_ext": bj, "flags": flags, "cells": cells}, rebases
 
 
 def _cases(rng, alphabet, n, max_len):
@@ -104,7 +110,7 @@ def test_packed_model_dna(match, mismatch, gap, X):
     for H, V in _cases(rng, "dna", 25, 160):
         got, rebases = packed_extend(H, V, sim, gap, X)
         want = oracle.extend(H, V, sim, gap, X, lib=lib)
-        for k in ("score", "h_ext", "v_ext", "cells"):
+        for k in ("score", "h_ext", "v_ext", "flags", "cells"):
             assert got[k] == want[k], (k, got, want)
         n_rebased += rebases > 0
     if X in (952, 322):
@@ -121,3 +127,18 @@ def test_packed_model_protein(X):
         want = oracle.extend(H, V, sim, -2, X, lib=lib)
         for k in ("score", "h_ext", "v_ext", "cells"):
             assert got[k] == want[k], (k, got, want)
+
+
+@pytest.mark.parametrize("delta", [1, 3, 8, 33])
+def test_packed_model_restricted(delta):
+    """The restricted window re-centres on the previous anti-diagonal's best cell, the one
+    the value + (31 - slot) keys select (lowest i on ties)."""
+    rng = np.random.default_rng(500 + delta)
+    sim = oracle.sim_table("dna", 1, -1)
+    lib = oracle.load()
+    for X in (5, 30):
+        for H, V in _cases(rng, "dna", 20, 150):
+            got, _ = packed_extend(H, V, sim, -1, X, delta)
+            want = oracle.extend(H, V, sim, -1, X, delta, lib=lib)
+            for k in ("score", "h_ext", "v_ext", "flags", "cells"):
+                assert got[k] == want[k], (k, got, want)
