@@ -788,7 +788,6 @@ __device__ __forceinline__ int group_step16(SideState& s, Res<CG, A>& res, uint3
 // queue that producers of the same launch may still append to: slots are reserved with an
 // atomic counter and published by storing the unit index over the kNoUnit sentinel.
 constexpr uint32_t kNoUnit = 0xffffffffu;
-constexpr uint32_t kMaxSpin = 1u << 24;
 constexpr uint64_t kWaitLimitNs = 10ull * 1000 * 1000 * 1000;   // default: 10 s without progress
 
 __device__ __forceinline__ uint64_t globaltimer_ns() {
