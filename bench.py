@@ -141,6 +141,17 @@ def cpu_oracle(b, n_sample, threads):
     return cells, dt, len(idx)
 
 
+def cpu_baseline(b, n_pairs, threads):
+    """The oracle timed on the host: on every core (one pair range per thread) over n_pairs
+    seeded pairs of the workload, and on one core over a twentieth of them."""
+    c, dt, n = cpu_oracle(b, n_pairs, threads)
+    c1, dt1, n1 = cpu_oracle(b, max(1, n_pairs // 20), 1)
+    return {"value": c / dt / 1e9, "unit": "GCUPS", "cores": threads, "kind": "oracle",
+            "sample": f"{n} seeded-random pairs of the same workload ({c:.3g} cells, {dt:.1f} s)",
+            "value_1_core": c1 / dt1 / 1e9,
+            "sample_1_core": f"{n1} seeded-random pairs ({c1:.3g} cells, {dt1:.1f} s)"}
+
+
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
@@ -534,10 +545,7 @@ def main():
 
         cpu = None
         if rank == 0 and not a.no_cpu:
-            threads = os.cpu_count() or 1
-            c, dt, n = cpu_oracle(b, a.cpu_pairs, threads)
-            cpu = {"value": c / dt / 1e9, "unit": "GCUPS", "cores": threads, "kind": "oracle",
-                   "sample": f"{n} seeded-random pairs of the same workload ({c:.3g} cells, {dt:.1f} s)"}
+            cpu = cpu_baseline(b, a.cpu_pairs, os.cpu_count() or 1)
 
         if rank == 0:
             line = {"metric": "GCUPS", "value": value, "unit": "GCUPS", "n_gpus": world,

@@ -95,3 +95,12 @@ def test_reference_arm_ranks(monkeypatch, capsys):
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_cpu_baseline_fields():
+    """The bench's CPU baseline: the oracle on every core and on one core (host only)."""
+    b = synth.dna_tiny(n_pairs=40)
+    d = bench.cpu_baseline(b, 40, 2)
+    assert d["kind"] == "oracle" and d["cores"] == 2 and d["unit"] == "GCUPS"
+    assert d["value"] > 0 and d["value_1_core"] > 0
+    assert d["sample"].startswith("40 ") and d["sample_1_core"].startswith("2 ")
