@@ -16,7 +16,11 @@ Parity status of each function (what pins it, all in ``tests/test_oracle_pins.py
                    unrestricted without overflow; hand-derived traces in tests/golden.
                    The end-cell tie-break and the band rule are fixed readings (R3, R4);
                    between alternative readings they are pinned only by the hand traces.
-  * orc_batch   -- pinned through orc_extend plus the seed-score closed form.
+  * orc_batch   -- pinned through orc_extend plus the seed-score closed form: for DNA
+                   (pin_pair_total, pin_left_is_right_on_reversed) and for protein
+                   (pin_protein_batch: each side against orc_extend with a BLOSUM62 table
+                   the test builds from the published entries, and the total against the
+                   seed's BLOSUM62 sum computed in the test).
 """
 import ctypes
 import os

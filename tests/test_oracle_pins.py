@@ -229,6 +229,43 @@ def pin_pair_total(lib, seed=19):
         assert tuple(R[p]) == ext(lib, hr, vr, DNA_SIM, -1, 4)
 
 
+PROT_LETTERS = "ARNDCQEGHILKMFPSTWYV"
+
+
+def pin_protein_batch(lib, seed=31):
+    """orc_batch on protein tuples (Sec. 2.2 scoring with a substitution matrix; Sec. 5.3:
+    BLOSUM62, gap -2).  Each side must equal orc_extend on side strings cut out here, scored
+    with a table built here from the published BLOSUM62 entries, and the pair total must add
+    the seed's BLOSUM62 sum computed here; the seeds are random residues, so negative
+    entries of the matrix take part."""
+    rng = np.random.default_rng(seed)
+    blosum = [[int(x) for x in row] for row in synth.BLOSUM62]
+    table = np.array(blosum, dtype=np.int32)
+    lut = {c: i for i, c in enumerate(PROT_LETTERS)}
+    rows = []
+    for t in range(50):
+        m, n, k = int(rng.integers(0, 50)), int(rng.integers(0, 50)), int(rng.integers(1, 8))
+        h = "".join(rng.choice(list(PROT_LETTERS), m + k))
+        v = "".join(rng.choice(list(PROT_LETTERS), n + k))
+        if t % 2 == 0 and min(m, n) > 0:
+            # a related pair: V copies H around the seed with a few substitutions
+            v = list(h[:n + k] + "".join(rng.choice(list(PROT_LETTERS), max(0, n + k - len(h)))))
+            for q in rng.integers(0, len(v), len(v) // 5):
+                v[q] = PROT_LETTERS[int(rng.integers(0, 20))]
+            v = "".join(v)
+        hs, vs = int(rng.integers(0, m + 1)), int(rng.integers(0, n + 1))
+        rows.append((h, v, hs, vs, k))
+    codes = lambda s: np.array([lut[c] for c in s], dtype=np.uint8)  # noqa: E731
+    for X in (5, 49):
+        b = synth.from_strings(rows, alphabet="protein", gap=-2, X=X)
+        L, R, T = oracle.run_batch(b, lib=lib)
+        for p, (h, v, hs, vs, k) in enumerate(rows):
+            seed_score = sum(blosum[lut[h[hs + t]]][lut[v[vs + t]]] for t in range(k))
+            assert T[p] == L[p]["score"] + R[p]["score"] + seed_score, (p, X)
+            assert tuple(L[p]) == ext(lib, codes(h[:hs][::-1]), codes(v[:vs][::-1]), table, -2, X), (p, X)
+            assert tuple(R[p]) == ext(lib, codes(h[hs + k:]), codes(v[vs + k:]), table, -2, X), (p, X)
+
+
 def pin_dense_restatement(lib, trials=400, seed=23):
     rng = np.random.default_rng(seed)
     for t in range(trials):
@@ -263,7 +300,7 @@ def pin_restricted_without_overflow(lib, trials=120, seed=29):
 
 PINS = [pin_hand_traces, pin_x_infinite_is_full_dp, pin_identical_sequences, pin_closed_forms,
         pin_swap_symmetry, pin_integer_scaling, pin_left_is_right_on_reversed, pin_pair_total,
-        pin_dense_restatement, pin_restricted_without_overflow]
+        pin_protein_batch, pin_dense_restatement, pin_restricted_without_overflow]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=lambda f: f.__name__)
@@ -307,6 +344,9 @@ MUTANTS = {
     "seed_not_scored": ("+ (int64_t)right[p].score + seed_score;", "+ (int64_t)right[p].score;"),
     "no_origin_cell": ("uint64_t cells = 1;", "uint64_t cells = 0;"),
     "centre_on_hi": ("int64_t centred = b - (int64_t)(delta / 2);", "int64_t centred = b;"),
+    "matrix_sign_dropped": ("(int32_t)matrix[a * 20 + b]", "(int32_t)(uint8_t)matrix[a * 20 + b]"),
+    "protein_scored_as_dna": ("alpha == 20 ? (int32_t)matrix[a * 20 + b] : (a == b ? match : mismatch)",
+                              "(a == b ? match : mismatch)"),
 }
 
 
