@@ -133,9 +133,11 @@ typedef struct {
     uint64_t graph_replays;      /* device-entry batches run by replaying a graph */
 } xd_stats;
 
-/* Create a context on cfg->device (NULL cfg = defaults).  Allocates nothing large until
- * the first batch.  Errors: XD_EINVAL (out == NULL), XD_EDEVICE (no such device or the
- * device is not compute capability 10.3). */
+/* Create a context on cfg->device (NULL cfg = defaults).  A context plays the part of the
+ * paper's wrapping driver class (Sec. 4.4, Multi-IPU Support): it owns the device, the
+ * work queue that submitted batches share, and the streams that overlap transfers with
+ * computation.  Allocates nothing large until the first batch.  Errors: XD_EINVAL
+ * (out == NULL), XD_EDEVICE (no such device or the device is not compute capability 10.3). */
 xd_status xd_create(const xd_config* cfg, xd_ctx** out);
 
 /* Validate and enqueue a host batch (Sec. 4.4 tuples; Sec. 3 method).  Copies every input
@@ -182,7 +184,9 @@ typedef struct {
  * with host batches.  Errors as xd_submit_batch; XD_EINVAL also for unknown handles. */
 xd_status xd_submit_pairs(xd_ctx* ctx, const xd_pairs_batch* batch, uint64_t* ticket);
 
-/* Wait up to wait_ms milliseconds (0 = do not wait, < 0 = wait without limit) for the
+/* Completion side of the driver's shared work queue (Sec. 4.4: batches are submitted to a
+ * queue and their results collected once the device has run them).
+ * Wait up to wait_ms milliseconds (0 = do not wait, < 0 = wait without limit) for the
  * batch of `ticket`; on XD_OK copies n_pairs results to the host array `out` and retires
  * the ticket.  Returns XD_PENDING if not finished and wait_ms == 0, XD_ETIMEDOUT if the
  * wait expired, XD_ENOTFOUND for an unknown ticket, XD_EDEVICE if the launch that ran the
@@ -261,6 +265,24 @@ xd_status xd_get_timing(xd_ctx* ctx, xd_timing* out);
  * runs for a few tens of milliseconds.  Errors: XD_EINVAL (unknown op), XD_EDEVICE. */
 xd_status xd_probe(xd_ctx* ctx, int32_t op, double* rate);
 
+/* Autotuner of the batching scheme (Sec. 4.2 Batching: per-batch cost estimation and
+ * distribution of the comparisons over the compute units; here the choice of launch
+ * configuration for a class of batches).  Runs the host batch `sample` (pointers as for
+ * xd_submit_batch) under candidate configurations -- the register-level chain (lanes per
+ * side extension and window of every level, i.e. threads per alignment and band tile
+ * width), the queue chunk of single-lane levels (1 - 64), the long-side head of the
+ * persistent grid and its role mix -- three runs each on a stream of its own, and keeps the
+ * fastest for the sample's bucket: alphabet x X (<= 15, <= 30, more) x longest side
+ * (<= 2,048, <= 20,000, more) x size (< 8,192, < 65,536, more side extensions).  Every
+ * candidate must reproduce the first candidate's results bit for bit, else the call fails
+ * with XD_EDEVICE and keeps nothing.  The winner applies to later batches of the context;
+ * if path is not NULL or empty it is also merged into the text table at path (created if
+ * missing), which xd_config.tune_table loads.  *best_ms (may be NULL) receives the winner's
+ * pipeline time in milliseconds.  Synchronous; allocates and frees its own device buffers.
+ * Errors: XD_EINVAL (invalid or empty sample, unreadable or unwritable table), XD_ENOMEM,
+ * XD_EDEVICE. */
+xd_status xd_autotune(xd_ctx* ctx, const xd_batch* sample, const char* path, float* best_ms);
+
 /* Allocation-free variant of xd_run_device (the paper has no counterpart: this exists for
  * callers that cannot allocate device memory, such as code running in a host callback, a
  * pipeline whose device memory is fixed up front, or a process whose memory is managed by
@@ -283,12 +305,15 @@ xd_status xd_probe(xd_ctx* ctx, int32_t op, double* rate);
 xd_status xd_run_device_noalloc(const xd_batch* dev_batch, uint32_t max_side_len, xd_result* d_out,
                                 void* stream);
 
-/* Stop the dispatcher, wait (at most 60 s) for launches in flight, fail batches that never
- * launched, then free every resource of the context.  XD_ETIMEDOUT if the wait expired. */
+/* Tear down the driver of Sec. 4.4: stop the dispatcher, wait (at most 60 s) for launches in
+ * flight, fail batches that never launched, then free every resource of the context.
+ * XD_ETIMEDOUT if the wait expired; the context is freed either way and must not be used
+ * again.  XD_EINVAL for ctx == NULL. */
 xd_status xd_destroy(xd_ctx* ctx);
 
-/* Last error message of the context (never NULL; "" when none).  ctx may be NULL for
- * errors of xd_create. */
+/* Last error message of the context (never NULL; "" when none), the host-side error report
+ * of the Sec. 4.4 driver.  The string belongs to the library and stays valid until the
+ * next call on the same context.  ctx may be NULL for errors of xd_create. */
 const char* xd_last_error(const xd_ctx* ctx);
 
 /* Library version string. */
