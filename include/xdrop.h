@@ -211,8 +211,10 @@ xd_status xd_reserve(xd_ctx* ctx, uint64_t n_codes, uint32_t n_seqs, uint32_t n_
                      uint32_t max_seq_len);
 
 /* Synchronise the context's device work and report the device-side validation word of
- * the last xd_run_device batch: 0 = valid; bit 0 code outside the alphabet, bit 1 seed
- * outside its sequence, bit 2 score range exceeded, bit 3 a bounded device wait gave up. */
+ * the last xd_run_device batch: 0 = valid; bit 0 code outside the alphabet, bit 1 a bad
+ * tuple (sequence id outside the table, seed outside its sequence, or a sequence whose
+ * offset + length passes n_codes; such pairs get empty sides and no seed score), bit 2
+ * score range exceeded, bit 3 a bounded device wait gave up. */
 xd_status xd_device_status(xd_ctx* ctx, uint32_t* flags);
 
 xd_status xd_get_stats(const xd_ctx* ctx, xd_stats* out);
@@ -297,9 +299,10 @@ xd_status xd_autotune(xd_ctx* ctx, const xd_batch* sample, const char* path, flo
  *   not fit the 64 MiB array.  Pairs with invalid inputs (bad ids, seeds outside their
  *   sequence, codes outside the alphabet, a side longer than max_side_len) get flags bit 31
  *   set on both sides instead of a result.
- * The first call on a device looks up the array's device address with that device current
- * (uses the calling thread's current device); make that first call before any stream
- * capture.  The array is shared by all calls: calls that overlap on the GPU (for instance
+ * The first call in each CUDA context looks up the array's device address with that context
+ * current (the calling thread's current context, or the current device's primary context
+ * when none is current); make that first call before any stream capture.  A context made
+ * later (for instance after cudaDeviceReset) gets its own look-up on its first call.  The array is shared by all calls: calls that overlap on the GPU (for instance
  * on two streams at once) race and give wrong results.  Asynchronous on `stream`.
  * Errors: XD_EINVAL, XD_EDEVICE. */
 xd_status xd_run_device_noalloc(const xd_batch* dev_batch, uint32_t max_side_len, xd_result* d_out,

@@ -589,7 +589,8 @@ xd_status run_pipeline(xd_ctx* c, Scratch& s, const BatchView& b, xd_result* d_o
     P.X = b.X;
     P.delta = b.delta;
     std::memcpy(P.sim, b.sim, sizeof(P.sim));
-    XD_CUDA(c, launch_units(b.pairs, b.n_pairs, b.offsets, b.lengths, b.n_seqs, b.max_abs, b.max_len,
+    const uint64_t n_res = b.packed ? b.packed_words * uint64_t(b.alpha == 4 ? 16 : 6) : b.n_codes;
+    XD_CUDA(c, launch_units(b.pairs, b.n_pairs, b.offsets, b.lengths, b.n_seqs, n_res, b.max_abs, b.max_len,
                             static_cast<Unit*>(s.units.p), static_cast<uint32_t*>(s.bucket.p),
                             static_cast<uint32_t*>(s.hist.p), err, st));
     XD_CUDA(c, mark(2));
@@ -640,7 +641,7 @@ xd_status run_pipeline(xd_ctx* c, Scratch& s, const BatchView& b, xd_result* d_o
         XD_CUDA(c, launch_generic(P, Q, static_cast<int32_t*>(s.generic.p), plan.generic_stride,
                                   plan.generic_blocks, st));
         XD_CUDA(c, mark(6));
-        XD_CUDA(c, launch_totals(b.pairs, b.n_pairs, b.offsets, b.lengths, b.n_seqs, P, st));
+        XD_CUDA(c, launch_totals(b.pairs, b.n_pairs, b.offsets, b.lengths, b.n_seqs, n_res, P, st));
         launches += 2;
     } else {
         XD_CUDA(c, mark(4));

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include "xd_device.cuh"
 #include "xd_launch.h"
+#include "xd_sweep.cuh"
 
 namespace xd {
 
@@ -68,6 +69,7 @@ __global__ void k_pack_prot(const uint8_t* __restrict__ codes, uint64_t n_codes,
 // about 2 min(m, n) when the alignment runs to the end of the shorter sequence.  Buckets are
 // quarter octaves of min(m, n) + 1.  Invalid tuples raise kErrSeed and become empty units;
 // sides whose scores could leave the exact range raise kErrRange and also become empty.
+// n_res: residues in the store; a sequence whose offset + length passes it is invalid.
 __device__ __forceinline__ uint32_t cost_bucket(uint32_t m, uint32_t n) {
     const uint32_t s = min(m, n) + 1u;
     const uint32_t lg = 31u - uint32_t(__clz(s));               // floor(log2 s)
@@ -77,7 +79,7 @@ __device__ __forceinline__ uint32_t cost_bucket(uint32_t m, uint32_t n) {
 
 __global__ void k_units(const xd_pair* __restrict__ pairs, uint32_t n_pairs,
                         const uint64_t* __restrict__ offsets, const uint32_t* __restrict__ lengths,
-                        uint32_t n_seqs, int32_t max_abs, uint32_t max_len,
+                        uint32_t n_seqs, uint64_t n_res, int32_t max_abs, uint32_t max_len,
                         Unit* __restrict__ units, uint32_t* __restrict__ bucket_of,
                         uint32_t* __restrict__ hist, uint32_t* err) {
     __shared__ uint32_t sh[64];
@@ -94,7 +96,9 @@ __global__ void k_units(const xd_pair* __restrict__ pairs, uint32_t n_pairs,
         } else {
             ho = offsets[e.h_id]; vo = offsets[e.v_id];
             lh = lengths[e.h_id]; lv = lengths[e.v_id];
-            if (uint64_t(e.h_seed) + e.seed_len > lh || uint64_t(e.v_seed) + e.seed_len > lv)
+            // a seed outside its sequence, or a sequence past the end of the residues
+            if (uint64_t(e.h_seed) + e.seed_len > lh || uint64_t(e.v_seed) + e.seed_len > lv ||
+                ho + lh > n_res || vo + lv > n_res)
                 bad = kErrSeed;
         }
         Unit r{}, l{};
@@ -158,72 +162,17 @@ __device__ __forceinline__ int32_t sim_of(const int32_t* sim, int alpha, uint32_
 
 __device__ void extend_generic(const Problem& P, const Unit& u, int32_t* A, int32_t* B,
                                int32_t* Cc, const int32_t* sim, int lane) {
-    const int64_t m = u.m, n = u.n;
-    const int64_t hdir = u.side ? -1 : 1;
-    const int64_t vdir = hdir;
-    int32_t* P1 = A; int32_t* P2 = B; int32_t* C = Cc;
-    int64_t p1lo = 0, p1hi = 0, p2lo = 1, p2hi = 0;
-    if (lane == 0) P1[0] = 0;
-    __syncwarp();
-    int32_t T = 0, best = 0;
-    int64_t bi_best = 0, bj_best = 0;
-    int64_t L = 0, U = 0, prev_arg = 0;
-    uint64_t cells = 1;
-    uint32_t flags = 0;
-    const int32_t g = P.gap;
-    for (int64_t d = 1; d <= m + n; d++) {
-        int64_t lo = L, hi = U + 1;
-        if (d - n > lo) lo = d - n;
-        if (lo < 0) lo = 0;
-        if (hi > m) hi = m;
-        if (hi > d) hi = d;
-        if (P.delta && hi - lo + 1 > int64_t(P.delta)) {
-            flags = 1;
-            int64_t start = prev_arg - int64_t(P.delta / 2);
-            int64_t latest = hi - int64_t(P.delta) + 1;
-            if (latest < start) start = latest;
-            if (start > lo) lo = start;
-            hi = lo + int64_t(P.delta) - 1;
-        }
-        const int32_t thr = max(T - P.X, kDeadLine);
-        int32_t first = INT32_MAX, last = -1, bmax = kNeg, barg = INT32_MAX;
-        for (int64_t i = lo + lane; i <= hi; i += 32) {
-            const int64_t j = d - i;
-            int32_t c = kNeg;
-            if (i >= 1 && j >= 1 && i - 1 >= p2lo && i - 1 <= p2hi) {
-                uint32_t a = residue(P.store, P.alpha, u.h0 + hdir * (i - 1));
-                uint32_t b = residue(P.store, P.alpha, u.v0 + vdir * (j - 1));
-                c = P2[i - 1] + sim_of(sim, P.alpha, a, b);
-            }
-            if (i >= 1 && i - 1 >= p1lo && i - 1 <= p1hi) c = max(c, P1[i - 1] + g);
-            if (j >= 1 && i >= p1lo && i <= p1hi) c = max(c, P1[i] + g);
-            if (c < thr) c = kNeg;
-            C[i] = c;
-            if (c != kNeg) {
-                if (first == INT32_MAX) first = int32_t(i);
-                last = int32_t(i);
-                if (c > bmax) { bmax = c; barg = int32_t(i); }
-            }
-        }
-        cells += uint64_t(hi - lo + 1);
-        first = __reduce_min_sync(0xffffffffu, first);
-        last = __reduce_max_sync(0xffffffffu, last);
-        const int32_t wmax = __reduce_max_sync(0xffffffffu, bmax);
-        barg = __reduce_min_sync(0xffffffffu, bmax == wmax ? barg : INT32_MAX);
-        __syncwarp();
-        if (first == INT32_MAX) break;
-        if (wmax > T) { T = wmax; best = wmax; bi_best = barg; bj_best = d - barg; }
-        prev_arg = barg;
-        L = first; U = last;
-        int32_t* old = P2;
-        P2 = P1; p2lo = p1lo; p2hi = p1hi;
-        P1 = C; p1lo = lo; p1hi = hi;
-        C = old;
-    }
+    const int64_t dir = u.side ? -1 : 1;
+    auto sim_at = [&](int64_t i, int64_t j) {
+        const uint32_t a = residue(P.store, P.alpha, u.h0 + dir * (i - 1));
+        const uint32_t b = residue(P.store, P.alpha, u.v0 + dir * (j - 1));
+        return sim_of(sim, P.alpha, a, b);
+    };
+    const SweepOut o = generic_sweep(int64_t(u.m), int64_t(u.n), P.gap, P.X, P.delta, sim_at, A, B, Cc, lane);
     if (lane == 0) {
-        write_side(P.results, u.pair, u.side, best, uint32_t(bi_best), uint32_t(bj_best), flags, cells);
+        write_side(P.results, u.pair, u.side, o.best, uint32_t(o.bi), uint32_t(o.bj), o.flags, o.cells);
         atomicAdd(&P.stats[2], 1ull);
-        atomicAdd(&P.stats[6], (unsigned long long)cells);
+        atomicAdd(&P.stats[6], (unsigned long long)o.cells);
     }
     __syncwarp();
 }
@@ -502,7 +451,7 @@ __global__ void k_route_all_generic(Queues Q) {
 // a9: pair totals = left + right + sum of Sim over the seed.
 __global__ void k_totals(const xd_pair* __restrict__ pairs, uint32_t n_pairs,
                          const uint64_t* __restrict__ offsets, const uint32_t* __restrict__ lengths,
-                         uint32_t n_seqs, Problem P) {
+                         uint32_t n_seqs, uint64_t n_res, Problem P) {
     __shared__ int32_t sim[400];
     for (int t = threadIdx.x; t < P.alpha * P.alpha; t += blockDim.x) sim[t] = P.sim[t];
     __syncthreads();
@@ -512,8 +461,11 @@ __global__ void k_totals(const xd_pair* __restrict__ pairs, uint32_t n_pairs,
     int64_t seed = 0;
     if (e.h_id < n_seqs && e.v_id < n_seqs) {
         uint64_t ho = offsets[e.h_id] + e.h_seed, vo = offsets[e.v_id] + e.v_seed;
+        // only tuples that k_units accepted: the seed inside its sequence, the sequence
+        // inside the store
         if (uint64_t(e.h_seed) + e.seed_len <= lengths[e.h_id] &&
-            uint64_t(e.v_seed) + e.seed_len <= lengths[e.v_id])
+            uint64_t(e.v_seed) + e.seed_len <= lengths[e.v_id] &&
+            offsets[e.h_id] + lengths[e.h_id] <= n_res && offsets[e.v_id] + lengths[e.v_id] <= n_res)
             for (uint32_t t = 0; t < e.seed_len; t++)
                 seed += sim[residue(P.store, P.alpha, ho + t) * P.alpha + residue(P.store, P.alpha, vo + t)];
     }
@@ -549,11 +501,11 @@ cudaError_t launch_pack(int alpha, const uint8_t* codes, uint64_t n_codes, uint3
 }
 
 cudaError_t launch_units(const xd_pair* pairs, uint32_t n_pairs, const uint64_t* offsets,
-                         const uint32_t* lengths, uint32_t n_seqs, int32_t max_abs,
+                         const uint32_t* lengths, uint32_t n_seqs, uint64_t n_res, int32_t max_abs,
                          uint32_t max_len, Unit* units, uint32_t* bucket_of, uint32_t* hist,
                          uint32_t* err, cudaStream_t st) {
     if (n_pairs == 0) return cudaSuccess;
-    k_units<<<(n_pairs + 255) / 256, 256, 0, st>>>(pairs, n_pairs, offsets, lengths, n_seqs,
+    k_units<<<(n_pairs + 255) / 256, 256, 0, st>>>(pairs, n_pairs, offsets, lengths, n_seqs, n_res,
                                                    max_abs, max_len, units, bucket_of, hist, err);
     return cudaGetLastError();
 }
@@ -591,10 +543,10 @@ cudaError_t launch_band(const Problem& P, const Queues& Q, int n_sm, cudaStream_
 }
 
 cudaError_t launch_totals(const xd_pair* pairs, uint32_t n_pairs, const uint64_t* offsets,
-                          const uint32_t* lengths, uint32_t n_seqs, const Problem& P,
+                          const uint32_t* lengths, uint32_t n_seqs, uint64_t n_res, const Problem& P,
                           cudaStream_t st) {
     if (n_pairs == 0) return cudaSuccess;
-    k_totals<<<(n_pairs + 255) / 256, 256, 0, st>>>(pairs, n_pairs, offsets, lengths, n_seqs, P);
+    k_totals<<<(n_pairs + 255) / 256, 256, 0, st>>>(pairs, n_pairs, offsets, lengths, n_seqs, n_res, P);
     return cudaGetLastError();
 }
 

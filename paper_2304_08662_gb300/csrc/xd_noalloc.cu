@@ -17,13 +17,14 @@
 
 #include <cuda_runtime.h>
 
+#include <cuda.h>   // driver API types only; its functions are reached through the runtime
+
 #include "xdrop.h"
+#include "xd_sweep.cuh"
 
 namespace {
 
-constexpr int32_t kNegN = -(1 << 30);
-constexpr int32_t kDeadLineN = -(1 << 29);
-constexpr int64_t kScoreLimitN = int64_t(1) << 29;
+constexpr int64_t kScoreLimitN = xd::kScoreLimit;
 constexpr int kWarpsPerBlock = 4;
 constexpr int kMaxWarps = 4096;
 constexpr uint32_t kFlagInvalid = 0x80000000u;   // result flag: the pair's inputs were invalid
@@ -60,91 +61,24 @@ __device__ __forceinline__ uint32_t code_at(const Args& a, uint64_t pos, bool& b
     return c;
 }
 
-// One side: H_side[t] = codes[h0 + dir t], V_side[t] = codes[v0 + dir t].  Same sweep as the
-// generic tier: band from the previous anti-diagonal, optional delta_b window, recurrence,
-// X-Drop against T of completed anti-diagonals, warp reductions of live range and best cell.
+// One side: H_side[t] = codes[h0 + dir t], V_side[t] = codes[v0 + dir t], swept exactly as
+// the generic tier sweeps it (generic_sweep); codes outside the alphabet set `bad`.
 __device__ void side_noalloc(const Args& a, const int32_t* sim, int64_t h0, int64_t v0, int64_t dir,
                              int64_t m, int64_t n, int32_t* A, int32_t* B, int32_t* Cc, int lane,
                              xd_side& res, bool& bad) {
-    int32_t* P1 = A;
-    int32_t* P2 = B;
-    int32_t* C = Cc;
-    int64_t p1lo = 0, p1hi = 0, p2lo = 1, p2hi = 0;
-    if (lane == 0) P1[0] = 0;
-    __syncwarp();
-    int32_t T = 0, best = 0;
-    int64_t bi = 0, bj = 0, L = 0, U = 0, prev_arg = 0;
-    uint64_t cells = 1;
-    uint32_t flags = 0;
     bool lane_bad = false;
-    for (int64_t d = 1; d <= m + n; d++) {
-        int64_t lo = L, hi = U + 1;
-        if (d - n > lo) lo = d - n;
-        if (lo < 0) lo = 0;
-        if (hi > m) hi = m;
-        if (hi > d) hi = d;
-        if (a.delta && hi - lo + 1 > int64_t(a.delta)) {
-            flags = 1;
-            int64_t start = prev_arg - int64_t(a.delta / 2);
-            const int64_t latest = hi - int64_t(a.delta) + 1;
-            if (latest < start) start = latest;
-            if (start > lo) lo = start;
-            hi = lo + int64_t(a.delta) - 1;
-        }
-        const int32_t thr = max(T - a.X, kDeadLineN);
-        int32_t first = INT32_MAX, last = -1, bmax = kNegN, barg = INT32_MAX;
-        for (int64_t i = lo + lane; i <= hi; i += 32) {
-            const int64_t j = d - i;
-            int32_t c = kNegN;
-            if (i >= 1 && j >= 1 && i - 1 >= p2lo && i - 1 <= p2hi) {
-                const uint32_t x = code_at(a, uint64_t(h0 + dir * (i - 1)), lane_bad);
-                const uint32_t y = code_at(a, uint64_t(v0 + dir * (j - 1)), lane_bad);
-                c = P2[i - 1] + sim[x * a.alpha + y];
-            }
-            if (i >= 1 && i - 1 >= p1lo && i - 1 <= p1hi) c = max(c, P1[i - 1] + a.gap);
-            if (j >= 1 && i >= p1lo && i <= p1hi) c = max(c, P1[i] + a.gap);
-            if (c < thr) c = kNegN;
-            C[i] = c;
-            if (c != kNegN) {
-                if (first == INT32_MAX) first = int32_t(i);
-                last = int32_t(i);
-                if (c > bmax) {
-                    bmax = c;
-                    barg = int32_t(i);
-                }
-            }
-        }
-        cells += uint64_t(hi - lo + 1);
-        first = __reduce_min_sync(0xffffffffu, first);
-        last = __reduce_max_sync(0xffffffffu, last);
-        const int32_t wmax = __reduce_max_sync(0xffffffffu, bmax);
-        barg = __reduce_min_sync(0xffffffffu, bmax == wmax ? barg : INT32_MAX);
-        __syncwarp();
-        if (first == INT32_MAX) break;
-        if (wmax > T) {
-            T = wmax;
-            best = wmax;
-            bi = barg;
-            bj = d - barg;
-        }
-        prev_arg = barg;
-        L = first;
-        U = last;
-        int32_t* old = P2;
-        P2 = P1;
-        p2lo = p1lo;
-        p2hi = p1hi;
-        P1 = C;
-        p1lo = lo;
-        p1hi = hi;
-        C = old;
-    }
+    auto sim_at = [&](int64_t i, int64_t j) {
+        const uint32_t x = code_at(a, uint64_t(h0 + dir * (i - 1)), lane_bad);
+        const uint32_t y = code_at(a, uint64_t(v0 + dir * (j - 1)), lane_bad);
+        return sim[x * a.alpha + y];
+    };
+    const xd::SweepOut o = xd::generic_sweep(m, n, a.gap, a.X, a.delta, sim_at, A, B, Cc, lane);
     bad |= __any_sync(0xffffffffu, lane_bad);
-    res.score = best;
-    res.h_ext = uint32_t(bi);
-    res.v_ext = uint32_t(bj);
-    res.flags = flags;
-    res.cells = cells;
+    res.score = o.best;
+    res.h_ext = uint32_t(o.bi);
+    res.v_ext = uint32_t(o.bj);
+    res.flags = o.flags;
+    res.cells = o.cells;
 }
 
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_noalloc(Args a, int32_t* scratch, uint64_t stride) {
@@ -204,10 +138,49 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_noalloc(Args a, int32_t
     }
 }
 
-// Device address of the scratch array, resolved once per device with that device current.
-constexpr int kMaxDevices = 64;
+// Device address of the scratch array, resolved once per CUDA context with that context
+// current.  The cache is keyed by the context's unique id (cuCtxGetId, never reused within
+// a process), not by the device number: a context made after cudaDeviceReset, or a second
+// context on the same device made through the driver API, loads its own copy of the module
+// and so has its own address.
+constexpr int kCacheSlots = 64;
+struct CacheSlot {
+    unsigned long long ctx_id;
+    int32_t* ptr;
+};
 std::mutex g_mu;
-int32_t* g_scratch_ptr[kMaxDevices] = {};
+CacheSlot g_cache[kCacheSlots] = {};
+int g_cache_next = 0;
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+// Id of the calling thread's current context; false if it cannot be had.  With no context
+// current yet, the runtime call that resolves the symbol makes the device's primary context
+// current first.
+bool current_context_id(unsigned long long& id) {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    if (!get_current || !get_id) {
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1{}, q2{};
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+            return false;
+        get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+        get_id = reinterpret_cast<CtxGetIdFn>(f2);
+    }
+    CUcontext cur = nullptr;
+    if (get_current(&cur) != CUDA_SUCCESS) return false;
+    if (!cur) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return false;
+        if (get_current(&cur) != CUDA_SUCCESS || !cur) return false;
+    }
+    return get_id(cur, &id) == CUDA_SUCCESS;
+}
 
 }  // namespace
 
@@ -223,17 +196,20 @@ extern "C" xd_status xd_run_device_noalloc(const xd_batch* b, uint32_t max_side_
     const uint64_t per_warp = 3 * stride * sizeof(int32_t);
     if (per_warp > kScratchBytes) return XD_EINVAL;   // a single side does not fit the scratch
     if (b->n_pairs == 0) return XD_OK;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return XD_EDEVICE;
     int32_t* scratch = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_scratch_ptr[dev]) {
+        unsigned long long id = 0;
+        if (!current_context_id(id)) return XD_EDEVICE;
+        for (const CacheSlot& cs : g_cache)
+            if (cs.ptr && cs.ctx_id == id) scratch = cs.ptr;
+        if (!scratch) {
             void* p = nullptr;
             if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return XD_EDEVICE;
-            g_scratch_ptr[dev] = static_cast<int32_t*>(p);
+            scratch = static_cast<int32_t*>(p);
+            g_cache[g_cache_next] = CacheSlot{id, scratch};
+            g_cache_next = (g_cache_next + 1) % kCacheSlots;
         }
-        scratch = g_scratch_ptr[dev];
     }
     Args a{};
     a.codes = b->seq_codes;

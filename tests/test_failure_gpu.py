@@ -63,3 +63,31 @@ def test_wait_that_runs_out_is_reported_and_context_survives():
         assert np.array_equal(out["left"]["cells"][idx], L["cells"])
     finally:
         xdrop.xd_destroy(good)
+
+
+def test_device_entry_flags_a_sequence_past_the_codes():
+    """xd_run_device validates on the device: a sequence whose offset + length passes
+    n_codes is reported in the validation word (bit 1) instead of being read clamped."""
+    b = synth.dna_tiny(n_pairs=8)
+    dev = torch.device("cuda", 0)
+    offs = b.offsets.copy()
+    offs[3] = np.uint64(b.codes.size - 5)        # sequence 3 now runs past the end
+    codes = torch.from_numpy(b.codes).to(dev)
+    lens = torch.from_numpy(b.lengths.view(np.int32)).to(dev)
+    pairs = torch.from_numpy(np.ascontiguousarray(b.pairs).view(np.int32)).to(dev)
+    args = xdrop.BatchArgs(b.alphabet, codes, torch.from_numpy(offs.view(np.int64)).to(dev), lens, pairs,
+                           b.match, b.mismatch, b.gap, b.matrix, b.X, b.delta)
+    out = torch.zeros(b.n_pairs * xdrop.RESULT_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    ctx = xdrop.xd_create(0)
+    try:
+        xdrop.xd_run_device(ctx, args, out, None)
+        torch.cuda.synchronize()
+        assert xdrop.xd_device_status(ctx) & 2
+        # the same context then runs a valid batch cleanly
+        good = xdrop.BatchArgs(b.alphabet, codes, torch.from_numpy(b.offsets.view(np.int64)).to(dev),
+                               lens, pairs, b.match, b.mismatch, b.gap, b.matrix, b.X, b.delta)
+        xdrop.xd_run_device(ctx, good, out, None)
+        torch.cuda.synchronize()
+        assert xdrop.xd_device_status(ctx) == 0
+    finally:
+        xdrop.xd_destroy(ctx)

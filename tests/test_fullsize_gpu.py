@@ -1,11 +1,13 @@
-"""Full-size parity for the protein and uneven/restricted workloads, through xd_run_device
-in the launch configuration the bench times.
+"""Full-size parity of every workload, through xd_run_device in the launch configuration
+the bench times: every pair of every batch against the oracle (run on all host cores),
+all five result fields and the total, bit for bit.
 
-At these sizes the oracle cannot recompute every pair within a test, so each batch is
-checked (a) on sampled pairs recomputed by the oracle one by one, and (b) on every pair
-through properties that hold at any size: score and extension bounds, the total, and for
-the memory-restricted variant (Sec. 3) equality with the unrestricted run wherever the
-window was never exceeded (overflow flag clear).
+Batches: DNA tiny (1,000 pairs, X = 15), DNA long-read (100,000 pairs) at X = 10, 20 and
+50, protein (1,000,000 pairs, BLOSUM62, X = 49), and the uneven batch (200,000 pairs)
+unrestricted and with the memory-restricted window delta_b = 256, 1024, 4096.  Every pair
+is also checked for properties that hold at any size (score and extension bounds, the
+total), and the restricted runs for equality with the unrestricted one wherever the
+window was never exceeded (the paper's claim for the memory-restricted variant, Sec. 3).
 """
 import os
 
@@ -42,16 +44,15 @@ def _run_device(ctx, b):
     return res
 
 
-def _sampled_parity(got, b, n, seed):
-    rng = np.random.default_rng(seed)
-    idx = np.sort(rng.choice(b.n_pairs, min(n, b.n_pairs), replace=False))
-    L, R, T = oracle.run_batch(b.subset(idx), threads=THREADS)
-    for side, ref in (("left", L), ("right", R)):
+def _all_parity(got, b, ref):
+    L, R, T = ref
+    assert len(L) == b.n_pairs == len(got)
+    for side, o in (("left", L), ("right", R)):
         for f in FIELDS:
-            g = got[side][f][idx]
-            bad = np.nonzero(g != ref[f])[0]
-            assert bad.size == 0, f"{side}.{f} differs at pairs {idx[bad[:10]].tolist()}"
-    assert np.array_equal(got["total"][idx], T)
+            bad = np.nonzero(got[side][f] != o[f])[0]
+            assert bad.size == 0, f"{side}.{f} differs at {bad.size} pairs, first {bad[:10].tolist()}"
+    bad = np.nonzero(got["total"] != T)[0]
+    assert bad.size == 0, f"total differs at {bad.size} pairs, first {bad[:10].tolist()}"
 
 
 def _seed_scores(b):
@@ -85,13 +86,31 @@ def ctx():
     xdrop.xd_destroy(c)
 
 
-def test_full_size_protein_sampled(ctx):
+def test_full_size_dna_tiny_all_pairs(ctx, oracle_all):
+    """1,000 pairs, 1-5 kbp, 15% error, X = 15."""
+    b = synth.dna_tiny()
+    got = _run_device(ctx, b)
+    _properties(got, b)
+    _all_parity(got, b, oracle_all(b))
+
+
+@pytest.mark.parametrize("X", [10, 20, 50])
+def test_full_size_longread_all_pairs(ctx, oracle_all, X):
+    """100,000 long-read pairs (lognormal lengths, median 8 kbp, 8-18% error)."""
+    b = synth.dna_longread().with_params(X=X)
+    got = _run_device(ctx, b)
+    _properties(got, b)
+    assert (got["right"]["flags"] == 0).all() and (got["left"]["flags"] == 0).all()
+    _all_parity(got, b, oracle_all(b))
+
+
+def test_full_size_protein_all_pairs(ctx, oracle_all):
     """1,000,000 protein pairs, BLOSUM62, gap -2, X = 49."""
     b = synth.protein()
     got = _run_device(ctx, b)
     _properties(got, b)
     assert (got["right"]["flags"] == 0).all() and (got["left"]["flags"] == 0).all()
-    _sampled_parity(got, b, 600, seed=31)
+    _all_parity(got, b, oracle_all(b))
 
 
 @pytest.fixture(scope="module")
@@ -104,14 +123,14 @@ def uneven_unrestricted(ctx, uneven):
     return _run_device(ctx, uneven)
 
 
-def test_full_size_uneven_unrestricted_sampled(ctx, uneven, uneven_unrestricted):
+def test_full_size_uneven_unrestricted_all_pairs(uneven, uneven_unrestricted, oracle_all):
     """200,000 DNA pairs, lengths log-uniform in [500, 100,000], X = 20."""
     _properties(uneven_unrestricted, uneven)
-    _sampled_parity(uneven_unrestricted, uneven, 150, seed=32)
+    _all_parity(uneven_unrestricted, uneven, oracle_all(uneven))
 
 
 @pytest.mark.parametrize("delta", [256, 1024, 4096])
-def test_full_size_uneven_restricted(ctx, uneven, uneven_unrestricted, delta):
+def test_full_size_uneven_restricted_all_pairs(ctx, uneven, uneven_unrestricted, oracle_all, delta):
     b = uneven.with_params(delta=delta)
     got = _run_device(ctx, b)
     _properties(got, b)
@@ -121,7 +140,7 @@ def test_full_size_uneven_restricted(ctx, uneven, uneven_unrestricted, delta):
         clear = f == 0
         for fld in FIELDS:
             assert np.array_equal(got[side][fld][clear], uneven_unrestricted[side][fld][clear]), (side, fld)
-    _sampled_parity(got, b, 100, seed=33 + delta)
+    _all_parity(got, b, oracle_all(b))
 
 
 def _ctx_env(env):

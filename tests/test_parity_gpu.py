@@ -3,8 +3,8 @@
 Every field is integer (score, h_ext, v_ext, flags, cells, total), so the tolerance is
 zero.  Cases cover the hand traces, random tiny and ragged inputs, empty and length-1
 sides, X = 0 and X = infinity, tiny and large restricted windows, every workload shape
-at reduced size, and the long-read workload at full size on sampled pairs through the
-device entry point in the launch configuration the bench times.
+at reduced size, and the long-read workload at full size (every pair) through the device
+entry point in the launch configuration the bench times.
 """
 import os
 
@@ -272,10 +272,9 @@ def test_device_entry_matches_host_entry(tiered):
     assert_parity(got, b)
 
 
-def test_full_size_longread_sampled(tiered):
-    """100,000 long-read pairs, X = 20, through xd_run_device as the bench runs it; 400
-    sampled pairs are recomputed by the oracle one by one; every result is also checked
-    for properties that hold at any size."""
+def test_full_size_longread_all_pairs(tiered, oracle_all):
+    """100,000 long-read pairs, X = 20, through xd_run_device as the bench runs it: every
+    pair against the oracle, and every result for properties that hold at any size."""
     b = synth.dna_longread()
     args, out = _device_args(b)
     xdrop.xd_reserve(tiered, b.codes.size, b.n_seqs, b.n_pairs, int(b.lengths.max()))
@@ -283,10 +282,12 @@ def test_full_size_longread_sampled(tiered):
     torch.cuda.synchronize()
     assert xdrop.xd_device_status(tiered) == 0
     got = _results(out)
-    rng = np.random.default_rng(2024)
-    idx = np.sort(rng.choice(b.n_pairs, 400, replace=False))
-    sub = b.subset(idx)
-    assert_parity(got[idx], sub)
+    L, R, T = oracle_all(b)
+    for side, ref in (("left", L), ("right", R)):
+        for f in FIELDS:
+            bad = np.nonzero(got[side][f] != ref[f])[0]
+            assert bad.size == 0, f"{side}.{f} differs at {bad.size} pairs, first {bad[:10].tolist()}"
+    assert np.array_equal(got["total"], T)
     p = b.pairs.astype(np.int64)
     lh, lv = b.lengths[p[:, 0]].astype(np.int64), b.lengths[p[:, 1]].astype(np.int64)
     r, l = got["right"], got["left"]

@@ -1,14 +1,17 @@
-"""The allocation-free entry point against xd_run_device, through the C ABI.
+"""The allocation-free entry point against xd_run_device and the oracle, through the C ABI.
 
 xd_run_device_noalloc serves callers that cannot allocate device memory; it keeps its
 scratch rows in a fixed array inside the library.  Its results must equal xd_run_device's
 bit for bit (all outputs are integers), on two calls in a row (the second call reuses
-whatever the first left in the shared array).  This file is collected last on purpose.
+whatever the first left in the shared array), and the oracle's.  Invalid pairs must be
+flagged, not computed.  This file is collected last on purpose.
 """
 import numpy as np
 import pytest
 
+import oracle
 import synth
+from synth import X_INF
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -52,6 +55,68 @@ def test_noalloc_matches_run_device_on_two_calls(make):
         got = out.cpu().numpy().view(xdrop.RESULT_DTYPE)
         want = ref.cpu().numpy().view(xdrop.RESULT_DTYPE)
         assert np.array_equal(got, want), f"call {call} differs from xd_run_device"
+    L, R, T = oracle.run_batch(b, threads=8)
+    for side, o in (("left", L), ("right", R)):
+        for f in ("score", "h_ext", "v_ext", "flags", "cells"):
+            assert np.array_equal(got[side][f], o[f]), (side, f)
+    assert np.array_equal(got["total"], T)
+
+
+def _noalloc(b, max_side, args=None):
+    args = args or _device_batch(b)
+    out = torch.full((b.n_pairs * xdrop.RESULT_DTYPE.itemsize,), 0xAB, dtype=torch.uint8, device="cuda")
+    assert xdrop.xd_run_device_noalloc(args, max_side, out, None) == xdrop.XD_OK
+    torch.cuda.synchronize()
+    return out.cpu().numpy().view(xdrop.RESULT_DTYPE)
+
+
+INVALID = 0x80000000
+
+
+def test_noalloc_flags_invalid_pairs_on_both_sides():
+    rows = [("ACGTACGTAC", "ACGTACGTAC", 3, 3, 4)] * 4
+    b = synth.from_strings(rows, X=5)
+    b.pairs[1, 0] = b.n_seqs + 7                 # a sequence id past the table
+    b.codes[int(b.offsets[4]) + 1] = 9           # a code outside the DNA alphabet (pair 2's H)
+    got = _noalloc(b, 16)
+    for p in (1, 2):
+        assert got["left"]["flags"][p] & INVALID and got["right"]["flags"][p] & INVALID, p
+    for p in (0, 3):
+        assert not (got["left"]["flags"][p] & INVALID) and not (got["right"]["flags"][p] & INVALID), p
+    # a side longer than max_side_len: H's right side is 10 - 3 - 4 = 3, its left side 3
+    got = _noalloc(b.subset(np.array([0])), 2)
+    assert got["left"]["flags"][0] & INVALID and got["right"]["flags"][0] & INVALID
+
+
+def test_noalloc_single_warp_blocks_when_few_warps_fit():
+    # three rows of 2,000,001 scores take about 24 MB: two warps fit the 64 MiB array, fewer
+    # than a block of four, so the entry point launches single-warp blocks
+    b = synth.dna_longread(n_pairs=40)
+    L, R, T = oracle.run_batch(b, threads=8)
+    for call in range(2):
+        got = _noalloc(b, 2_000_000)
+        for side, o in (("left", L), ("right", R)):
+            for f in ("score", "h_ext", "v_ext", "flags", "cells"):
+                assert np.array_equal(got[side][f], o[f]), (call, side, f)
+        assert np.array_equal(got["total"], T), call
+
+
+def test_noalloc_x_infinite_against_oracle():
+    rng = np.random.default_rng(5)
+    rows = []
+    for _ in range(30):
+        m, n = int(rng.integers(0, 60)), int(rng.integers(0, 60))
+        h = "".join(rng.choice(list("ACGT"), m + 3))
+        v = "".join(rng.choice(list("ACGT"), n + 3))
+        rows.append((h, v, int(rng.integers(0, m + 1)), int(rng.integers(0, n + 1)), 3))
+    for X in (1 << 30, X_INF):
+        b = synth.from_strings(rows, X=X)
+        got = _noalloc(b, 64)
+        L, R, T = oracle.run_batch(b)
+        for side, o in (("left", L), ("right", R)):
+            for f in ("score", "h_ext", "v_ext", "flags", "cells"):
+                assert np.array_equal(got[side][f], o[f]), (X, side, f)
+        assert np.array_equal(got["total"], T)
 
 
 def test_noalloc_rejects_sides_beyond_its_scratch():
