@@ -80,6 +80,8 @@ def parse():
     ap.add_argument("--tune-table", default=None, help="tuning table written by xd_autotune")
     ap.add_argument("--autotune", default=None, help="run xd_autotune on the workload first and write "
                                                       "the table to this path")
+    ap.add_argument("--trace", default=None, help="after the timed region, run one traced batch and save "
+                                                  "its per-side timeline (numpy .npy) to this path")
     return ap.parse_args()
 
 
@@ -467,6 +469,14 @@ def main():
         # seeded differently, so their cell counts differ)
         (job_cells, job_paper, job_pairs), (ms,) = job_totals(dist, dev, [cells, cells_paper, b.n_pairs], [ms])
         value = job_cells / (ms * 1e-3) / 1e9
+
+        if a.trace:
+            # outside the timed region: one more batch with the per-side timeline recorded
+            xdrop.xd_set_trace(ctx, True)
+            xdrop.xd_run_device(ctx, args, out, stream.cuda_stream)
+            torch.cuda.synchronize(dev)
+            np.save(a.trace, xdrop.xd_get_trace(ctx))
+            xdrop.xd_set_trace(ctx, False)
 
         # ---- roofline of the dominant alignment tier
         nb = max(1, tim["batches"])

@@ -252,6 +252,33 @@ xd_status xd_set_timing(xd_ctx* ctx, int32_t enable);
  * XD_ENOTFOUND if no batch was recorded. */
 xd_status xd_get_timing(xd_ctx* ctx, xd_timing* out);
 
+/* Per-side timeline of xd_run_device batches (tracing; off by default).  With enable != 0
+ * every following xd_run_device batch of the context records, for each side extension
+ * (unit u: pair u / 2, right side for even u, left side for odd u) and each level that
+ * worked on it, one xd_trace_rec at index u * 8 + level: level 0 - 4 the register levels
+ * (0 - 3: the roles of the fused persistent grid), 5 the band tier, 6 the generic tier,
+ * 7 the persistent grid's long-side role; records of levels that never saw the side stay
+ * zero.  Each batch overwrites the previous one's records.  Tracing adds a clock read and a
+ * 24-byte store per side and level, turns off graph capture, and allocates 192 bytes per
+ * side extension of device memory (grown on demand, kept until xd_destroy). */
+typedef struct {
+    uint64_t start_ns;      /* globaltimer when the level took the side */
+    uint32_t dur_ns;        /* until the level finished or escalated it */
+    uint32_t diags;         /* anti-diagonals the level computed (register levels) */
+    uint16_t window;        /* window slots of the level */
+    uint16_t smid;          /* SM that ran it */
+    uint8_t lanes;          /* lanes per side (band tier: warps) */
+    uint8_t level;
+    uint16_t outcome;       /* 1 the side finished here, 2 it was escalated */
+} xd_trace_rec;
+
+xd_status xd_set_trace(xd_ctx* ctx, int32_t enable);
+
+/* Synchronises the last traced batch's stream and copies up to capacity bytes of its
+ * records (8 xd_trace_rec per side extension) to the host buffer out; *n_units (may be
+ * NULL) receives the number of side extensions.  XD_ENOTFOUND if no batch was traced. */
+xd_status xd_get_trace(xd_ctx* ctx, void* out, uint64_t capacity, uint64_t* n_units);
+
 /* Throughput microbenchmarks on the context's device: the measured integer/DPX
  * denominators of the alignment kernels' roofline (the method is bound by plain integer
  * arithmetic, Sec. 2.2 recurrence and X-Drop test).  op selects one instruction kind run

@@ -281,6 +281,11 @@ struct xd_ctx {
     cudaGraphExec_t graph_exec = nullptr;
     uint64_t graph_launches = 0;       // kernels per replay
     uint64_t graph_replays = 0, graph_captures = 0;
+    // per-side timeline of xd_run_device batches (xd_set_trace / xd_get_trace)
+    bool tracing = false;
+    DevBuf trace;
+    uint64_t trace_units = 0;          // units of the last traced batch (0: none yet)
+    cudaStream_t trace_stream = nullptr;
 };
 
 namespace {
@@ -583,6 +588,15 @@ xd_status run_pipeline(xd_ctx* c, Scratch& s, const BatchView& b, xd_result* d_o
     P.rec_of = static_cast<uint32_t*>(s.rec_of.p);
     P.rec_ctr = static_cast<uint32_t*>(s.ctr.p) + (3 + 2 * kLevels);
     P.rec_cap = plan.rec_cap;
+    P.trace = nullptr;
+    if (c->tracing && &s == &c->dev && b.n_pairs) {
+        const size_t tb = size_t(2) * b.n_pairs * kTraceVisits * sizeof(TraceRec);
+        XD_CUDA(c, grow(c->trace, tb));
+        XD_CUDA(c, cudaMemsetAsync(c->trace.p, 0, tb, st));
+        P.trace = static_cast<TraceRec*>(c->trace.p);
+        c->trace_units = uint64_t(2) * b.n_pairs;
+        c->trace_stream = st;
+    }
     if (b.n_pairs) XD_CUDA(c, cudaMemsetAsync(s.rec_of.p, 0xff, size_t(2) * b.n_pairs * 4, st));
     P.alpha = b.alpha;
     P.gap = b.gap;
@@ -1177,7 +1191,8 @@ xd_status xd_run_device(xd_ctx* c, const xd_batch* b, xd_result* d_out, void* st
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     XD_CUDA(c, cudaStreamIsCapturing(st, &cs));
     if (cs != cudaStreamCaptureStatusNone) return run_pipeline(c, c->dev, v, d_out, st, nullptr);
-    if (!c->graphs || c->timing || st == nullptr) return run_pipeline(c, c->dev, v, d_out, st, c->coop_done);
+    if (!c->graphs || c->timing || c->tracing || st == nullptr)
+        return run_pipeline(c, c->dev, v, d_out, st, c->coop_done);
     // the scratch must be in place before a capture (no allocation inside one)
     const ScratchPlan plan = plan_scratch(c, v.alpha, v.n_codes, v.n_pairs, v.max_len);
     XD_CUDA(c, ensure_scratch(c->dev, plan));
@@ -1604,6 +1619,25 @@ xd_status xd_get_timing(xd_ctx* c, xd_timing* out) {
     return XD_OK;
 }
 
+xd_status xd_set_trace(xd_ctx* c, int32_t enable) {
+    if (!c) return XD_EINVAL;
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->tracing = enable != 0;
+    return XD_OK;
+}
+
+xd_status xd_get_trace(xd_ctx* c, void* out, uint64_t capacity, uint64_t* n_units) {
+    if (!c || (capacity && !out)) return XD_EINVAL;
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (c->trace_units == 0) return fail(c, XD_ENOTFOUND, "no traced batch");
+    XD_CUDA(c, cudaSetDevice(c->device));
+    XD_CUDA(c, cudaStreamSynchronize(c->trace_stream));
+    const uint64_t bytes = c->trace_units * kTraceVisits * sizeof(TraceRec);
+    if (n_units) *n_units = c->trace_units;
+    if (capacity) XD_CUDA(c, cudaMemcpy(out, c->trace.p, std::min(bytes, capacity), cudaMemcpyDeviceToHost));
+    return XD_OK;
+}
+
 xd_status xd_probe(xd_ctx* c, int32_t op, double* rate) {
     if (!c || !rate) return XD_EINVAL;
     if (!((op >= 0 && op <= 10) || (op >= 100 && op <= 103))) return fail(c, XD_EINVAL, "unknown probe op");
@@ -1793,6 +1827,7 @@ xd_status xd_destroy(xd_ctx* c) {
     }
     release(c->dev);
     release(c->stats);
+    release(c->trace);
     for (SeqStore& ss : c->store) {
         release(ss.words);
         release(ss.d_off);

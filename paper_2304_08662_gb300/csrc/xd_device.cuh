@@ -30,6 +30,27 @@ struct Unit {
 };
 static_assert(sizeof(Unit) == 32, "unit layout");
 
+// Per-side timeline (tracing, off unless the host asks for it): one record per side
+// extension and level that worked on it.  Visit slot: register levels 0 .. 4 (the fused
+// grid's roles are levels 0 .. 3), 5 the band tier, 6 the generic tier, 7 the fused grid's
+// long-side role.
+using TraceRec = xd_trace_rec;   // layout in xdrop.h
+static_assert(sizeof(TraceRec) == 24, "trace record layout");
+constexpr int kTraceVisits = 8;
+constexpr int kTraceLong = 7, kTraceBand = 5, kTraceGeneric = 6;
+
+__device__ __forceinline__ unsigned long long trace_clock() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t trace_smid() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+    return r;
+}
+
 // Everything a tier kernel needs about the batch.
 struct Problem {
     const uint32_t* store;      // packed residues of the whole codes buffer
@@ -55,8 +76,24 @@ struct Problem {
     uint32_t* rec_of;           // per unit: offset of its record, or 0xffffffff (start from scratch)
     uint32_t* rec_ctr;          // pool allocation counter (ints)
     uint32_t rec_cap;
+    TraceRec* trace;            // per unit kTraceVisits records, or null (no tracing)
     int8_t sim[400];            // alpha x alpha similarity, row-major with stride alpha
 };
+
+__device__ __forceinline__ void trace_visit(const Problem& P, uint32_t unit, int level, unsigned long long t0,
+                                            uint32_t diags, int window, int lanes, int outcome) {
+    TraceRec r;
+    r.start_ns = t0;
+    const unsigned long long t1 = trace_clock();
+    r.dur_ns = uint32_t(t1 - t0 < 0xffffffffull ? t1 - t0 : 0xffffffffull);
+    r.diags = diags;
+    r.window = uint16_t(window);
+    r.smid = uint16_t(trace_smid());
+    r.lanes = uint8_t(lanes);
+    r.level = uint8_t(level);
+    r.outcome = uint16_t(outcome);
+    P.trace[size_t(unit) * kTraceVisits + level] = r;
+}
 
 // Queue state of one batch.  The first register level pulls the cost-ordered unit list;
 // a side whose band does not fit a level's window is appended to the next level's queue.

@@ -1050,7 +1050,7 @@ __device__ __forceinline__ bool load_record16(const Problem& P, const Z16& zc, u
 // time (the roles of the fused grid) without sharing shift buffers.
 template <int G, int CG, int A, bool LIVE>
 __device__ __forceinline__ void group_loop(const Problem& P, const Queues& Q, const Source& S, int out_q,
-                                           int chunk, int32_t* smem, int stage, int warp_ints) {
+                                           int chunk, int32_t* smem, int stage, int warp_ints, int level) {
     constexpr int W = G * CG;
     const int lane = threadIdx.x & 31;
     const int gl = lane % G;
@@ -1069,6 +1069,7 @@ __device__ __forceinline__ void group_loop(const Problem& P, const Queues& Q, co
     bool active = false, done = false, skip_odd = false;
     int32_t d_start = 0;
     uint64_t cells_start = 0;
+    unsigned long long t_take = 0;   // tracing: when the group took its side
     LiveWait lw;   // unused (optimised away) for a finished list
     uint32_t pause = 128;
     for (;;) {
@@ -1087,6 +1088,7 @@ __device__ __forceinline__ void group_loop(const Problem& P, const Queues& Q, co
                     pair = u.pair;
                     if (s.m + s.n == 0) {
                         if (gl == 0) {
+                            if (P.trace) trace_visit(P, uidx, level, trace_clock(), 0, W, G, 1);
                             write_side(P.results, pair, s.side, 0, 0, 0, 0, 1);
                             atomicAdd(&P.stats[stage], 1ull);
                             atomicAdd(&P.stats[4 + stage], 1ull);
@@ -1123,6 +1125,7 @@ __device__ __forceinline__ void group_loop(const Problem& P, const Queues& Q, co
                         active = true;
                         d_start = s.d;
                         cells_start = s.cells;
+                        if (P.trace) t_take = trace_clock();
                     }
                 }
             }
@@ -1144,6 +1147,8 @@ __device__ __forceinline__ void group_loop(const Problem& P, const Queues& Q, co
                     // window fill of this level: in-band cells against the slots evaluated
                     atomicAdd(&P.stats[9], (unsigned long long)(s.cells - cells_start));
                     atomicAdd(&P.stats[10], (unsigned long long)(s.d + 1 - d_start) * (unsigned long long)W);
+                    if (P.trace)
+                        trace_visit(P, uidx, level, t_take, uint32_t(s.d + 1 - d_start), W, G, r == kDone ? 1 : 2);
                 }
                 if (r == kDone) {
                     if (gl == 0) {
@@ -1219,7 +1224,7 @@ __global__ void __launch_bounds__(128, MINB) k_group(Problem P, Queues Q, int in
     extern __shared__ __align__(16) int32_t group_smem[];
     build_table<A>(group_smem, P);
     group_loop<G, CG, A, false>(P, Q, static_source(Q, in_q), out_q, chunk, group_smem, in_q < 0 ? 0 : 1,
-                                64 * CG);
+                                64 * CG, in_q + 1);
 }
 
 // The first register levels fused into one persistent, cooperatively launched grid.
@@ -1304,23 +1309,23 @@ __global__ void __launch_bounds__(128, MINB) k_fused(Problem P, Queues Q, RolePl
             Source SL = static_source(Q, -1);
             SL.pull = &Q.ctr[kLongPull];
             SL.n = R.n_long;
-            group_loop<GL, CL, A, false>(P, Q, SL, 0, 1, group_smem, 0, kWarpInts);
+            group_loop<GL, CL, A, false>(P, Q, SL, 0, 1, group_smem, 0, kWarpInts, kTraceLong);
         }
     }
     if (role == 0) {
         Source S0 = static_source(Q, -1);
         S0.list = Q.order + R.n_long;
         S0.n = Q.n_units - R.n_long;
-        group_loop<G0, C0, A, false>(P, Q, S0, 0, chunk, group_smem, 0, kWarpInts);
+        group_loop<G0, C0, A, false>(P, Q, S0, 0, chunk, group_smem, 0, kWarpInts, 0);
         signal_done(done0);
     }
     if (role <= 1) {
         group_loop<G1, C1, A, true>(P, Q, live_source(Q, 0, done0, R.producers0, R.wait_limit_ns), 1, 1, group_smem, 0,
-                              kWarpInts);
+                              kWarpInts, 1);
         signal_done(done1);
     }
     group_loop<G2, C2, A, true>(P, Q, live_source(Q, 1, done1, R.producers1, R.wait_limit_ns), R.out2, 1, group_smem, 0,
-                          kWarpInts);
+                          kWarpInts, 2);
 }
 
 // Four roles: k_fused with a fourth level.  Role 2 appends its overflows to the live queue
@@ -1344,28 +1349,28 @@ __global__ void __launch_bounds__(128, MINB) k_fused4(Problem P, Queues Q, RoleP
             Source SL = static_source(Q, -1);
             SL.pull = &Q.ctr[kLongPull];
             SL.n = R.n_long;
-            group_loop<GL, CL, A, false>(P, Q, SL, 0, 1, group_smem, 0, kWarpInts);
+            group_loop<GL, CL, A, false>(P, Q, SL, 0, 1, group_smem, 0, kWarpInts, kTraceLong);
         }
     }
     if (role == 0) {
         Source S0 = static_source(Q, -1);
         S0.list = Q.order + R.n_long;
         S0.n = Q.n_units - R.n_long;
-        group_loop<G0, C0, A, false>(P, Q, S0, 0, chunk, group_smem, 0, kWarpInts);
+        group_loop<G0, C0, A, false>(P, Q, S0, 0, chunk, group_smem, 0, kWarpInts, 0);
         signal_done(done0);
     }
     if (role <= 1) {
         group_loop<G1, C1, A, true>(P, Q, live_source(Q, 0, done0, R.producers0, R.wait_limit_ns), 1, 1, group_smem, 0,
-                              kWarpInts);
+                              kWarpInts, 1);
         signal_done(done1);
     }
     if (role <= 2) {
         group_loop<G2, C2, A, true>(P, Q, live_source(Q, 1, done1, R.producers1, R.wait_limit_ns), 2, 1, group_smem, 0,
-                              kWarpInts);
+                              kWarpInts, 2);
         signal_done(done2);
     }
     group_loop<G3, C3, A, true>(P, Q, live_source(Q, 2, done2, R.producers2, R.wait_limit_ns), R.out2, 1, group_smem, 0,
-                          kWarpInts);
+                          kWarpInts, 3);
 }
 
 template <int G, int CG, int MINB, int A>

@@ -192,8 +192,11 @@ __global__ void __launch_bounds__(128) k_generic(Problem P, Queues Q, int32_t* s
         if (lane == 0) k = atomicAdd(&Q.ctr[2 + 2 * G], 1u);
         k = __shfl_sync(0xffffffffu, k, 0);
         if (k >= n_q) break;
-        const Unit u = P.units[Q.q[G][k]];
+        const uint32_t uidx = Q.q[G][k];
+        const Unit u = P.units[uidx];
+        const unsigned long long t0 = P.trace ? trace_clock() : 0ull;
         extend_generic(P, u, A, A + stride, A + 2 * stride, sim, lane);
+        if (P.trace && lane == 0) trace_visit(P, uidx, kTraceGeneric, t0, 0, 0, 32, 1);
     }
 }
 
@@ -430,7 +433,10 @@ __global__ void __launch_bounds__(32 * NW) k_band(Problem P, Queues Q) {
         if (k >= n_q) break;
         const uint32_t uidx = Q.q[kBandQ][k];
         const Unit u = P.units[uidx];
-        if (!extend_band<NW>(P, u, uidx, R0, R1, sim, red, tid)) {
+        const unsigned long long t0 = P.trace ? trace_clock() : 0ull;
+        const bool fit = extend_band<NW>(P, u, uidx, R0, R1, sim, red, tid);
+        if (P.trace && tid == 0) trace_visit(P, uidx, kTraceBand, t0, 0, kBandW, 32 * NW / 8, fit ? 1 : 2);
+        if (!fit) {
             if (tid == 0) {
                 push_unit(Q, kGenericQ, uidx);
                 atomicAdd(&P.stats[3], 1ull);

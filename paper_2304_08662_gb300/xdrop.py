@@ -87,6 +87,8 @@ def lib():
         L.xd_set_timing.argtypes = [P, ctypes.c_int32]
         L.xd_get_timing.argtypes = [P, ctypes.POINTER(xd_timing)]
         L.xd_probe.argtypes = [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
+        L.xd_set_trace.argtypes = [P, ctypes.c_int32]
+        L.xd_get_trace.argtypes = [P, V, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]
         L.xd_run_device_noalloc.argtypes = [ctypes.POINTER(xd_batch), ctypes.c_uint32, V, V]
         L.xd_autotune.argtypes = [P, ctypes.POINTER(xd_batch), ctypes.c_char_p, ctypes.POINTER(ctypes.c_float)]
         L.xd_store_add.argtypes = [P, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64, V, V, V, V]
@@ -98,6 +100,7 @@ def lib():
         L.xd_version.restype = ctypes.c_char_p
         for name in ("xd_create", "xd_submit_batch", "xd_poll", "xd_run_device", "xd_reserve",
                      "xd_device_status", "xd_get_stats", "xd_destroy", "xd_set_timing", "xd_get_timing", "xd_probe", "xd_run_device_noalloc", "xd_autotune",
+                     "xd_set_trace", "xd_get_trace",
                      "xd_store_add", "xd_store_info", "xd_submit_pairs"):
             getattr(L, name).restype = ctypes.c_int
         _LIB = L
@@ -241,6 +244,32 @@ def xd_get_timing(ctx):
 PROBE_OPS = {"add": 0, "max": 1, "dpx_addmax": 2, "dpx_max3": 3, "lop3": 4, "imad": 5,
              "cmp_sel": 6, "prmt": 7, "dpx_addmax_16x2": 8, "dpx_max3_16x2": 9, "max_16x2": 10,
              "cell_dna": 100, "cell_prot": 101, "cell_dna16": 102, "cell_prot16": 103}
+
+
+TRACE_DTYPE = np.dtype([("start_ns", np.uint64), ("dur_ns", np.uint32), ("diags", np.uint32),
+                        ("window", np.uint16), ("smid", np.uint16), ("lanes", np.uint8), ("level", np.uint8),
+                        ("outcome", np.uint16)])
+assert TRACE_DTYPE.itemsize == 24
+TRACE_VISITS = 8
+
+
+def xd_set_trace(ctx, enable):
+    rc = lib().xd_set_trace(ctx, 1 if enable else 0)
+    if rc != XD_OK:
+        raise XdError(rc, xd_last_error(ctx))
+
+
+def xd_get_trace(ctx):
+    """Records of the last traced xd_run_device batch: array [n_units, 8] of TRACE_DTYPE."""
+    n = ctypes.c_uint64()
+    rc = lib().xd_get_trace(ctx, None, 0, ctypes.byref(n))
+    if rc != XD_OK:
+        raise XdError(rc, xd_last_error(ctx))
+    out = np.zeros((n.value, TRACE_VISITS), dtype=TRACE_DTYPE)
+    rc = lib().xd_get_trace(ctx, out.ctypes.data_as(ctypes.c_void_p), out.nbytes, ctypes.byref(n))
+    if rc != XD_OK:
+        raise XdError(rc, xd_last_error(ctx))
+    return out
 
 
 def xd_probe(ctx, op):
