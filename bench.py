@@ -47,6 +47,20 @@ ALU_LANES_PER_SM = 64
 DOMINANT_KERNEL_TRAFFIC = {}
 
 
+def save_trace(path, tr):
+    """Compact per-side timeline: one row per (side extension, level) that ran, times in
+    microseconds from the batch's first start, written with numpy's compressed format."""
+    seen = tr["start_ns"] != 0
+    u, lv = np.nonzero(seen)
+    r = tr[u, lv]
+    t0 = int(r["start_ns"].min()) if r.size else 0
+    np.savez_compressed(path, unit=u.astype(np.uint32), level=lv.astype(np.uint8),
+                        start_us=((r["start_ns"].astype(np.int64) - t0) / 1e3).astype(np.float32),
+                        dur_us=(r["dur_ns"] / 1e3).astype(np.float32), diags=r["diags"], window=r["window"],
+                        smid=r["smid"], lanes=r["lanes"], outcome=r["outcome"].astype(np.uint8),
+                        n_units=np.array([tr.shape[0]]))
+
+
 def packed_scores(b):
     """True when the library runs this batch's register levels on 16-bit scores (the bound
     of the packed representation: -127 <= gap <= 0 and theta1 - theta0 >= 64)."""
@@ -80,8 +94,11 @@ def parse():
     ap.add_argument("--tune-table", default=None, help="tuning table written by xd_autotune")
     ap.add_argument("--autotune", default=None, help="run xd_autotune on the workload first and write "
                                                       "the table to this path")
+    ap.add_argument("--batches-per-launch", type=int, default=1,
+                    help="batches of the workload that share one pass of the hot path (xd_run_device_many): "
+                         "the timed steps run as launches of this many batches each")
     ap.add_argument("--trace", default=None, help="after the timed region, run one traced batch and save "
-                                                  "its per-side timeline (numpy .npy) to this path")
+                                                  "its per-side timeline (compressed numpy .npz) to this path")
     return ap.parse_args()
 
 
@@ -104,8 +121,10 @@ def make_batch(a, rank):
 
 def workload_config(a, b):
     seeds = b.meta.get("seeds_per_pair", 1)
+    bpl = max(1, getattr(a, "batches_per_launch", 1))
     return {"workload": f"{a.workload}_{b.n_pairs // seeds}_x{b.X}" + (f"_delta{b.delta}" if b.delta else "") +
                         (f"_{seeds}seeds" if seeds > 1 else ""),
+            "batches_per_launch": bpl,
             "pairs": b.n_pairs, "residues": int(b.codes.size), "X": b.X, "delta_b": b.delta,
             "alphabet": b.alphabet, "scoring": ("BLOSUM62" if b.alphabet == "protein" else
                                                 f"{b.match}/{b.mismatch}/{b.gap}"),
@@ -437,15 +456,28 @@ def main():
         args = xdrop.BatchArgs(b.alphabet, codes, offs, lens, pairs, b.match, b.mismatch, b.gap,
                                b.matrix, b.X, b.delta)
         out = torch.zeros(b.n_pairs * xdrop.RESULT_DTYPE.itemsize, dtype=torch.uint8, device=dev)
-        xdrop.xd_reserve(ctx, b.codes.size, b.n_seqs, b.n_pairs, int(b.lengths.max()))
         stream = torch.cuda.current_stream(dev)
+        bpl = max(1, a.batches_per_launch)
         for _ in range(max(3, a.warmup)):
             xdrop.xd_run_device(ctx, args, out, stream.cuda_stream)
         torch.cuda.synchronize(dev)
         if xdrop.xd_device_status(ctx) != 0:
             raise RuntimeError("device validation failed")
-        res = out.cpu().numpy().view(xdrop.RESULT_DTYPE)
+        res = out.cpu().numpy().view(xdrop.RESULT_DTYPE).copy()
         cells = float(res["left"]["cells"].sum() + res["right"]["cells"].sum())
+        # the timed steps: launches of bpl batches each (the last one may hold fewer)
+        launch_sizes = [min(bpl, a.steps - k) for k in range(0, a.steps, bpl)]
+        out_many = None
+        if bpl > 1:
+            xdrop.xd_reserve(ctx, bpl * b.codes.size, bpl * b.n_seqs, bpl * b.n_pairs, int(b.lengths.max()))
+            out_many = torch.zeros(bpl * b.n_pairs * xdrop.RESULT_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+            for _ in range(max(1, -(-max(3, a.warmup) // bpl))):
+                xdrop.xd_run_device_many(ctx, [args] * bpl, out_many, stream.cuda_stream)
+            torch.cuda.synchronize(dev)
+            if xdrop.xd_device_status(ctx) != 0:
+                raise RuntimeError("device validation failed")
+        else:
+            xdrop.xd_reserve(ctx, b.codes.size, b.n_seqs, b.n_pairs, int(b.lengths.max()))
 
         # ---- timed region: device-resident inputs
         xdrop.xd_set_timing(ctx, True)
@@ -455,8 +487,12 @@ def main():
         torch.cuda.synchronize(dev)
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        for _ in range(a.steps):
-            xdrop.xd_run_device(ctx, args, out, stream.cuda_stream)
+        if bpl > 1:
+            for k in launch_sizes:
+                xdrop.xd_run_device_many(ctx, [args] * k, out_many, stream.cuda_stream)
+        else:
+            for _ in range(a.steps):
+                xdrop.xd_run_device(ctx, args, out, stream.cuda_stream)
         ev1.record(stream)
         torch.cuda.synchronize(dev)
         if dist:
@@ -465,6 +501,12 @@ def main():
         ms = ev0.elapsed_time(ev1) / a.steps
         tim = xdrop.xd_get_timing(ctx)
         xdrop.xd_set_timing(ctx, False)
+        if bpl > 1:
+            # every batch of the last launch gave the single-batch results
+            got = out_many.cpu().numpy().view(xdrop.RESULT_DTYPE)
+            for k in range(launch_sizes[-1]):
+                if not np.array_equal(got[k * b.n_pairs:(k + 1) * b.n_pairs], res):
+                    raise RuntimeError(f"batch {k} of a shared launch differs from its single-batch run")
         # whole job: every rank's cells over the slowest rank's time (the ranks' batches are
         # seeded differently, so their cell counts differ)
         (job_cells, job_paper, job_pairs), (ms,) = job_totals(dist, dev, [cells, cells_paper, b.n_pairs], [ms])
@@ -475,7 +517,7 @@ def main():
             xdrop.xd_set_trace(ctx, True)
             xdrop.xd_run_device(ctx, args, out, stream.cuda_stream)
             torch.cuda.synchronize(dev)
-            np.save(a.trace, xdrop.xd_get_trace(ctx))
+            save_trace(a.trace, xdrop.xd_get_trace(ctx))
             xdrop.xd_set_trace(ctx, False)
 
         # ---- roofline of the dominant alignment tier

@@ -206,6 +206,22 @@ xd_status xd_poll(xd_ctx* ctx, uint64_t ticket, xd_result* out, int32_t wait_ms)
  * Errors: XD_EINVAL (null pointers, X < 0, protein without matrix), XD_ENOMEM, XD_EDEVICE. */
 xd_status xd_run_device(xd_ctx* ctx, const xd_batch* dev_batch, xd_result* d_out, void* stream);
 
+/* Several device batches in one pass of the hot path: as xd_run_device, but the n_batches
+ * batches (device pointers as for xd_run_device) share one set of launches -- one packed
+ * store, one cost-ordered list of all their side extensions, one persistent extension grid
+ * -- so the long serial chains of one batch overlap the bulk work of the others instead of
+ * leaving the GPU idle at the end of each batch (the load-balancing goal of Sec. 4.2 and the
+ * shared work queue of Sec. 4.4, across batches).  The batches must share alphabet, scoring,
+ * X and delta_b.  d_out receives the results of every pair in batch order: batch k's pairs
+ * start at the sum of the earlier batches' n_pairs.  Each batch's results are identical to
+ * running it alone.  Never captured as a graph by the library (the call may still be
+ * captured into the caller's graph).  Not reentrant per context; shares the scratch of
+ * xd_run_device (size it with xd_reserve for the sum of the batches).  Errors: XD_EINVAL
+ * (null pointers, differing parameters, X < 0, protein without matrix, 2^31 or more pairs in
+ * all), XD_ENOMEM, XD_EDEVICE; device-side validation as for xd_run_device. */
+xd_status xd_run_device_many(xd_ctx* ctx, uint32_t n_batches, const xd_batch* batches, xd_result* d_out,
+                             void* stream);
+
 /* Pre-size the scratch used by xd_run_device for batches up to the given sizes. */
 xd_status xd_reserve(xd_ctx* ctx, uint64_t n_codes, uint32_t n_seqs, uint32_t n_pairs,
                      uint32_t max_seq_len);

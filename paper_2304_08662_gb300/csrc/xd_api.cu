@@ -546,11 +546,35 @@ const TierConfig& tiers_for(const xd_ctx* c, const BatchView& b) {
     return c->tiers_large_x;
 }
 
-// The hot path of one batch (Sec. 3 method on every side extension), all on stream st.
+// The hot path of nb batches that share alphabet, scoring, X and delta_b (Sec. 3 method on
+// every side extension), all on stream st and in one set of launches: the batches' residues
+// are packed into one store (each batch from a word boundary), their side extensions form
+// one cost-ordered unit list for the tiers, and batch k's results land at d_out + its first
+// pair (the batches' pairs in order).  One batch is the common case (nb = 1).
 // chain: an event that orders the fused persistent launches of the context (may be null).
-xd_status run_pipeline(xd_ctx* c, Scratch& s, const BatchView& b, xd_result* d_out, cudaStream_t st,
+xd_status run_pipeline(xd_ctx* c, Scratch& s, const BatchView* bs, int nb, xd_result* d_out, cudaStream_t st,
                        cudaEvent_t chain) {
     Range range("xd.pipeline");
+    const BatchView& b0 = bs[0];
+    const uint64_t per_word = b0.alpha == 4 ? 16 : 6;
+    // per batch: first pair, first store word; totals over the batches
+    std::vector<uint32_t> pair_base(nb);
+    std::vector<uint64_t> word_base(nb);
+    uint64_t n_pairs_all = 0, words_all = 0, codes_all = 0;
+    uint32_t max_len = 0;
+    for (int k = 0; k < nb; k++) {
+        pair_base[k] = uint32_t(n_pairs_all);
+        word_base[k] = words_all;
+        n_pairs_all += bs[k].n_pairs;
+        words_all += (bs[k].n_codes + per_word - 1) / per_word;
+        codes_all += bs[k].n_codes;
+        max_len = std::max(max_len, bs[k].max_len);
+    }
+    if (n_pairs_all >= (uint64_t(1) << 31)) return fail(c, XD_EINVAL, "too many pairs in one launch");
+    BatchView b = b0;                  // the parameters, with the sizes of all batches
+    b.n_pairs = uint32_t(n_pairs_all);
+    b.n_codes = words_all * per_word;
+    b.max_len = max_len;
     ScratchPlan plan = plan_scratch(c, b.alpha, b.n_codes, b.n_pairs, b.max_len);
     XD_CUDA(c, ensure_scratch(s, plan));
     bool timed = c->timing && c->ev_used < 4096;
@@ -571,7 +595,9 @@ xd_status run_pipeline(xd_ctx* c, Scratch& s, const BatchView& b, xd_result* d_o
     auto* err = static_cast<uint32_t*>(s.err.p);
     const uint32_t* store = b.packed ? b.packed : static_cast<const uint32_t*>(s.store.p);
     if (!b.packed)
-        XD_CUDA(c, launch_pack(b.alpha, b.codes, b.n_codes, static_cast<uint32_t*>(s.store.p), err, c->n_sm, st));
+        for (int k = 0; k < nb; k++)
+            XD_CUDA(c, launch_pack(b.alpha, bs[k].codes, bs[k].n_codes,
+                                   static_cast<uint32_t*>(s.store.p) + word_base[k], err, c->n_sm, st));
     XD_CUDA(c, mark(1));
     Problem P{};
     P.store = store;
@@ -603,10 +629,13 @@ xd_status run_pipeline(xd_ctx* c, Scratch& s, const BatchView& b, xd_result* d_o
     P.X = b.X;
     P.delta = b.delta;
     std::memcpy(P.sim, b.sim, sizeof(P.sim));
-    const uint64_t n_res = b.packed ? b.packed_words * uint64_t(b.alpha == 4 ? 16 : 6) : b.n_codes;
-    XD_CUDA(c, launch_units(b.pairs, b.n_pairs, b.offsets, b.lengths, b.n_seqs, n_res, b.max_abs, b.max_len,
-                            static_cast<Unit*>(s.units.p), static_cast<uint32_t*>(s.bucket.p),
-                            static_cast<uint32_t*>(s.hist.p), err, st));
+    // residues each batch may address (a resident-store batch: the whole store)
+    auto n_res_of = [&](int k) { return b.packed ? b.packed_words * per_word : bs[k].n_codes; };
+    for (int k = 0; k < nb; k++)
+        XD_CUDA(c, launch_units(bs[k].pairs, bs[k].n_pairs, bs[k].offsets, bs[k].lengths, bs[k].n_seqs, n_res_of(k),
+                                b.max_abs, b.max_len, pair_base[k], word_base[k] * per_word,
+                                static_cast<Unit*>(s.units.p), static_cast<uint32_t*>(s.bucket.p),
+                                static_cast<uint32_t*>(s.hist.p), err, st));
     XD_CUDA(c, mark(2));
     Queues Q{};
     Q.order = static_cast<const uint32_t*>(s.order.p);
@@ -620,8 +649,8 @@ xd_status run_pipeline(xd_ctx* c, Scratch& s, const BatchView& b, xd_result* d_o
                             static_cast<const uint32_t*>(s.bucket.p), Q.n_units,
                             static_cast<uint32_t*>(s.order.p), st));
     XD_CUDA(c, mark(3));
-    uint64_t launches = b.n_pairs ? 4 : 3;   // pack (when codes exist), units, scan, scatter
-    if (b.n_codes == 0) launches -= 1;
+    uint64_t launches = 1 + (b.n_pairs ? 1 : 0);   // scan, scatter (with pairs), plus per batch below
+    for (int k = 0; k < nb; k++) launches += (bs[k].n_codes ? 1 : 0) + (bs[k].n_pairs ? 1 : 0);   // pack, units
     if (b.n_pairs) {
         if (c->generic_only) {
             XD_CUDA(c, launch_route_all_generic(Q, st));
@@ -655,8 +684,10 @@ xd_status run_pipeline(xd_ctx* c, Scratch& s, const BatchView& b, xd_result* d_o
         XD_CUDA(c, launch_generic(P, Q, static_cast<int32_t*>(s.generic.p), plan.generic_stride,
                                   plan.generic_blocks, st));
         XD_CUDA(c, mark(6));
-        XD_CUDA(c, launch_totals(b.pairs, b.n_pairs, b.offsets, b.lengths, b.n_seqs, n_res, P, st));
-        launches += 2;
+        for (int k = 0; k < nb; k++)
+            XD_CUDA(c, launch_totals(bs[k].pairs, bs[k].n_pairs, bs[k].offsets, bs[k].lengths, bs[k].n_seqs,
+                                     n_res_of(k), pair_base[k], word_base[k] * per_word, P, st));
+        launches += 1 + nb;
     } else {
         XD_CUDA(c, mark(4));
         XD_CUDA(c, mark(5));
@@ -670,6 +701,11 @@ xd_status run_pipeline(xd_ctx* c, Scratch& s, const BatchView& b, xd_result* d_o
     c->batches += 1;
     c->pairs += b.n_pairs;
     return XD_OK;
+}
+
+xd_status run_pipeline(xd_ctx* c, Scratch& s, const BatchView& b, xd_result* d_out, cudaStream_t st,
+                       cudaEvent_t chain) {
+    return run_pipeline(c, s, &b, 1, d_out, st, chain);
 }
 
 // ---------------------------------------------------------------- request dispatcher
@@ -1264,6 +1300,47 @@ xd_status xd_run_device(xd_ctx* c, const xd_batch* b, xd_result* d_out, void* st
     c->batches += 1;
     c->pairs += v.n_pairs;
     return XD_OK;
+}
+
+xd_status xd_run_device_many(xd_ctx* c, uint32_t n_batches, const xd_batch* batches, xd_result* d_out,
+                             void* stream) {
+    if (!c || (n_batches && !batches)) return XD_EINVAL;
+    std::lock_guard<std::mutex> lk(c->mu);
+    XD_CUDA(c, cudaSetDevice(c->device));
+    if (n_batches == 0) return XD_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::vector<BatchView> vs(n_batches);
+    uint64_t pairs = 0;
+    for (uint32_t k = 0; k < n_batches; k++) {
+        const xd_batch* b = &batches[k];
+        BatchView& v = vs[k];
+        xd_status s = scoring_view(c, b, v);
+        if (s != XD_OK) return s;
+        if (k > 0 && !same_params(vs[0], v))
+            return fail(c, XD_EINVAL, "the batches of one call must share alphabet, scoring, X and delta_b");
+        if (b->n_pairs && (!b->pairs || !b->seq_offsets || !b->seq_lengths || !d_out))
+            return fail(c, XD_EINVAL, "null device pointer in batch " + std::to_string(k));
+        if (b->n_codes && !b->seq_codes) return fail(c, XD_EINVAL, "null seq_codes in batch " + std::to_string(k));
+        v.codes = b->seq_codes;
+        v.offsets = b->seq_offsets;
+        v.lengths = b->seq_lengths;
+        v.pairs = b->pairs;
+        pairs += b->n_pairs;
+        if (c->reserved_len == 0 && b->n_seqs) {
+            // no reservation: size the generic scratch from the actual lengths (synchronous)
+            std::vector<uint32_t> lens(b->n_seqs);
+            XD_CUDA(c, cudaMemcpyAsync(lens.data(), b->seq_lengths, 4ull * b->n_seqs, cudaMemcpyDeviceToHost, st));
+            XD_CUDA(c, cudaStreamSynchronize(st));
+            v.max_len = *std::max_element(lens.begin(), lens.end());
+        } else {
+            v.max_len = c->reserved_len;
+        }
+    }
+    if (pairs >= (uint64_t(1) << 31)) return fail(c, XD_EINVAL, "too many pairs in one call");
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    XD_CUDA(c, cudaStreamIsCapturing(st, &cs));
+    return run_pipeline(c, c->dev, vs.data(), int(n_batches), d_out, st,
+                        cs != cudaStreamCaptureStatusNone ? nullptr : c->coop_done);
 }
 
 xd_status xd_device_status(xd_ctx* c, uint32_t* flags) {

@@ -69,7 +69,9 @@ __global__ void k_pack_prot(const uint8_t* __restrict__ codes, uint64_t n_codes,
 // about 2 min(m, n) when the alignment runs to the end of the shorter sequence.  Buckets are
 // quarter octaves of min(m, n) + 1.  Invalid tuples raise kErrSeed and become empty units;
 // sides whose scores could leave the exact range raise kErrRange and also become empty.
-// n_res: residues in the store; a sequence whose offset + length passes it is invalid.
+// n_res: residues of the batch; a sequence whose offset + length passes it is invalid.
+// Several batches can share one launch: batch-local pair p becomes pair pair_base + p (units
+// 2 (pair_base + p) and + 1), and its residues start at res_base in the shared store.
 __device__ __forceinline__ uint32_t cost_bucket(uint32_t m, uint32_t n) {
     const uint32_t s = min(m, n) + 1u;
     const uint32_t lg = 31u - uint32_t(__clz(s));               // floor(log2 s)
@@ -80,6 +82,7 @@ __device__ __forceinline__ uint32_t cost_bucket(uint32_t m, uint32_t n) {
 __global__ void k_units(const xd_pair* __restrict__ pairs, uint32_t n_pairs,
                         const uint64_t* __restrict__ offsets, const uint32_t* __restrict__ lengths,
                         uint32_t n_seqs, uint64_t n_res, int32_t max_abs, uint32_t max_len,
+                        uint32_t pair_base, uint64_t res_base,
                         Unit* __restrict__ units, uint32_t* __restrict__ bucket_of,
                         uint32_t* __restrict__ hist, uint32_t* err) {
     __shared__ uint32_t sh[64];
@@ -102,7 +105,9 @@ __global__ void k_units(const xd_pair* __restrict__ pairs, uint32_t n_pairs,
                 bad = kErrSeed;
         }
         Unit r{}, l{};
-        r.pair = l.pair = p;
+        r.pair = l.pair = pair_base + p;
+        ho += res_base;
+        vo += res_base;
         r.side = 0; l.side = 1;
         if (!bad) {
             r.h0 = ho + e.h_seed + e.seed_len; r.m = lh - e.h_seed - e.seed_len;
@@ -115,11 +120,12 @@ __global__ void k_units(const xd_pair* __restrict__ pairs, uint32_t n_pairs,
             bad |= range;
         }
         if (bad) atomicOr(err, bad);
-        units[2 * p] = r;
-        units[2 * p + 1] = l;
+        const uint32_t u = 2 * (pair_base + p);
+        units[u] = r;
+        units[u + 1] = l;
         uint32_t br = cost_bucket(r.m, r.n), bl = cost_bucket(l.m, l.n);
-        bucket_of[2 * p] = br;
-        bucket_of[2 * p + 1] = bl;
+        bucket_of[u] = br;
+        bucket_of[u + 1] = bl;
         atomicAdd(&sh[br], 1u);
         atomicAdd(&sh[bl], 1u);
     }
@@ -457,7 +463,7 @@ __global__ void k_route_all_generic(Queues Q) {
 // a9: pair totals = left + right + sum of Sim over the seed.
 __global__ void k_totals(const xd_pair* __restrict__ pairs, uint32_t n_pairs,
                          const uint64_t* __restrict__ offsets, const uint32_t* __restrict__ lengths,
-                         uint32_t n_seqs, uint64_t n_res, Problem P) {
+                         uint32_t n_seqs, uint64_t n_res, uint32_t pair_base, uint64_t res_base, Problem P) {
     __shared__ int32_t sim[400];
     for (int t = threadIdx.x; t < P.alpha * P.alpha; t += blockDim.x) sim[t] = P.sim[t];
     __syncthreads();
@@ -466,7 +472,7 @@ __global__ void k_totals(const xd_pair* __restrict__ pairs, uint32_t n_pairs,
     xd_pair e = pairs[p];
     int64_t seed = 0;
     if (e.h_id < n_seqs && e.v_id < n_seqs) {
-        uint64_t ho = offsets[e.h_id] + e.h_seed, vo = offsets[e.v_id] + e.v_seed;
+        uint64_t ho = res_base + offsets[e.h_id] + e.h_seed, vo = res_base + offsets[e.v_id] + e.v_seed;
         // only tuples that k_units accepted: the seed inside its sequence, the sequence
         // inside the store
         if (uint64_t(e.h_seed) + e.seed_len <= lengths[e.h_id] &&
@@ -475,7 +481,7 @@ __global__ void k_totals(const xd_pair* __restrict__ pairs, uint32_t n_pairs,
             for (uint32_t t = 0; t < e.seed_len; t++)
                 seed += sim[residue(P.store, P.alpha, ho + t) * P.alpha + residue(P.store, P.alpha, vo + t)];
     }
-    xd_result& r = P.results[p];
+    xd_result& r = P.results[pair_base + p];
     r.total = int64_t(r.left.score) + int64_t(r.right.score) + seed;
 }
 
@@ -508,11 +514,12 @@ cudaError_t launch_pack(int alpha, const uint8_t* codes, uint64_t n_codes, uint3
 
 cudaError_t launch_units(const xd_pair* pairs, uint32_t n_pairs, const uint64_t* offsets,
                          const uint32_t* lengths, uint32_t n_seqs, uint64_t n_res, int32_t max_abs,
-                         uint32_t max_len, Unit* units, uint32_t* bucket_of, uint32_t* hist,
-                         uint32_t* err, cudaStream_t st) {
+                         uint32_t max_len, uint32_t pair_base, uint64_t res_base, Unit* units,
+                         uint32_t* bucket_of, uint32_t* hist, uint32_t* err, cudaStream_t st) {
     if (n_pairs == 0) return cudaSuccess;
     k_units<<<(n_pairs + 255) / 256, 256, 0, st>>>(pairs, n_pairs, offsets, lengths, n_seqs, n_res,
-                                                   max_abs, max_len, units, bucket_of, hist, err);
+                                                   max_abs, max_len, pair_base, res_base, units,
+                                                   bucket_of, hist, err);
     return cudaGetLastError();
 }
 
@@ -549,10 +556,11 @@ cudaError_t launch_band(const Problem& P, const Queues& Q, int n_sm, cudaStream_
 }
 
 cudaError_t launch_totals(const xd_pair* pairs, uint32_t n_pairs, const uint64_t* offsets,
-                          const uint32_t* lengths, uint32_t n_seqs, uint64_t n_res, const Problem& P,
-                          cudaStream_t st) {
+                          const uint32_t* lengths, uint32_t n_seqs, uint64_t n_res, uint32_t pair_base,
+                          uint64_t res_base, const Problem& P, cudaStream_t st) {
     if (n_pairs == 0) return cudaSuccess;
-    k_totals<<<(n_pairs + 255) / 256, 256, 0, st>>>(pairs, n_pairs, offsets, lengths, n_seqs, n_res, P);
+    k_totals<<<(n_pairs + 255) / 256, 256, 0, st>>>(pairs, n_pairs, offsets, lengths, n_seqs, n_res,
+                                                    pair_base, res_base, P);
     return cudaGetLastError();
 }
 

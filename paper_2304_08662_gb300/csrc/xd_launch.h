@@ -16,8 +16,8 @@ cudaError_t launch_pack(int alpha, const uint8_t* codes, uint64_t n_codes, uint3
                         uint32_t* err, int n_sm, cudaStream_t st);
 cudaError_t launch_units(const xd_pair* pairs, uint32_t n_pairs, const uint64_t* offsets,
                          const uint32_t* lengths, uint32_t n_seqs, uint64_t n_res, int32_t max_abs,
-                         uint32_t max_len, Unit* units, uint32_t* bucket_of, uint32_t* hist,
-                         uint32_t* err, cudaStream_t st);
+                         uint32_t max_len, uint32_t pair_base, uint64_t res_base, Unit* units,
+                         uint32_t* bucket_of, uint32_t* hist, uint32_t* err, cudaStream_t st);
 cudaError_t launch_order(uint32_t* hist, uint32_t* ctr, int n_ctr, const uint32_t* bucket_of,
                          uint32_t n_units, uint32_t* order, cudaStream_t st);
 cudaError_t launch_route_all_generic(const Queues& Q, cudaStream_t st);
@@ -25,8 +25,8 @@ cudaError_t launch_generic(const Problem& P, const Queues& Q, int32_t* scratch,
                            uint64_t stride, int n_blocks, cudaStream_t st);
 cudaError_t launch_band(const Problem& P, const Queues& Q, int n_sm, cudaStream_t st);
 cudaError_t launch_totals(const xd_pair* pairs, uint32_t n_pairs, const uint64_t* offsets,
-                          const uint32_t* lengths, uint32_t n_seqs, uint64_t n_res, const Problem& P,
-                          cudaStream_t st);
+                          const uint32_t* lengths, uint32_t n_seqs, uint64_t n_res, uint32_t pair_base,
+                          uint64_t res_base, const Problem& P, cudaStream_t st);
 
 cudaError_t launch_accumulate(const unsigned long long* batch, unsigned long long* total, int n,
                               cudaStream_t st);

@@ -88,6 +88,7 @@ def lib():
         L.xd_get_timing.argtypes = [P, ctypes.POINTER(xd_timing)]
         L.xd_probe.argtypes = [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
         L.xd_set_trace.argtypes = [P, ctypes.c_int32]
+        L.xd_run_device_many.argtypes = [P, ctypes.c_uint32, ctypes.POINTER(xd_batch), V, V]
         L.xd_get_trace.argtypes = [P, V, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]
         L.xd_run_device_noalloc.argtypes = [ctypes.POINTER(xd_batch), ctypes.c_uint32, V, V]
         L.xd_autotune.argtypes = [P, ctypes.POINTER(xd_batch), ctypes.c_char_p, ctypes.POINTER(ctypes.c_float)]
@@ -100,7 +101,7 @@ def lib():
         L.xd_version.restype = ctypes.c_char_p
         for name in ("xd_create", "xd_submit_batch", "xd_poll", "xd_run_device", "xd_reserve",
                      "xd_device_status", "xd_get_stats", "xd_destroy", "xd_set_timing", "xd_get_timing", "xd_probe", "xd_run_device_noalloc", "xd_autotune",
-                     "xd_set_trace", "xd_get_trace",
+                     "xd_set_trace", "xd_get_trace", "xd_run_device_many",
                      "xd_store_add", "xd_store_info", "xd_submit_pairs"):
             getattr(L, name).restype = ctypes.c_int
         _LIB = L
@@ -187,6 +188,14 @@ def xd_poll(ctx, ticket, out, wait_ms=-1):
 
 def xd_run_device(ctx, args, d_out, stream=None):
     rc = lib().xd_run_device(ctx, ctypes.byref(args.c), _ptr(d_out), stream)
+    if rc != XD_OK:
+        raise XdError(rc, xd_last_error(ctx))
+
+
+def xd_run_device_many(ctx, args_list, d_out, stream=None):
+    """Several device batches (BatchArgs) in one pass; d_out holds their results in order."""
+    arr = (xd_batch * len(args_list))(*[a.c for a in args_list])
+    rc = lib().xd_run_device_many(ctx, len(args_list), arr, _ptr(d_out), stream)
     if rc != XD_OK:
         raise XdError(rc, xd_last_error(ctx))
 
