@@ -59,7 +59,8 @@ typedef enum { XD_DNA2 = 0, XD_PROT5 = 1 } xd_alphabet;
  * table written by xd_autotune, or NULL for built-in defaults.  batching: 0 or 1 = continuous
  * batching (host batches that wait for a free launch slot and share scoring, X and delta_b
  * are merged into one launch); -1 = one launch per host batch.  max_batch_pairs: cap on the
- * pairs of one merged launch (0 = 2^20; a single larger batch still runs alone). */
+ * pairs of one merged launch (0 = 2^20; a single larger batch still runs alone); a merged
+ * launch also holds at most 24 GiB of residue codes. */
 typedef struct {
     int32_t device;
     uint64_t store_bytes_cap;
@@ -318,7 +319,8 @@ xd_status xd_probe(xd_ctx* ctx, int32_t op, double* rate);
  * width), the queue chunk of single-lane levels (1 - 64), the long-side head of the
  * persistent grid and its role mix -- three runs each on a stream of its own, and keeps the
  * fastest for the sample's bucket: alphabet x X (<= 15, <= 30, more) x longest side
- * (<= 2,048, <= 20,000, more) x size (< 8,192, < 65,536, more side extensions).  Every
+ * (<= 2,048, <= 20,000, more) x size (< 8,192, < 65,536, < 1,048,576, more side extensions
+ * in one launch).  Every
  * candidate must reproduce the first candidate's results bit for bit, else the call fails
  * with XD_EDEVICE and keeps nothing.  The winner applies to later batches of the context;
  * if path is not NULL or empty it is also merged into the text table at path (created if

@@ -13,7 +13,7 @@ CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libxd.so")
 SOURCES = ["xd_api.cu", "xd_kernels.cu", "xd_tiers.cu", "xd_tiers_dna.cu", "xd_tiers_dna16.cu", "xd_tiers_prot.cu",
-           "xd_tiers_prot16.cu", "xd_roof.cu", "xd_noalloc.cu"]
+           "xd_tiers_prot16.cu", "xd_tiers_wide.cu", "xd_roof.cu", "xd_noalloc.cu"]
 HEADERS = ["xd_device.cuh", "xd_launch.h", "xd_group.cuh", "xd_sweep.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]

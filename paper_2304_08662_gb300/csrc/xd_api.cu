@@ -243,7 +243,10 @@ struct xd_ctx {
     bool generic_only = false;
     TierConfig tiers{}, tiers_tiny_x{}, tiers_small_x{}, tiers_large_x{}, tiers_protein{};
     TierConfig tiers_latency{}, tiers_latency_mid{}, tiers_latency_prot{};
+    TierConfig tiers_huge{}, tiers_huge_tiny_x{}, tiers_huge_small_x{}, tiers_huge_large_x{};   // DNA launches
+                                                                                           // of >= huge_units sides
     uint32_t latency_units = 0;        // batches with fewer side extensions use tiers_latency
+    uint32_t huge_units = 0;           // launches with at least this many use tiers_huge
     std::vector<TuneEntry> tuned;      // autotuned configurations by (alphabet, X, length) bucket
     const TierConfig* force_tiers = nullptr;   // set while the autotuner times a candidate
     DevBuf stats;                // uint64 [16]: cumulative per-batch counters (see Problem::stats)
@@ -258,7 +261,7 @@ struct xd_ctx {
     // request dispatcher
     bool merge = true;           // merge waiting requests with identical parameters
     uint32_t max_batch_pairs = 1u << 20;
-    uint64_t max_batch_codes = uint64_t(8) << 30;
+    uint64_t max_batch_codes = uint64_t(24) << 30;   // residue bytes of one merged launch
     std::deque<Request*> pending;
     std::unordered_map<uint64_t, Request*> requests;
     std::vector<HostBuf> pinned_cache;
@@ -449,6 +452,11 @@ bool parse_chain(const char* ch, TierConfig& t) {
 // their time is the serial anti-diagonal chain of their longest sides, so they run with a
 // full warp per side from the first level (lower latency per anti-diagonal).
 constexpr uint32_t kLatencyUnits = 65536;
+// Launches with this many side extensions or more (several batches in one pass, or one very
+// large batch) are bound by the total work, not by the serial chains of their longest sides
+// (the bulk of the others overlaps them), so their wide levels use the fewest lanes per
+// side: 4 x 32 and 8 x 32 slots instead of 16 x 16 and 32 x 16.
+constexpr uint32_t kHugeUnits = 1u << 20;
 
 void default_tiers(xd_ctx* c) {
     TierConfig& t = c->tiers;
@@ -509,6 +517,24 @@ void default_tiers(xd_ctx* c) {
     for (TierConfig* tc : {&c->tiers_latency, &c->tiers_latency_mid, &c->tiers_latency_prot})
         tc->blocks_per_sm[kG32C16] = 3;
     c->latency_units = uint32_t(std::max(0, env_int("XD_LATENCY_UNITS", int(kLatencyUnits))));
+    c->huge_units = uint32_t(std::max(0, env_int("XD_HUGE_UNITS", int(kHugeUnits))));
+    // huge DNA launches: 1 x 32 -> 4 x 32 -> 8 x 32 in the three-block grid, then 32 x 32 and
+    // the band tier (measured on ten long-read batches per launch, X = 10 and 20)
+    c->tiers_huge = t;
+    set_chain(c->tiers_huge, {kG1C32, kG4C32, kG8C32, kG32C32});
+    c->tiers_huge.fused_minb = env_int("XD_FUSED_MINB", 3);
+    // every warp starts in the first level (the wide sides wait for the bulk of the narrow ones;
+    // the other batches of the launch cover their chains)
+    c->tiers_huge.every1 = std::max(0, env_int("XD_EVERY1", 0));
+    c->tiers_huge.every2 = std::max(0, env_int("XD_EVERY2", 0));
+    for (int* e : {&c->tiers_huge.every1, &c->tiers_huge.every2})
+        if (*e == 1) *e = 2;
+    c->tiers_huge_small_x = c->tiers_huge;
+    set_chain(c->tiers_huge_small_x, {kG1C24, kG4C32, kG8C32, kG32C32});
+    c->tiers_huge_tiny_x = c->tiers_huge;
+    set_chain(c->tiers_huge_tiny_x, {kG1C20, kG4C32, kG8C32, kG32C32});
+    // X > 30: the chain of large batches (measured faster than the 32-slot wide levels at X = 50)
+    c->tiers_huge_large_x = c->tiers_large_x;
     // overrides for experiments: comma-separated variant ids
     if (const char* ch = std::getenv("XD_CHAIN_PROT")) parse_chain(ch, c->tiers_protein);
     if (const char* ch = std::getenv("XD_CHAIN_SMALL")) {
@@ -518,7 +544,9 @@ void default_tiers(xd_ctx* c) {
     }
     if (const char* ch = std::getenv("XD_CHAIN")) {
         TierConfig forced = t;
-        if (parse_chain(ch, forced)) c->tiers = c->tiers_tiny_x = c->tiers_small_x = c->tiers_large_x = forced;
+        if (parse_chain(ch, forced))
+            c->tiers = c->tiers_tiny_x = c->tiers_small_x = c->tiers_large_x = c->tiers_huge =
+                c->tiers_huge_tiny_x = c->tiers_huge_small_x = c->tiers_huge_large_x = forced;
     }
 }
 
@@ -526,7 +554,7 @@ int x_bucket(int32_t X) { return X <= 15 ? 0 : X <= 30 ? 1 : 2; }
 int len_bucket(uint32_t max_len) { return max_len <= 2048 ? 0 : max_len <= 20000 ? 1 : 2; }
 int size_bucket(uint32_t n_pairs) {
     const uint64_t u = uint64_t(n_pairs) * 2;
-    return u < 8192 ? 0 : u < kLatencyUnits ? 1 : 2;
+    return u < 8192 ? 0 : u < kLatencyUnits ? 1 : u < kHugeUnits ? 2 : 3;
 }
 
 const TierConfig& tiers_for(const xd_ctx* c, const BatchView& b) {
@@ -540,6 +568,9 @@ const TierConfig& tiers_for(const xd_ctx* c, const BatchView& b) {
         return units < c->latency_units / 2 ? c->tiers_latency : c->tiers_latency_mid;
     }
     if (b.alpha == 20) return c->tiers_protein;
+    if (units >= c->huge_units)
+        return b.X <= 12 ? c->tiers_huge_tiny_x : b.X <= 15 ? c->tiers_huge_small_x
+               : b.X <= 30 ? c->tiers_huge : c->tiers_huge_large_x;
     if (b.X <= 12) return c->tiers_tiny_x;
     if (b.X <= 15) return c->tiers_small_x;
     if (b.X <= 30) return c->tiers;
@@ -1028,7 +1059,7 @@ bool parse_entry(const std::string& line, const TierConfig& base, TuneEntry& out
     }
     if (!have_chain) { why = "entry without chain"; return false; }
     if (out.alpha != 4 && out.alpha != 20) { why = "alpha must be 4 or 20"; return false; }
-    if (out.xb < 0 || out.xb > 2 || out.lb < 0 || out.lb > 2 || out.sb < 0 || out.sb > 2) {
+    if (out.xb < 0 || out.xb > 2 || out.lb < 0 || out.lb > 2 || out.sb < 0 || out.sb > 3) {
         why = "bucket out of range";
         return false;
     }
@@ -1869,8 +1900,8 @@ xd_status xd_autotune(xd_ctx* c, const xd_batch* b, const char* path, float* bes
         if (!f) return fail(c, XD_EINVAL, std::string("cannot write tuning table ") + path);
         std::fprintf(f, "# xdrop-gb300 tuning table: alpha (4 DNA, 20 protein), X bucket (0: X <= 15, 1: <= 30,\n"
                         "# 2: more), length bucket (0: longest side <= 2048, 1: <= 20000, 2: more), size bucket\n"
-                        "# (0: < 8192 side extensions, 1: < 65536, 2: more), chain of register-level variants,\n"
-                        "# queue chunk, fused grid and its role mix, measured ms\n");
+                        "# (0: < 8192 side extensions, 1: < 65536, 2: < 1048576, 3: more), chain of register-level\n"
+                        "# variants, queue chunk, fused grid and its role mix, measured ms\n");
         for (const TuneEntry& t : table) std::fprintf(f, "%s\n", format_entry(t).c_str());
         std::fclose(f);
     }

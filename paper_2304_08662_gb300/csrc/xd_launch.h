@@ -73,6 +73,8 @@ cudaError_t launch_fused_levels(const Problem& P, const Queues& Q, const TierCon
 // Levels 0-3 in one grid (four roles); fused_roles(cfg, alpha) is 4 when the variant
 // quadruple is compiled and cfg asks for it, 3 for the triple, else 0.
 int fused_roles(const TierConfig& cfg, int alpha);
+// The fused grids with 32-slot wide levels (xd_tiers_wide.cu).
+cudaError_t launch_fused_wide(const Problem& P, const Queues& Q, const TierConfig& cfg, int n_sm, cudaStream_t st);
 
 // DNA levels (xd_tiers_dna.cu) and protein instantiations (xd_tiers_prot.cu), reached
 // through the launchers above.

@@ -49,7 +49,8 @@ bool fused_supported(const TierConfig& c, int alpha) {
     if (c.n_levels < 3) return false;
     const int a = c.variant[0], b = c.variant[1], d = c.variant[2];
     if (alpha == 20) return fused_supported_prot(a, b, d);
-    return (a == kG1C32 && b == kG4C32 && d == kG8C32) || (a == kG1C32 && b == kG8C16 && d == kG16C16) ||
+    return ((a == kG1C32 || a == kG1C24 || a == kG1C20) && b == kG4C32 && d == kG8C32) ||
+           (a == kG1C32 && b == kG8C16 && d == kG16C16) ||
            (a == kG1C32 && b == kG16C16 && d == kG32C16) || (a == kG1C32 && b == kG8C16 && d == kG32C16) ||
            (a == kG1C16 && b == kG4C16 && d == kG16C16) || (a == kG1C16 && b == kG8C16 && d == kG32C16) ||
            (a == kG4C16 && b == kG16C16 && d == kG32C32) || (a == kG1C32 && b == kG32C8 && d == kG32C16) ||
@@ -101,7 +102,9 @@ cudaError_t launch_fused_levels(const Problem& P, const Queues& Q, const TierCon
     if (fused_roles(cfg, P.alpha) == 4) return launch_fused4_levels(P, Q, cfg, n_sm, st);
     if (P.alpha == 20) return launch_fused_levels_prot(P, Q, cfg, n_sm, st);
     if (!packed_ok(P)) return cudaErrorInvalidValue;   // DNA grids are compiled packed only
-    if (a == kG1C32 && b == kG4C32 && d == kG8C32) return launch_fused<1, 32, 4, 32, 8, 32, 2, kDna16>(P, Q, cfg, n_sm, st);
+    // 32-slot wide levels after a 20-, 24- or 32-slot first level (xd_tiers_wide.cu)
+    if (b == kG4C32 && d == kG8C32 && (a == kG1C32 || a == kG1C24 || a == kG1C20))
+        return launch_fused_wide(P, Q, cfg, n_sm, st);
     if (a == kG1C32 && b == kG8C16 && d == kG16C16) return launch_fused<1, 32, 8, 16, 16, 16, 2, kDna16>(P, Q, cfg, n_sm, st);
     // 128 registers (four blocks per SM, no spills) unless fused_minb asks for three blocks
     if (a == kG1C32 && b == kG16C16 && d == kG32C16)
@@ -116,7 +119,9 @@ cudaError_t launch_fused_levels(const Problem& P, const Queues& Q, const TierCon
     if (a == kG1C24 && b == kG16C16 && d == kG32C16) return launch_fused<1, 24, 16, 16, 32, 16, 2, kDna16, 32, 4>(P, Q, cfg, n_sm, st);
     if (a == kG1C20 && b == kG16C16 && d == kG32C16) return launch_fused<1, 20, 16, 16, 32, 16, 2, kDna16, 32, 4>(P, Q, cfg, n_sm, st);
     if (a == kG1C32 && b == kG8C32 && d == kG32C16) return launch_fused<1, 32, 8, 32, 32, 16, 2, kDna16, 8, 4>(P, Q, cfg, n_sm, st);
-    if (a == kG1C32 && b == kG8C32 && d == kG16C32) return launch_fused<1, 32, 8, 32, 16, 32, 2, kDna16, 8, 4>(P, Q, cfg, n_sm, st);
+    if (a == kG1C32 && b == kG8C32 && d == kG16C32)
+        return cfg.fused_minb == 3 ? launch_fused<1, 32, 8, 32, 16, 32, 3, kDna16>(P, Q, cfg, n_sm, st)
+                                   : launch_fused<1, 32, 8, 32, 16, 32, 2, kDna16, 8, 4>(P, Q, cfg, n_sm, st);
     if (a == kG1C16 && b == kG4C16 && d == kG16C16) return launch_fused<1, 16, 4, 16, 16, 16, 3, kDna16>(P, Q, cfg, n_sm, st);
     if (a == kG1C16 && b == kG8C16 && d == kG32C16) return launch_fused<1, 16, 8, 16, 32, 16, 3, kDna16>(P, Q, cfg, n_sm, st);
     if (a == kG4C16 && b == kG16C16 && d == kG32C32) return launch_fused<4, 16, 16, 16, 32, 32, 2, kDna16, 32, 4>(P, Q, cfg, n_sm, st);

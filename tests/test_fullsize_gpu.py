@@ -144,7 +144,8 @@ def test_full_size_uneven_restricted_all_pairs(ctx, uneven, uneven_unrestricted,
 
 
 def _ctx_env(env):
-    keys = ("XD_FUSED", "XD_FUSED_PROT", "XD_EVERY1", "XD_EVERY2", "XD_EVERY3", "XD_LONG_PERMILLE", "XD_CHAIN")
+    keys = ("XD_FUSED", "XD_FUSED_PROT", "XD_EVERY1", "XD_EVERY2", "XD_EVERY3", "XD_LONG_PERMILLE", "XD_CHAIN",
+            "XD_FUSED_MINB")
     old = {k: os.environ.get(k) for k in keys}
     for k in keys:
         os.environ.pop(k, None)
@@ -159,13 +160,17 @@ def _ctx_env(env):
                 os.environ[k] = v
 
 
-@pytest.mark.parametrize("X,chain", [(10, None), (20, None), (50, None), (20, "1,3,4,5,6")])
-def test_full_size_fused_grid_equals_level_launches(X, chain):
+@pytest.mark.parametrize("X,chain,minb", [(10, None, None), (20, None, None), (50, None, None),
+                                          (20, "1,3,4,5,6", None), (20, "1,7,8,6", "3"), (10, "1,7,8,6", "3"),
+                                          (50, "1,7,8,6", "3")])
+def test_full_size_fused_grid_equals_level_launches(X, chain, minb):
     """Every one of the 100,000 long-read pairs: the persistent grid whose warps run
     different group shapes at once (and the long-side role) must give exactly the results of
     one launch per register level; also the four-role grid (windows 32, 128, 256, 512)."""
     b = synth.dna_longread().with_params(X=X)
     extra = {"XD_CHAIN": chain, "XD_EVERY3": "8"} if chain else {}
+    if minb:
+        extra["XD_FUSED_MINB"] = minb
     fused = _ctx_env({"XD_EVERY1": "2", "XD_EVERY2": "4", "XD_LONG_PERMILLE": "5", **extra})
     split = _ctx_env({"XD_FUSED": "0", **({"XD_CHAIN": chain} if chain else {})})
     try:
@@ -176,3 +181,25 @@ def test_full_size_fused_grid_equals_level_launches(X, chain):
         xdrop.xd_destroy(split)
     diff = np.nonzero((a.view(np.uint8).reshape(len(a), -1) != c.view(np.uint8).reshape(len(c), -1)).any(axis=1))[0]
     assert diff.size == 0, f"{diff.size} pairs differ, first {diff[:10].tolist()}"
+
+
+@pytest.mark.parametrize("X", [10, 20])
+def test_full_size_longread_ten_batches_per_launch_all_pairs(ctx, oracle_all, X):
+    """Ten long-read batches of 100,000 pairs in one pass (xd_run_device_many), the launch
+    the bench times by default: every pair of every batch against the oracle."""
+    b = synth.dna_longread().with_params(X=X)
+    dev = torch.device("cuda", 0)
+    keep = [torch.from_numpy(b.codes).to(dev), torch.from_numpy(b.offsets.view(np.int64)).to(dev),
+            torch.from_numpy(b.lengths.view(np.int32)).to(dev),
+            torch.from_numpy(np.ascontiguousarray(b.pairs).view(np.int32)).to(dev)]
+    args = xdrop.BatchArgs(b.alphabet, *keep, b.match, b.mismatch, b.gap, b.matrix, b.X, b.delta)
+    k = 10
+    out = torch.zeros(k * b.n_pairs * xdrop.RESULT_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    xdrop.xd_reserve(ctx, k * b.codes.size, k * b.n_seqs, k * b.n_pairs, int(b.lengths.max()))
+    xdrop.xd_run_device_many(ctx, [args] * k, out, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert xdrop.xd_device_status(ctx) == 0
+    res = out.cpu().numpy().view(xdrop.RESULT_DTYPE)
+    ref = oracle_all(b)
+    for j in range(k):
+        _all_parity(res[j * b.n_pairs:(j + 1) * b.n_pairs].copy(), b, ref)

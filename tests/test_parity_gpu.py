@@ -31,9 +31,12 @@ MODES = {"tiered": {}, "generic": {"XD_TIERS": "generic"},
          "throughput": {"XD_LATENCY_UNITS": "0"},
          "split": {"XD_LATENCY_UNITS": "0", "XD_FUSED": "0"},
          # DNA through the four-role fused grid (windows 32, 128, 256, 512)
-         "four_roles": {"XD_LATENCY_UNITS": "0", "XD_CHAIN": "1,3,4,5,6", "XD_EVERY1": "16"}}
+         "four_roles": {"XD_LATENCY_UNITS": "0", "XD_CHAIN": "1,3,4,5,6", "XD_EVERY1": "16"},
+         # the chains of launches with a million or more sides (1 x 32, 4 x 32, 8 x 32 in the
+         # three-block grid, then 32 x 32), here on every batch size
+         "huge": {"XD_LATENCY_UNITS": "0", "XD_HUGE_UNITS": "0", "XD_EVERY1": "4"}}
 ENV_KEYS = ("XD_TIERS", "XD_FUSED", "XD_FUSED_PROT", "XD_LATENCY_UNITS", "XD_CHAIN", "XD_CHAIN_PROT",
-            "XD_CHAIN_SMALL", "XD_EVERY1")
+            "XD_CHAIN_SMALL", "XD_EVERY1", "XD_HUGE_UNITS")
 
 
 def _ctx(mode, env=None):
@@ -52,7 +55,7 @@ def _ctx(mode, env=None):
                 os.environ[k] = v
 
 
-@pytest.fixture(scope="module", params=["tiered", "throughput", "split", "generic", "four_roles"])
+@pytest.fixture(scope="module", params=["tiered", "throughput", "split", "generic", "four_roles", "huge"])
 def ctx(request):
     c = _ctx(request.param)
     yield c
