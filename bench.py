@@ -89,6 +89,8 @@ def parse():
                     help="seed tuples per overlap on the same reads (dna_longread only)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the short record of the other workloads (configs sub-object)")
     ap.add_argument("--cpu-pairs", type=int, default=100_000,
                     help="oracle sample of the cpu_baseline (about 10 s on 16 cores for the long-read "
                          "workload); the reference arm times a quarter of it per step")
@@ -222,6 +224,108 @@ class Clocks:
                 "sm_max_mhz": max(mx) if mx else None,
                 "power_w_max": max(power) if power else None,
                 "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------- per-config record
+
+CONFIG_SET = [("dna_tiny", {}), ("dna_longread", {"X": 10}), ("dna_longread", {"X": 50}),
+              ("protein", {}), ("uneven", {"delta": 0}), ("uneven", {"delta": 256}),
+              ("uneven", {"delta": 1024}), ("uneven", {"delta": 4096})]
+
+
+def device_args(xdrop, torch, dev, b):
+    keep = [torch.from_numpy(b.codes).to(dev), torch.from_numpy(b.offsets.view(np.int64)).to(dev),
+            torch.from_numpy(b.lengths.view(np.int32)).to(dev),
+            torch.from_numpy(np.ascontiguousarray(b.pairs).view(np.int32)).to(dev)]
+    return xdrop.BatchArgs(b.alphabet, *keep, b.match, b.mismatch, b.gap, b.matrix, b.X, b.delta)
+
+
+def config_record(xdrop, torch, ctx, dev, b, bpl, launches, oracle_pairs, peak_16, peak_32):
+    """Short measurement of one workload: one batch per launch and bpl batches per launch
+    (device-resident inputs, CUDA events on the launching stream), the dominant stage's
+    fraction of the integer roofline, and the oracle on a bounded sample."""
+    stream = torch.cuda.current_stream(dev)
+    args = device_args(xdrop, torch, dev, b)
+    out = torch.zeros(bpl * b.n_pairs * xdrop.RESULT_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    xdrop.xd_reserve(ctx, bpl * b.codes.size, bpl * b.n_seqs, bpl * b.n_pairs, int(b.lengths.max()))
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rec = {"pairs": b.n_pairs, "X": b.X, "delta_b": b.delta, "batches_per_launch": bpl}
+    # one batch per launch
+    for _ in range(3):
+        xdrop.xd_run_device(ctx, args, out, stream.cuda_stream)
+    torch.cuda.synchronize(dev)
+    if xdrop.xd_device_status(ctx) != 0:
+        raise RuntimeError(f"device validation failed for {b.name}")
+    res = out[:b.n_pairs * xdrop.RESULT_DTYPE.itemsize].cpu().numpy().view(xdrop.RESULT_DTYPE)
+    cells = float(res["left"]["cells"].sum() + res["right"]["cells"].sum())
+    ev0.record(stream)
+    for _ in range(3):
+        xdrop.xd_run_device(ctx, args, out, stream.cuda_stream)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    single_ms = ev0.elapsed_time(ev1) / 3
+    rec["single_batch"] = {"ms_per_batch": single_ms, "gcups": cells / (single_ms * 1e-3) / 1e9,
+                           "pairs_per_s": b.n_pairs / (single_ms * 1e-3)}
+    # bpl batches per launch, timed with the stage events
+    xdrop.xd_run_device_many(ctx, [args] * bpl, out, stream.cuda_stream)
+    torch.cuda.synchronize(dev)
+    xdrop.xd_set_timing(ctx, True)
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    for _ in range(launches):
+        xdrop.xd_run_device_many(ctx, [args] * bpl, out, stream.cuda_stream)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    tim = xdrop.xd_get_timing(ctx)
+    xdrop.xd_set_timing(ctx, False)
+    if xdrop.xd_device_status(ctx) != 0:
+        raise RuntimeError(f"device validation failed for {b.name}")
+    got = out.cpu().numpy().view(xdrop.RESULT_DTYPE)
+    for k in range(bpl):
+        if not np.array_equal(got[k * b.n_pairs:(k + 1) * b.n_pairs], res):
+            raise RuntimeError(f"{b.name}: batch {k} of a shared launch differs from its single-batch run")
+    ms = ev0.elapsed_time(ev1) / (launches * bpl)
+    nb = max(1, tim["batches"])
+    tier_ms = [x / nb for x in tim["tier_ms"]]
+    top = int(np.argmax(tier_ms))
+    top_cells = tim["tier_cells"][top] / nb
+    packed = packed_scores(b)
+    peak = peak_16 if packed else peak_32
+    achieved = ALG_OPS_PER_CELL * top_cells / (tier_ms[top] * 1e-3) / 1e12 if tier_ms[top] > 0 else 0.0
+    rec.update({"gcups": cells / (ms * 1e-3) / 1e9, "pairs_per_s": b.n_pairs / (ms * 1e-3), "ms_per_batch": ms,
+                "paper_gcups": paper_cells(b) / (ms * 1e-3) / 1e9, "cells_per_batch": cells,
+                "roofline_frac": achieved / peak if peak else None, "dominant_stage_ms_per_launch": tier_ms[top],
+                "dtype": "int16" if packed else "int32",
+                "register_window_fill": (tim["register_band_cells"] / tim["register_slot_cells"]
+                                         if tim["register_slot_cells"] else None)})
+    del args, out
+    if oracle_pairs:
+        c, dt, n = cpu_oracle(b, oracle_pairs, os.cpu_count() or 1)
+        rec["cpu_baseline"] = {"value": c / dt / 1e9, "unit": "GCUPS", "cores": os.cpu_count() or 1, "kind": "oracle",
+                               "sample": f"{n} seeded-random pairs ({c:.3g} cells, {dt:.1f} s)"}
+    return rec
+
+
+def configs_bench(xdrop, torch, ctx, dev, bpl, peak_16, peak_32, headline):
+    """The other workloads, a few launches each; the headline's batch object is reused for
+    its X variants."""
+    out = {}
+    uneven = None
+    for name, kw in CONFIG_SET:
+        if name == "dna_longread":
+            b = headline.with_params(X=kw["X"])
+        elif name == "uneven":
+            uneven = uneven if uneven is not None else synth.uneven()
+            b = uneven.with_params(delta=kw["delta"])
+        else:
+            b = synth.WORKLOADS[name]()
+        k = f"{name}_{b.n_pairs}_x{b.X}" + (f"_delta{b.delta}" if b.delta else "")
+        # large batches need fewer batches per launch to fill the GPU; the oracle sample is
+        # sized to a few seconds of host work
+        per = bpl if b.n_pairs <= 200_000 else max(1, bpl // 5)
+        sample = {"dna_tiny": 1000, "protein": 50_000, "uneven": 5000}.get(name, 20_000)
+        out[k] = config_record(xdrop, torch, ctx, dev, b, per, 2, sample, peak_16, peak_32)
+    return out
 
 
 # ----------------------------------------------------------------------------- serving
@@ -540,7 +644,9 @@ def main():
         sm_max = float(peaks.get("sm_max_mhz", 2070.0))
         packed = packed_scores(b)
         width = 2 if packed else 1    # 16-bit lanes per ALU lane
-        peak = width * props.multi_processor_count * ALU_LANES_PER_SM * sm_max * 1e6 / 1e12
+        peak32 = props.multi_processor_count * ALU_LANES_PER_SM * sm_max * 1e6 / 1e12
+        peak16 = 2 * peak32
+        peak = width * peak32
         # measured in this run: the ALU pipe's issue rate (max, or max on 16x2) and the tiers'
         # own cell update
         alu_meas = width * xdrop.xd_probe(ctx, "max_16x2" if packed else "max") / 1e12
@@ -607,6 +713,10 @@ def main():
         if rank == 0 and not a.no_cpu:
             cpu = cpu_baseline(b, a.cpu_pairs, os.cpu_count() or 1)
 
+        configs = None
+        if rank == 0 and not a.no_configs and a.workload == "dna_longread" and a.pairs is None and a.x is None:
+            configs = configs_bench(xdrop, torch, ctx, dev, bpl, peak16, peak32, b)
+
         if rank == 0:
             line = {"metric": "GCUPS", "value": value, "unit": "GCUPS", "n_gpus": world,
                     "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
@@ -629,6 +739,7 @@ def main():
                     "register_window_fill": (tim["register_band_cells"] / tim["register_slot_cells"]
                                              if tim["register_slot_cells"] else None),
                     "serving": serving,
+                    "configs": configs,
                     "clocks": clk}
             print(json.dumps(line), flush=True)
     finally:

@@ -316,8 +316,9 @@ xd_status xd_probe(xd_ctx* ctx, int32_t op, double* rate);
  * configuration for a class of batches).  Runs the host batch `sample` (pointers as for
  * xd_submit_batch) under candidate configurations -- the register-level chain (lanes per
  * side extension and window of every level, i.e. threads per alignment and band tile
- * width), the queue chunk of single-lane levels (1 - 64), the long-side head of the
- * persistent grid and its role mix -- three runs each on a stream of its own, and keeps the
+ * width), the queue chunk of single-lane levels (1 - 64), the band tier's warps per side
+ * (1 - 32, i.e. 32 - 1024 threads per alignment of the widest bands), the long-side head of
+ * the persistent grid and its role mix -- three runs each on a stream of its own, and keeps the
  * fastest for the sample's bucket: alphabet x X (<= 15, <= 30, more) x longest side
  * (<= 2,048, <= 20,000, more) x size (< 8,192, < 65,536, < 1,048,576, more side extensions
  * in one launch).  Every

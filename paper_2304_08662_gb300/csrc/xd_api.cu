@@ -481,6 +481,7 @@ void default_tiers(xd_ctx* c) {
     // failure-detection tests: a short wait limit and a producer that never finishes
     t.wait_limit_ms = std::max(0, env_int("XD_TEST_WAIT_MS", 0));
     t.phantom_producer = env_int("XD_TEST_PHANTOM_PRODUCER", 0) != 0;
+    t.band_warps = env_int("XD_BAND_WARPS", 8);
     set_chain(t, {kG1C32, kG16C16, kG32C16, kG32C32});
     // X <= 15: narrower first windows (measured at X = 10: 20 slots 195, 24 slots 184,
     // 32 slots 152 GCUPS); 20 slots up to X = 12, 24 slots up to X = 15
@@ -708,7 +709,7 @@ xd_status run_pipeline(xd_ctx* c, Scratch& s, const BatchView* bs, int nb, xd_re
                 if (lv == 0) XD_CUDA(c, mark(4));
                 launches += 1;
             }
-            XD_CUDA(c, launch_band(P, Q, c->n_sm, st));
+            XD_CUDA(c, launch_band(P, Q, c->n_sm, tc.band_warps, st));
             launches += 1;
             XD_CUDA(c, mark(5));
         }
@@ -1008,9 +1009,9 @@ std::string format_entry(const TuneEntry& t) {
     char buf[256];
     std::snprintf(buf, sizeof(buf),
                   "alpha=%d xb=%d lb=%d sb=%d chain=%s chunk=%d fused=%d every1=%d every2=%d every3=%d minb=%d long=%d "
-                  "ms=%.4f",
+                  "band=%d ms=%.4f",
                   t.alpha, t.xb, t.lb, t.sb, chain.c_str(), t.cfg.chunk, t.cfg.fused ? 1 : 0, t.cfg.every1,
-                  t.cfg.every2, t.cfg.every3, t.cfg.fused_minb, t.cfg.long_permille, double(t.ms));
+                  t.cfg.every2, t.cfg.every3, t.cfg.fused_minb, t.cfg.long_permille, t.cfg.band_warps, double(t.ms));
     return buf;
 }
 
@@ -1054,6 +1055,7 @@ bool parse_entry(const std::string& line, const TierConfig& base, TuneEntry& out
             else if (k == "every3") out.cfg.every3 = x == 1 ? 2 : std::max(0, x);
             else if (k == "minb") out.cfg.fused_minb = x;
             else if (k == "long") out.cfg.long_permille = std::max(0, std::min(250, x));
+            else if (k == "band") out.cfg.band_warps = x;
             else if (k == "ms") out.ms = float(std::atof(v.c_str()));
         }
     }
@@ -1865,6 +1867,13 @@ xd_status xd_autotune(xd_ctx* c, const xd_batch* b, const char* path, float* bes
         for (int ch : {2, 4, 8, 16, 32, 64}) {
             TierConfig cand = best.cfg;
             cand.chunk = ch;
+            if (r == XD_OK) r = consider(cand);
+        }
+    // the band tier's warps per side: 32 - 1024 threads per alignment of the widest bands
+    if (r == XD_OK)
+        for (int nw : {1, 2, 4, 16, 32}) {
+            TierConfig cand = best.cfg;
+            cand.band_warps = nw;
             if (r == XD_OK) r = consider(cand);
         }
     if (r == XD_OK && best.cfg.fused)

@@ -542,17 +542,33 @@ cudaError_t launch_generic(const Problem& P, const Queues& Q, int32_t* scratch,
     return cudaGetLastError();
 }
 
-cudaError_t launch_band(const Problem& P, const Queues& Q, int n_sm, cudaStream_t st) {
-    constexpr int NW = kBandWarps;
+template <int NW>
+static cudaError_t launch_band_nw(const Problem& P, const Queues& Q, int n_sm, cudaStream_t st) {
     const size_t smem = (416 + 8 * NW + 2 * size_t(kBandW)) * sizeof(int32_t);
-    static bool attr = false;
-    if (!attr) {
+    static int per_sm = 0;
+    if (per_sm == 0) {
         cudaError_t e = cudaFuncSetAttribute(k_band<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (e != cudaSuccess) return e;
-        attr = true;
+        e = cudaFuncSetAttribute(k_band<NW>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_band<NW>, 32 * NW, smem);
+        if (e != cudaSuccess) return e;
+        per_sm = per_sm < 1 ? 1 : per_sm;
     }
-    k_band<NW><<<n_sm, 32 * NW, smem, st>>>(P, Q);
+    // blocks that pull sides from the band queue: as many as fit (the queue decides the work)
+    k_band<NW><<<n_sm * per_sm, 32 * NW, smem, st>>>(P, Q);
     return cudaGetLastError();
+}
+
+cudaError_t launch_band(const Problem& P, const Queues& Q, int n_sm, int nw, cudaStream_t st) {
+    switch (nw) {
+        case 1: return launch_band_nw<1>(P, Q, n_sm, st);
+        case 2: return launch_band_nw<2>(P, Q, n_sm, st);
+        case 4: return launch_band_nw<4>(P, Q, n_sm, st);
+        case 16: return launch_band_nw<16>(P, Q, n_sm, st);
+        case 32: return launch_band_nw<32>(P, Q, n_sm, st);
+        default: return launch_band_nw<kBandWarps>(P, Q, n_sm, st);
+    }
 }
 
 cudaError_t launch_totals(const xd_pair* pairs, uint32_t n_pairs, const uint64_t* offsets,

@@ -23,7 +23,8 @@ cudaError_t launch_order(uint32_t* hist, uint32_t* ctr, int n_ctr, const uint32_
 cudaError_t launch_route_all_generic(const Queues& Q, cudaStream_t st);
 cudaError_t launch_generic(const Problem& P, const Queues& Q, int32_t* scratch,
                            uint64_t stride, int n_blocks, cudaStream_t st);
-cudaError_t launch_band(const Problem& P, const Queues& Q, int n_sm, cudaStream_t st);
+// Band tier with nw warps per side (1, 2, 4, 8, 16 or 32: 32 - 1024 threads per alignment).
+cudaError_t launch_band(const Problem& P, const Queues& Q, int n_sm, int nw, cudaStream_t st);
 cudaError_t launch_totals(const xd_pair* pairs, uint32_t n_pairs, const uint64_t* offsets,
                           const uint32_t* lengths, uint32_t n_seqs, uint64_t n_res, uint32_t pair_base,
                           uint64_t res_base, const Problem& P, cudaStream_t st);
@@ -56,6 +57,7 @@ struct TierConfig {
     int long_shape;                     // their groups: 0 = 32 lanes x 4 slots, 1 = 8 x 4, 2 = 4 x 8
     int wait_limit_ms;                  // fused grid: live-queue wait limit (0 = default, 10 s)
     bool phantom_producer;              // failure-detection test: one producer never finishes
+    int band_warps;                     // band tier: warps per side (1 - 32; 0 = default 8)
 };
 
 // Runs register level `level` of the chain: pulls the cost-ordered list (level 0) or

@@ -49,7 +49,8 @@ bool fused_supported(const TierConfig& c, int alpha) {
     if (c.n_levels < 3) return false;
     const int a = c.variant[0], b = c.variant[1], d = c.variant[2];
     if (alpha == 20) return fused_supported_prot(a, b, d);
-    return ((a == kG1C32 || a == kG1C24 || a == kG1C20) && b == kG4C32 && d == kG8C32) ||
+    return ((a == kG1C32 || a == kG1C24 || a == kG1C20 || a == kG1C16) && b == kG4C32 && d == kG8C32) ||
+           (a == kG1C16 && b == kG2C32 && d == kG8C32) ||
            (a == kG1C32 && b == kG8C16 && d == kG16C16) ||
            (a == kG1C32 && b == kG16C16 && d == kG32C16) || (a == kG1C32 && b == kG8C16 && d == kG32C16) ||
            (a == kG1C16 && b == kG4C16 && d == kG16C16) || (a == kG1C16 && b == kG8C16 && d == kG32C16) ||
@@ -103,7 +104,8 @@ cudaError_t launch_fused_levels(const Problem& P, const Queues& Q, const TierCon
     if (P.alpha == 20) return launch_fused_levels_prot(P, Q, cfg, n_sm, st);
     if (!packed_ok(P)) return cudaErrorInvalidValue;   // DNA grids are compiled packed only
     // 32-slot wide levels after a 20-, 24- or 32-slot first level (xd_tiers_wide.cu)
-    if (b == kG4C32 && d == kG8C32 && (a == kG1C32 || a == kG1C24 || a == kG1C20))
+    if ((b == kG4C32 && d == kG8C32 && (a == kG1C32 || a == kG1C24 || a == kG1C20 || a == kG1C16)) ||
+        (a == kG1C16 && b == kG2C32 && d == kG8C32))
         return launch_fused_wide(P, Q, cfg, n_sm, st);
     if (a == kG1C32 && b == kG8C16 && d == kG16C16) return launch_fused<1, 32, 8, 16, 16, 16, 2, kDna16>(P, Q, cfg, n_sm, st);
     // 128 registers (four blocks per SM, no spills) unless fused_minb asks for three blocks

@@ -1,6 +1,6 @@
 // Register tiers: fused DNA grids (16-bit packed scores) whose wide levels have 32 slots per
-// lane -- 1 x 20 / 1 x 24 / 1 x 32 -> 4 x 32 -> 8 x 32 (windows 128 and 256 for the wide sides,
-// with the fewest lanes per side).  These are the chains of launches whose time is set by the
+// lane -- 1 x 16 / 1 x 20 / 1 x 24 / 1 x 32 -> 4 x 32 -> 8 x 32 (windows 128 and 256 for the wide
+// sides, with the fewest lanes per side), and 1 x 16 -> 2 x 32 -> 8 x 32.  These are the chains of launches whose time is set by the
 // total work; they need 166-168 registers, built for three blocks per SM (and the 1 x 32 one
 // also for two).
 #include "xd_group.cuh"
@@ -9,7 +9,9 @@ namespace xd {
 
 cudaError_t launch_fused_wide(const Problem& P, const Queues& Q, const TierConfig& cfg, int n_sm, cudaStream_t st) {
     if (!packed_ok(P) || P.alpha != 4) return cudaErrorInvalidValue;
-    const int a = cfg.variant[0];
+    const int a = cfg.variant[0], b = cfg.variant[1];
+    if (a == kG1C16 && b == kG2C32) return launch_fused<1, 16, 2, 32, 8, 32, 3, kDna16>(P, Q, cfg, n_sm, st);
+    if (a == kG1C16) return launch_fused<1, 16, 4, 32, 8, 32, 3, kDna16>(P, Q, cfg, n_sm, st);
     if (a == kG1C20) return launch_fused<1, 20, 4, 32, 8, 32, 3, kDna16>(P, Q, cfg, n_sm, st);
     if (a == kG1C24) return launch_fused<1, 24, 4, 32, 8, 32, 3, kDna16>(P, Q, cfg, n_sm, st);
     return cfg.fused_minb == 3 ? launch_fused<1, 32, 4, 32, 8, 32, 3, kDna16>(P, Q, cfg, n_sm, st)

@@ -36,7 +36,7 @@ MODES = {"tiered": {}, "generic": {"XD_TIERS": "generic"},
          # three-block grid, then 32 x 32), here on every batch size
          "huge": {"XD_LATENCY_UNITS": "0", "XD_HUGE_UNITS": "0", "XD_EVERY1": "4"}}
 ENV_KEYS = ("XD_TIERS", "XD_FUSED", "XD_FUSED_PROT", "XD_LATENCY_UNITS", "XD_CHAIN", "XD_CHAIN_PROT",
-            "XD_CHAIN_SMALL", "XD_EVERY1", "XD_HUGE_UNITS")
+            "XD_CHAIN_SMALL", "XD_EVERY1", "XD_HUGE_UNITS", "XD_BAND_WARPS")
 
 
 def _ctx(mode, env=None):
@@ -235,6 +235,19 @@ def test_every_variant_chain(chain_batches, chain, fused):
     c = _ctx("tiered", env)
     try:
         for b in chain_batches[1 if prot else 0]:
+            assert_parity(xdrop.extend_host(c, b), b)
+    finally:
+        xdrop.xd_destroy(c)
+
+
+@pytest.mark.parametrize("nw", ["1", "2", "4", "16", "32"])
+def test_band_tier_warps_per_side(chain_batches, nw):
+    """The band tier with 1 - 32 warps per side (32 - 1024 threads per alignment): with a
+    single 16-slot register level most sides reach it."""
+    env = {"XD_LATENCY_UNITS": "0", "XD_CHAIN": "0", "XD_CHAIN_PROT": "0", "XD_BAND_WARPS": nw}
+    c = _ctx("tiered", env)
+    try:
+        for b in chain_batches[0] + chain_batches[1]:
             assert_parity(xdrop.extend_host(c, b), b)
     finally:
         xdrop.xd_destroy(c)
