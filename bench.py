@@ -45,11 +45,15 @@ SM_COUNT_GB300 = 152
 # (and protein) register levels compute on 16-bit halves (16x2 DPX at the same instruction
 # rate) when the scores allow, so their peak counts two 16-bit lanes per ALU lane.
 ALU_LANES_PER_SM = 64
-# DRAM bytes (read + write) of one launch of the dominant kernel, from one ncu capture of the
-# same workload and kernel build (profiles/k_fused_dna_longread_100k_x20.md); reported as
-# roofline.traffic only for that workload with the default configuration, and only while
-# the kernel is the build the counters were taken on (empty: the kernel has changed since).
-DOMINANT_KERNEL_TRAFFIC = {}
+# DRAM bytes (read + write) per computed cell of the dominant kernel, from one ncu capture of
+# the same kernel build on the same workload (profiles/k_fused_dna_longread_100k_x20.md: the
+# fused grid of ten-batch launches, 1 x 32 -> 4 x 32 -> 8 x 32, captured on 40,000 pairs);
+# roofline.traffic = that figure x the cells of one launch.  Reported only for that workload
+# with the default configuration, and only while the kernel is the build the counters were
+# taken on (empty: the kernel has changed since).
+DOMINANT_KERNEL_TRAFFIC_PER_CELL = {
+    ("dna_longread_100000_x20", 10): (92_092_928 + 6_771_200) / 8_761_163_347,
+}
 
 
 def save_trace(path, tr):
@@ -655,9 +659,13 @@ def main():
         tier_names = ["first register launch (fused persistent grid of levels 0-2, or level 0)",
                       "later register levels and band tier", "generic tier"]
         tuned_env = any(k.startswith("XD_") for k in os.environ)
-        traffic = None if tuned_env else DOMINANT_KERNEL_TRAFFIC.get(workload_config(a, b)["workload"])
+        per_cell = None if tuned_env else DOMINANT_KERNEL_TRAFFIC_PER_CELL.get((workload_config(a, b)["workload"], bpl))
+        traffic = per_cell * top_cells if per_cell else None   # bytes per launch
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                     "frac": achieved / peak if peak else None, "traffic": traffic,
+                    "traffic_basis": ("dram__bytes_read.sum + dram__bytes_write.sum per computed cell of the same "
+                                      "kernel build (ncu, 40,000 pairs) x the launch's cells") if traffic else None,
+                    "achieved_hbm_gbs": traffic / (tier_ms[top] * 1e-3) / 1e9 if traffic else None,
                     "kernel": tier_names[top], "ops_per_cell": ALG_OPS_PER_CELL,
                     "peak_basis": f"{props.multi_processor_count} SMs x {ALU_LANES_PER_SM} integer ALU-pipe "
                                   f"lanes x {width} ({'16-bit halves' if packed else '32-bit'}) x "
@@ -675,11 +683,10 @@ def main():
         if not a.no_e2e:
             hargs = xdrop.BatchArgs.from_host(b)
             hout = np.zeros(b.n_pairs, dtype=xdrop.RESULT_DTYPE)
-            # several batches in flight (as many as a device launch holds, at least two): the
-            # dispatcher merges waiting batches into shared launches, and the next batches'
-            # staging copies and uploads overlap the current launch (every copy stays inside
-            # the timed region)
-            in_flight = max(2, min(bpl, 6, a.steps))   # at most 6: their pinned staging stays cached
+            # two batches in flight: the next batch's host staging and upload overlap the
+            # current one's launch (every copy stays inside the timed region); the host-side
+            # staging copy, not the device, sets this rate
+            in_flight = 2
 
             def e2e_pass(n):
                 pending = []

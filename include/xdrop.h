@@ -91,7 +91,12 @@ typedef struct {
  * a host pointer; for xd_run_device, seq_codes, seq_offsets, seq_lengths and pairs are
  * device pointers (scoring.matrix20x20 stays a host pointer).  n_codes is the length of
  * seq_codes in bytes.  X >= 0; X >= 2^30 means no pruning (X = infinity).  delta_b = 0
- * runs the unrestricted method, delta_b >= 1 the memory-restricted window of Sec. 3. */
+ * runs the unrestricted method, delta_b >= 1 the memory-restricted window of Sec. 3.
+ * z_drop = 0 runs X-Drop alone; z_drop > 0 adds the Z-Drop rule that Sec. 1 names among the
+ * X-Drop variants, in minimap2's definition: after each anti-diagonal, with (i', j') the
+ * best cell so far and (i, j) the anti-diagonal's best live cell (lowest i on ties), the
+ * side stops when S(i', j') - S(i, j) > z_drop + |gap| |(i - i') - (j - j')|; its result is
+ * the best cell up to that anti-diagonal and carries flags bit 1. */
 typedef struct {
     xd_alphabet alpha;
     uint32_t n_seqs;
@@ -104,10 +109,11 @@ typedef struct {
     xd_scoring scoring;
     int32_t X;
     uint32_t delta_b;
+    int32_t z_drop;
 } xd_batch;
 
 /* Result of one side.  flags bit 0: the memory-restricted window was exceeded at least
- * once (the band was clipped to delta_b cells). */
+ * once (the band was clipped to delta_b cells); bit 1: the Z-Drop rule ended the side. */
 typedef struct {
     int32_t score;
     uint32_t h_ext, v_ext;
@@ -178,6 +184,7 @@ typedef struct {
     xd_scoring scoring;
     int32_t X;
     uint32_t delta_b;
+    int32_t z_drop;
 } xd_pairs_batch;
 
 /* As xd_submit_batch, but only the seed tuples travel: the sequences are already resident.

@@ -16,6 +16,10 @@ Parity status of each function (what pins it, all in ``tests/test_oracle_pins.py
                    unrestricted without overflow; hand-derived traces in tests/golden.
                    The end-cell tie-break and the band rule are fixed readings (R3, R4);
                    between alternative readings they are pinned only by the hand traces.
+  * orc_extend_z (Z-Drop, z > 0) -- pinned: against a dense-matrix restatement of the same
+                   rules on random small inputs (several Z), equal to orc_extend when Z is
+                   never reached, and identical sequences never trigger it.  Mutants of the
+                   Z test are caught.
   * orc_batch   -- pinned through orc_extend plus the seed-score closed form: for DNA
                    (pin_pair_total, pin_left_is_right_on_reversed) and for protein
                    (pin_protein_batch: each side against orc_extend with a BLOSUM62 table
@@ -68,6 +72,13 @@ def load(so=None):
                               ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P,
                               ctypes.c_int32, ctypes.c_uint32, P, P, P]
     lib.orc_batch.restype = ctypes.c_int
+    lib.orc_extend_z.argtypes = [P, ctypes.c_int64, ctypes.c_int64, P, ctypes.c_int64, ctypes.c_int64,
+                                 P, ctypes.c_int, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32, ctypes.c_int32, P]
+    lib.orc_extend_z.restype = ctypes.c_int
+    lib.orc_batch_z.argtypes = [ctypes.c_int, P, P, P, P, ctypes.c_uint64, ctypes.c_uint64,
+                                ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P,
+                                ctypes.c_int32, ctypes.c_uint32, ctypes.c_int32, P, P, P]
+    lib.orc_batch_z.restype = ctypes.c_int
     if so == _SO:
         _LIB = lib
     return lib
@@ -86,8 +97,9 @@ def sim_table(alphabet, match=1, mismatch=-1, matrix=None):
     return np.ascontiguousarray(np.asarray(matrix, dtype=np.int32).reshape(20, 20))
 
 
-def extend(h_side, v_side, sim, gap, X, delta=0, lib=None):
-    """One side extension on already-oriented side strings (codes as uint8 arrays).
+def extend(h_side, v_side, sim, gap, X, delta=0, lib=None, zdrop=0):
+    """One side extension on already-oriented side strings (codes as uint8 arrays);
+    zdrop > 0 adds the Z-Drop rule with Z = zdrop.
 
     Returns a dict with score, h_ext, v_ext, flags, cells."""
     lib = lib or load()
@@ -97,8 +109,12 @@ def extend(h_side, v_side, sim, gap, X, delta=0, lib=None):
     hb = h if h.size else np.zeros(1, np.uint8)
     vb = v if v.size else np.zeros(1, np.uint8)
     out = np.zeros(1, dtype=SIDE_DTYPE)
-    rc = lib.orc_extend(_p(hb), 1, h.size, _p(vb), 1, v.size, _p(sim), sim.shape[0],
-                        int(gap), int(X), int(delta), _p(out))
+    if zdrop:
+        rc = lib.orc_extend_z(_p(hb), 1, h.size, _p(vb), 1, v.size, _p(sim), sim.shape[0],
+                              int(gap), int(X), int(delta), int(zdrop), _p(out))
+    else:
+        rc = lib.orc_extend(_p(hb), 1, h.size, _p(vb), 1, v.size, _p(sim), sim.shape[0],
+                            int(gap), int(X), int(delta), _p(out))
     if rc != 0:
         raise RuntimeError(f"orc_extend failed ({rc})")
     r = out[0]
@@ -123,11 +139,19 @@ def run_batch(batch, first=0, count=None, threads=1, lib=None):
     right = np.zeros(batch.n_pairs, dtype=SIDE_DTYPE)
     total = np.zeros(batch.n_pairs, dtype=np.int64)
 
+    zdrop = int(getattr(batch, "zdrop", 0) or 0)
+
     def work(lo, hi):
-        rc = lib.orc_batch(alpha, _p(codes), _p(offs), _p(lens), _p(pairs), lo, hi - lo,
-                           batch.match, batch.mismatch, batch.gap,
-                           None if matrix is None else _p(matrix), batch.X, batch.delta,
-                           _p(left), _p(right), _p(total))
+        if zdrop:
+            rc = lib.orc_batch_z(alpha, _p(codes), _p(offs), _p(lens), _p(pairs), lo, hi - lo,
+                                 batch.match, batch.mismatch, batch.gap,
+                                 None if matrix is None else _p(matrix), batch.X, batch.delta, zdrop,
+                                 _p(left), _p(right), _p(total))
+        else:
+            rc = lib.orc_batch(alpha, _p(codes), _p(offs), _p(lens), _p(pairs), lo, hi - lo,
+                               batch.match, batch.mismatch, batch.gap,
+                               None if matrix is None else _p(matrix), batch.X, batch.delta,
+                               _p(left), _p(right), _p(total))
         if rc != 0:
             raise RuntimeError(f"orc_batch failed ({rc})")
 

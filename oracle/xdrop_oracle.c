@@ -24,6 +24,13 @@
  *   - Left/right extension: each seed splits a pair into a right extension read forward
  *     from the seed end and a left extension read backward from the seed start, through
  *     an index transform op(.) rather than reversed copies (Sec. 3, the op(.) paragraph).
+ *   - Z-Drop, optional (z > 0): the paper names the Z-Drop variant among the X-Drop
+ *     variants genomic pipelines use (Sec. 1) and cites minimap2 for it; its definition is
+ *     minimap2's (Li 2018): with (i', j') the best cell so far and (i, j) the best cell of
+ *     the anti-diagonal just completed, the extension stops when
+ *     S(i', j') - S(i, j) > Z + e |(i - i') - (j - j')|, e the gap-extension penalty (here
+ *     the linear gap's |gap|).  It is applied after each anti-diagonal on top of the X-Drop
+ *     pruning; the result is the best cell up to and including that anti-diagonal, flag bit 1.
  *
  * Readings where the paper is silent or garbled (each one is listed in the design notes):
  *   R1 cell (i,j) with i,j >= 1 pairs H[i-1] with V[j-1]; i indexes H.
@@ -36,6 +43,9 @@
  *      anti-diagonal: lo' = max(lo, min(b - floor(delta/2), hi - delta + 1)),
  *      hi' = lo' + delta - 1; flag bit 0.
  *   R7 the cell count includes every cell evaluated (pruned ones too) plus S(0,0).
+ *   R8 Z-Drop: (i, j) is the anti-diagonal's best live cell, lowest i on ties; (i', j') is
+ *      the best cell after that anti-diagonal's update of T (so an anti-diagonal that sets
+ *      a new best never triggers it); the comparison is strict.
  *
  * Scores are int64; -inf is represented by an explicit "not live" state, never by an
  * arithmetic sentinel.
@@ -72,11 +82,11 @@ typedef struct {
 static uint8_t side_h(const orc_strings* s, int64_t t) { return s->h[t * s->h_step]; }
 static uint8_t side_v(const orc_strings* s, int64_t t) { return s->v[t * s->v_step]; }
 
-/* Extend one side.  sim is a dense alpha x alpha table. */
-int orc_extend(const uint8_t* h, int64_t h_step, int64_t m,
-               const uint8_t* v, int64_t v_step, int64_t n,
-               const int32_t* sim, int alpha, int32_t gap, int32_t X, uint32_t delta,
-               orc_side* out)
+/* Extend one side.  sim is a dense alpha x alpha table.  z > 0: Z-Drop with Z = z. */
+int orc_extend_z(const uint8_t* h, int64_t h_step, int64_t m,
+                 const uint8_t* v, int64_t v_step, int64_t n,
+                 const int32_t* sim, int alpha, int32_t gap, int32_t X, uint32_t delta,
+                 int32_t z, orc_side* out)
 {
     orc_strings s = { h, h_step, m, v, v_step, n };
     orc_diag buf[3];
@@ -149,6 +159,15 @@ int orc_extend(const uint8_t* h, int64_t h_step, int64_t m,
         if (first < 0) break;                                         /* no live cell */
         L = first; U = last;
         T = T_new;
+        if (z > 0) {
+            /* Z-Drop: this anti-diagonal's best live cell against the best cell so far */
+            int64_t zi = -1, zv = 0;
+            for (int64_t i = lo; i <= hi; i++)
+                if (C->live[i] && (zi < 0 || C->val[i] > zv)) { zi = i; zv = C->val[i]; }
+            int64_t shift = (zi - best_i) - ((d - zi) - best_j);
+            if (shift < 0) shift = -shift;
+            if (best - zv > (int64_t)z + (-(int64_t)gap) * shift) { flags |= 2u; break; }
+        }
         orc_diag* old = P2; P2 = P1; P1 = C; C = old;
     }
 
@@ -159,6 +178,14 @@ int orc_extend(const uint8_t* h, int64_t h_step, int64_t m,
     out->cells = cells;
     for (int k = 0; k < 3; k++) { free(buf[k].val); free(buf[k].live); }
     return 0;
+}
+
+int orc_extend(const uint8_t* h, int64_t h_step, int64_t m,
+               const uint8_t* v, int64_t v_step, int64_t n,
+               const int32_t* sim, int alpha, int32_t gap, int32_t X, uint32_t delta,
+               orc_side* out)
+{
+    return orc_extend_z(h, h_step, m, v, v_step, n, sim, alpha, gap, X, delta, 0, out);
 }
 
 /* Similarity table: DNA (alpha 4) from match/mismatch, protein (alpha 20) from the
@@ -176,11 +203,11 @@ static void build_sim(int alpha, int32_t match, int32_t mismatch, const int8_t* 
  * Right side: H_R[t] = H[h_seed + k + t], V_R[t] = V[v_seed + k + t].
  * Left side:  H_L[t] = H[h_seed - 1 - t], V_L[t] = V[v_seed - 1 - t].
  * total = left.score + right.score + sum of Sim over the seed. */
-int orc_batch(int alpha, const uint8_t* codes, const uint64_t* offsets, const uint32_t* lengths,
-              const uint32_t* pairs, uint64_t first, uint64_t count,
-              int32_t match, int32_t mismatch, int32_t gap, const int8_t* matrix,
-              int32_t X, uint32_t delta,
-              orc_side* left, orc_side* right, int64_t* total)
+int orc_batch_z(int alpha, const uint8_t* codes, const uint64_t* offsets, const uint32_t* lengths,
+                const uint32_t* pairs, uint64_t first, uint64_t count,
+                int32_t match, int32_t mismatch, int32_t gap, const int8_t* matrix,
+                int32_t X, uint32_t delta, int32_t z,
+                orc_side* left, orc_side* right, int64_t* total)
 {
     if (alpha != 4 && alpha != 20) return -1;
     if (alpha == 20 && !matrix) return -1;
@@ -193,15 +220,25 @@ int orc_batch(int alpha, const uint8_t* codes, const uint64_t* offsets, const ui
         int64_t lh = lengths[e[0]], lv = lengths[e[1]];
         int64_t hs = e[2], vs = e[3], k = e[4];
         if (hs + k > lh || vs + k > lv) return -2;
-        int rc = orc_extend(H + hs + k, 1, lh - hs - k, V + vs + k, 1, lv - vs - k,
-                            sim, alpha, gap, X, delta, &right[p]);
+        int rc = orc_extend_z(H + hs + k, 1, lh - hs - k, V + vs + k, 1, lv - vs - k,
+                              sim, alpha, gap, X, delta, z, &right[p]);
         if (rc) return rc;
-        rc = orc_extend(hs > 0 ? H + hs - 1 : H, -1, hs, vs > 0 ? V + vs - 1 : V, -1, vs,
-                        sim, alpha, gap, X, delta, &left[p]);
+        rc = orc_extend_z(hs > 0 ? H + hs - 1 : H, -1, hs, vs > 0 ? V + vs - 1 : V, -1, vs,
+                          sim, alpha, gap, X, delta, z, &left[p]);
         if (rc) return rc;
         int64_t seed_score = 0;
         for (int64_t t = 0; t < k; t++) seed_score += sim[H[hs + t] * alpha + V[vs + t]];
         total[p] = (int64_t)left[p].score + (int64_t)right[p].score + seed_score;
     }
     return 0;
+}
+
+int orc_batch(int alpha, const uint8_t* codes, const uint64_t* offsets, const uint32_t* lengths,
+              const uint32_t* pairs, uint64_t first, uint64_t count,
+              int32_t match, int32_t mismatch, int32_t gap, const int8_t* matrix,
+              int32_t X, uint32_t delta,
+              orc_side* left, orc_side* right, int64_t* total)
+{
+    return orc_batch_z(alpha, codes, offsets, lengths, pairs, first, count, match, mismatch, gap, matrix,
+                       X, delta, 0, left, right, total);
 }

@@ -95,7 +95,7 @@ struct BatchView {
     uint32_t n_pairs = 0;
     const xd_pair* pairs = nullptr;
     int8_t sim[400] = {};
-    int32_t gap = 0, X = 0, max_abs = 1;
+    int32_t gap = 0, X = 0, max_abs = 1, zdrop = 0;
     uint32_t delta = 0, max_len = 0;
     const uint32_t* packed = nullptr;   // resident store: residues already packed (no codes)
     uint64_t packed_words = 0;
@@ -201,6 +201,7 @@ void par_memcpy(void* dst, const void* src, size_t n) { par_copy_check(dst, src,
 struct GraphKey {
     int alpha;
     uint32_t n_seqs, n_pairs, max_len, delta;
+    int32_t zdrop;
     uint64_t n_codes;
     const void *codes, *offsets, *lengths, *pairs, *out, *stream;
     int32_t gap, X;
@@ -337,6 +338,8 @@ xd_status scoring_view(xd_ctx* c, const xd_batch* b, BatchView& v) {
     v.gap = b->scoring.gap;
     v.X = b->X;
     v.delta = b->delta_b;
+    if (b->z_drop < 0) return fail(c, XD_EINVAL, "z_drop must be >= 0");
+    v.zdrop = b->z_drop;
     v.max_abs = score_max_abs(v.sim, v.alpha, v.gap);
     v.n_seqs = b->n_seqs;
     v.n_codes = b->n_codes;
@@ -660,6 +663,7 @@ xd_status run_pipeline(xd_ctx* c, Scratch& s, const BatchView* bs, int nb, xd_re
     P.gap = b.gap;
     P.X = b.X;
     P.delta = b.delta;
+    P.zdrop = b.zdrop;
     std::memcpy(P.sim, b.sim, sizeof(P.sim));
     // residues each batch may address (a resident-store batch: the whole store)
     auto n_res_of = [&](int k) { return b.packed ? b.packed_words * per_word : bs[k].n_codes; };
@@ -782,7 +786,7 @@ void give_pinned(xd_ctx* c, HostBuf& b) {
 
 // Two requests can share a launch when the kernels see the same parameters.
 bool same_params(const BatchView& a, const BatchView& b) {
-    return a.alpha == b.alpha && a.gap == b.gap && a.X == b.X && a.delta == b.delta &&
+    return a.alpha == b.alpha && a.gap == b.gap && a.X == b.X && a.delta == b.delta && a.zdrop == b.zdrop &&
            std::memcmp(a.sim, b.sim, size_t(a.alpha) * a.alpha) == 0;
 }
 
@@ -1272,6 +1276,7 @@ xd_status xd_run_device(xd_ctx* c, const xd_batch* b, xd_result* d_out, void* st
     k.n_pairs = v.n_pairs;
     k.max_len = v.max_len;
     k.delta = v.delta;
+    k.zdrop = v.zdrop;
     k.n_codes = v.n_codes;
     k.codes = v.codes;
     k.offsets = v.offsets;
@@ -1350,7 +1355,7 @@ xd_status xd_run_device_many(xd_ctx* c, uint32_t n_batches, const xd_batch* batc
         xd_status s = scoring_view(c, b, v);
         if (s != XD_OK) return s;
         if (k > 0 && !same_params(vs[0], v))
-            return fail(c, XD_EINVAL, "the batches of one call must share alphabet, scoring, X and delta_b");
+            return fail(c, XD_EINVAL, "the batches of one call must share alphabet, scoring, X, delta_b and z_drop");
         if (b->n_pairs && (!b->pairs || !b->seq_offsets || !b->seq_lengths || !d_out))
             return fail(c, XD_EINVAL, "null device pointer in batch " + std::to_string(k));
         if (b->n_codes && !b->seq_codes) return fail(c, XD_EINVAL, "null seq_codes in batch " + std::to_string(k));
@@ -1516,6 +1521,7 @@ xd_status xd_submit_pairs(xd_ctx* c, const xd_pairs_batch* pb, uint64_t* ticket)
     b.scoring = pb->scoring;
     b.X = pb->X;
     b.delta_b = pb->delta_b;
+    b.z_drop = pb->z_drop;
     BatchView v;
     xd_status s = scoring_view(c, &b, v);
     if (s != XD_OK) return s;

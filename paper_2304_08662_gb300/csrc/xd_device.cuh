@@ -68,6 +68,7 @@ struct Problem {
     int32_t gap;
     int32_t X;
     uint32_t delta;             // 0 = unrestricted
+    int32_t zdrop;              // 0 = X-Drop alone, > 0: Z-Drop with Z = zdrop
     int32_t max_abs;            // largest |score| of one step (similarity or gap)
     int32_t s_max;              // largest similarity, at least 0
     // Escalation records: a side that outgrows a register level's window saves its two

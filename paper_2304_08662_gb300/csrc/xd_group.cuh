@@ -298,6 +298,15 @@ __device__ __forceinline__ void band_of(SideState& s, const Problem& P, int32_t 
     }
 }
 
+// Z-Drop (z > 0; Sec. 1 names the variant, minimap2's definition): after anti-diagonal d,
+// whose best live cell is (arg, d - arg) with score wmax, the side stops when the best cell so
+// far beats it by more than Z + |gap| times the difference of their diagonals.
+__device__ __forceinline__ bool zdrop_stops(const Problem& P, const SideState& s, int32_t wmax, int32_t arg,
+                                            int32_t d) {
+    const int32_t shift = abs((arg - s.bi) - ((d - arg) - s.bj));
+    return int64_t(s.best) - wmax > int64_t(P.zdrop) + int64_t(-P.gap) * shift;
+}
+
 // The lane's CG cells.  P1 holds d-1, P2 holds d-2 and receives d.  upb / lfb are the
 // neighbours beyond the lane's first / last slot.  tab is the block's similarity table:
 // for DNA 256 int4 entries indexed by one byte of the xor of the residue slices (four
@@ -668,6 +677,10 @@ __device__ __forceinline__ int group_step(SideState& s, Res<CG, A>& res, int32_t
     }
     s.barg = arg;
     s.d = d + 1;
+    if (P.zdrop > 0 && zdrop_stops(P, s, wmax, arg, d)) {
+        s.flags |= 2u;
+        return kDone;
+    }
     return d == s.m + s.n ? kDone : kCont;
 }
 
@@ -780,6 +793,10 @@ __device__ __forceinline__ int group_step16(SideState& s, Res<CG, A>& res, uint3
     }
     s.barg = arg;
     s.d = d + 1;
+    if (P.zdrop > 0 && zdrop_stops(P, s, wmax, arg, d)) {
+        s.flags |= 2u;
+        return kDone;
+    }
     return d == s.m + s.n ? kDone : kCont;
 }
 

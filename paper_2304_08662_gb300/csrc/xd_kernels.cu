@@ -174,7 +174,8 @@ __device__ void extend_generic(const Problem& P, const Unit& u, int32_t* A, int3
         const uint32_t b = residue(P.store, P.alpha, u.v0 + dir * (j - 1));
         return sim_of(sim, P.alpha, a, b);
     };
-    const SweepOut o = generic_sweep(int64_t(u.m), int64_t(u.n), P.gap, P.X, P.delta, sim_at, A, B, Cc, lane);
+    const SweepOut o = generic_sweep(int64_t(u.m), int64_t(u.n), P.gap, P.X, P.delta, P.zdrop, sim_at, A, B, Cc,
+                                     lane);
     if (lane == 0) {
         write_side(P.results, u.pair, u.side, o.best, uint32_t(o.bi), uint32_t(o.bj), o.flags, o.cells);
         atomicAdd(&P.stats[2], 1ull);
@@ -397,6 +398,14 @@ __device__ bool extend_band(const Problem& P, const Unit& u, uint32_t uidx, int3
             bj = d - arg;
         }
         barg = arg;
+        if (P.zdrop > 0) {
+            // Z-Drop: the anti-diagonal's best cell against the best so far
+            const int64_t shift = llabs((arg - bi) - ((d - arg) - bj));
+            if (int64_t(best) - wmax > int64_t(P.zdrop) + int64_t(-P.gap) * shift) {
+                flags |= 2u;
+                break;
+            }
+        }
         L = int32_t(ib + first);
         U = int32_t(ib + last);
         int32_t* tmp = P2;

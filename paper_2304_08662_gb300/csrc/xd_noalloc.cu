@@ -46,7 +46,7 @@ struct Args {
     const xd_pair* pairs;
     uint32_t n_pairs;
     xd_result* out;
-    int32_t alpha, gap, X;
+    int32_t alpha, gap, X, zdrop;
     uint32_t delta, max_side_len;
     int32_t max_abs;
     int8_t sim[400];
@@ -72,7 +72,7 @@ __device__ void side_noalloc(const Args& a, const int32_t* sim, int64_t h0, int6
         const uint32_t y = code_at(a, uint64_t(v0 + dir * (j - 1)), lane_bad);
         return sim[x * a.alpha + y];
     };
-    const xd::SweepOut o = xd::generic_sweep(m, n, a.gap, a.X, a.delta, sim_at, A, B, Cc, lane);
+    const xd::SweepOut o = xd::generic_sweep(m, n, a.gap, a.X, a.delta, a.zdrop, sim_at, A, B, Cc, lane);
     bad |= __any_sync(0xffffffffu, lane_bad);
     res.score = o.best;
     res.h_ext = uint32_t(o.bi);
@@ -223,6 +223,8 @@ extern "C" xd_status xd_run_device_noalloc(const xd_batch* b, uint32_t max_side_
     a.alpha = b->alpha == XD_DNA2 ? 4 : 20;
     a.gap = b->scoring.gap;
     a.X = b->X;
+    if (b->z_drop < 0) return XD_EINVAL;
+    a.zdrop = b->z_drop;
     a.delta = b->delta_b;
     a.max_side_len = max_side_len;
     int32_t max_abs = a.gap < 0 ? -a.gap : a.gap;

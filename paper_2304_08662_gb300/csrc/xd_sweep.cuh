@@ -23,9 +23,11 @@ struct SweepOut {
 };
 
 // sim_at(i, j), i, j >= 1: Sim(H_side[i-1], V_side[j-1]).
+// zdrop > 0: the Z-Drop rule after each anti-diagonal (flag bit 1 when it ends the side).
 template <class SimAt>
 __device__ __forceinline__ SweepOut generic_sweep(int64_t m, int64_t n, int32_t gap, int32_t X, uint32_t delta,
-                                                  SimAt sim_at, int32_t* A, int32_t* B, int32_t* Cc, int lane) {
+                                                  int32_t zdrop, SimAt sim_at, int32_t* A, int32_t* B, int32_t* Cc,
+                                                  int lane) {
     int32_t* P1 = A;
     int32_t* P2 = B;
     int32_t* C = Cc;
@@ -82,6 +84,13 @@ __device__ __forceinline__ SweepOut generic_sweep(int64_t m, int64_t n, int32_t 
             o.bj = d - barg;
         }
         prev_arg = barg;
+        if (zdrop > 0) {
+            const int64_t shift = llabs((int64_t(barg) - o.bi) - ((d - barg) - o.bj));
+            if (int64_t(o.best) - wmax > int64_t(zdrop) + int64_t(-gap) * shift) {
+                o.flags |= 2u;
+                break;
+            }
+        }
         L = first;
         U = last;
         int32_t* old = P2;

@@ -39,12 +39,13 @@ class xd_batch(ctypes.Structure):
                 ("seq_codes", ctypes.c_void_p), ("seq_offsets", ctypes.c_void_p),
                 ("seq_lengths", ctypes.c_void_p), ("n_pairs", ctypes.c_uint32),
                 ("pairs", ctypes.c_void_p), ("scoring", xd_scoring), ("X", ctypes.c_int32),
-                ("delta_b", ctypes.c_uint32)]
+                ("delta_b", ctypes.c_uint32), ("z_drop", ctypes.c_int32)]
 
 
 class xd_pairs_batch(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_int), ("n_pairs", ctypes.c_uint32), ("pairs", ctypes.c_void_p),
-                ("scoring", xd_scoring), ("X", ctypes.c_int32), ("delta_b", ctypes.c_uint32)]
+                ("scoring", xd_scoring), ("X", ctypes.c_int32), ("delta_b", ctypes.c_uint32),
+                ("z_drop", ctypes.c_int32)]
 
 
 class xd_stats(ctypes.Structure):
@@ -65,7 +66,7 @@ class xd_timing(ctypes.Structure):
                 ("register_band_cells", ctypes.c_uint64), ("register_slot_cells", ctypes.c_uint64)]
 
 
-assert ctypes.sizeof(xd_batch) == 88 and RESULT_DTYPE.itemsize == 56 and ctypes.sizeof(xd_config) == 40
+assert ctypes.sizeof(xd_batch) == 96 and RESULT_DTYPE.itemsize == 56 and ctypes.sizeof(xd_config) == 40
 
 _LIB = None
 
@@ -150,7 +151,7 @@ def xd_destroy(ctx):
 class BatchArgs:
     """Keeps the arrays of one xd_batch alive while the C call reads them."""
 
-    def __init__(self, alphabet, codes, offsets, lengths, pairs, match, mismatch, gap, matrix, X, delta):
+    def __init__(self, alphabet, codes, offsets, lengths, pairs, match, mismatch, gap, matrix, X, delta, zdrop=0):
         self.keep = [codes, offsets, lengths, pairs, matrix]
         self.matrix = None if matrix is None else np.ascontiguousarray(matrix, dtype=np.int8)
         sc = xd_scoring(int(match), int(mismatch), int(gap), None if self.matrix is None else _ptr(self.matrix))
@@ -158,7 +159,7 @@ class BatchArgs:
         n_seqs = int(lengths.numel() if hasattr(lengths, "numel") else lengths.size)
         n_pairs = int(pairs.shape[0])
         self.c = xd_batch(XD_DNA2 if alphabet == "dna" else XD_PROT5, n_seqs, n_codes, _ptr(codes),
-                          _ptr(offsets), _ptr(lengths), n_pairs, _ptr(pairs), sc, int(X), int(delta))
+                          _ptr(offsets), _ptr(lengths), n_pairs, _ptr(pairs), sc, int(X), int(delta), int(zdrop))
 
     @classmethod
     def from_host(cls, b):
@@ -167,7 +168,7 @@ class BatchArgs:
         return cls(b.alphabet, np.ascontiguousarray(b.codes, dtype=np.uint8),
                    np.ascontiguousarray(b.offsets, dtype=np.uint64),
                    np.ascontiguousarray(b.lengths, dtype=np.uint32), pairs,
-                   b.match, b.mismatch, b.gap, b.matrix, b.X, b.delta)
+                   b.match, b.mismatch, b.gap, b.matrix, b.X, b.delta, getattr(b, "zdrop", 0))
 
 
 def xd_submit_batch(ctx, args):
@@ -320,13 +321,13 @@ def xd_store_info(ctx, alphabet):
     return n.value, b.value
 
 
-def xd_submit_pairs(ctx, alphabet, pairs, match=1, mismatch=-1, gap=-1, matrix=None, X=20, delta=0):
+def xd_submit_pairs(ctx, alphabet, pairs, match=1, mismatch=-1, gap=-1, matrix=None, X=20, delta=0, zdrop=0):
     """Submit seed tuples whose h_id / v_id are resident-store handles; returns a ticket."""
     pairs = np.ascontiguousarray(pairs, dtype=np.uint32).reshape(-1, 5)
     mat = None if matrix is None else np.ascontiguousarray(matrix, dtype=np.int8)
     sc = xd_scoring(int(match), int(mismatch), int(gap), None if mat is None else _ptr(mat))
     pb = xd_pairs_batch(XD_DNA2 if alphabet == "dna" else XD_PROT5, pairs.shape[0], _ptr(pairs), sc, int(X),
-                        int(delta))
+                        int(delta), int(zdrop))
     t = ctypes.c_uint64()
     rc = lib().xd_submit_pairs(ctx, ctypes.byref(pb), ctypes.byref(t))
     if rc != XD_OK:

@@ -59,6 +59,7 @@ class Batch:
     delta: int = 0             # 0 = unrestricted
     name: str = ""
     meta: dict = field(default_factory=dict)
+    zdrop: int = 0             # > 0: the Z-Drop rule with Z = zdrop on top of X-Drop
 
     @property
     def n_pairs(self):
@@ -73,7 +74,7 @@ class Batch:
         h = hashlib.sha256()
         for a in (self.codes, self.offsets, self.lengths, self.pairs):
             h.update(np.ascontiguousarray(a).tobytes())
-        h.update(np.array([self.match, self.mismatch, self.gap, self.X, self.delta],
+        h.update(np.array([self.match, self.mismatch, self.gap, self.X, self.delta, self.zdrop],
                           dtype=np.int64).tobytes())
         if self.matrix is not None:
             h.update(np.ascontiguousarray(self.matrix).tobytes())
@@ -95,7 +96,7 @@ class Batch:
         new_pairs[:, 1] = np.arange(1, 2 * len(idx), 2, dtype=np.uint32)
         return Batch(self.alphabet, codes, offs, lens.astype(np.uint32), new_pairs,
                      self.match, self.mismatch, self.gap, self.matrix, self.X, self.delta,
-                     self.name + "[subset]", dict(self.meta))
+                     self.name + "[subset]", dict(self.meta), self.zdrop)
 
     def pair_range(self, a, b):
         """Batch of the pairs [a, b) sharing this batch's arrays where possible.
@@ -117,13 +118,13 @@ class Batch:
         pairs[:, :2] -= np.uint32(2 * a)
         return Batch(self.alphabet, self.codes[base:end], offs, lens, pairs,
                      self.match, self.mismatch, self.gap, self.matrix, self.X, self.delta,
-                     f"{self.name}[{a}:{b}]", dict(self.meta))
+                     f"{self.name}[{a}:{b}]", dict(self.meta), self.zdrop)
 
-    def with_params(self, X=None, delta=None):
+    def with_params(self, X=None, delta=None, zdrop=None):
         b = Batch(self.alphabet, self.codes, self.offsets, self.lengths, self.pairs,
                   self.match, self.mismatch, self.gap, self.matrix,
                   self.X if X is None else int(X), self.delta if delta is None else int(delta),
-                  self.name, dict(self.meta))
+                  self.name, dict(self.meta), self.zdrop if zdrop is None else int(zdrop))
         return b
 
 

@@ -22,7 +22,7 @@ def oracle_all():
     cache = {}
 
     def get(batch):
-        key = (batch.name, batch.n_pairs, batch.X, batch.delta, repr(sorted(batch.meta.items())))
+        key = (batch.name, batch.n_pairs, batch.X, batch.delta, batch.zdrop, repr(sorted(batch.meta.items())))
         if key not in cache:
             cache[key] = oracle.run_batch(batch, threads=max(1, os.cpu_count() or 1))
         return cache[key]

@@ -48,7 +48,7 @@ def test_every_exported_symbol_is_declared():
 
 
 def test_struct_layouts_match_header():
-    assert ctypes.sizeof(xdrop.xd_batch) == 88
+    assert ctypes.sizeof(xdrop.xd_batch) == 96
     assert xdrop.RESULT_DTYPE.itemsize == 56
     assert xdrop.SIDE_DTYPE.itemsize == 24
     assert xdrop.PAIR_DTYPE.itemsize == 20

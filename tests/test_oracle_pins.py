@@ -27,8 +27,8 @@ def enc(s):
     return np.array([LUT[c] for c in s], dtype=np.uint8)
 
 
-def ext(lib, h, v, sim, gap, X, delta=0):
-    r = oracle.extend(h, v, sim, gap, X, delta, lib=lib)
+def ext(lib, h, v, sim, gap, X, delta=0, zdrop=0):
+    r = oracle.extend(h, v, sim, gap, X, delta, lib=lib, zdrop=zdrop)
     return (r["score"], r["h_ext"], r["v_ext"], r["flags"], r["cells"])
 
 
@@ -58,11 +58,13 @@ def full_dp(h, v, sim, gap):
     return int(best), i, d - i
 
 
-def dense_xdrop(h, v, sim, gap, X, delta=0):
+def dense_xdrop(h, v, sim, gap, X, delta=0, zdrop=0):
     """The same rules restated on a dense matrix with per-cell live flags: the band of
     anti-diagonal d is read off the live flags of anti-diagonal d-1 in the full matrix,
     and predecessors are read from the full matrix.  No band bookkeeping is shared with
-    the C oracle's three rotating arrays."""
+    the C oracle's three rotating arrays.  zdrop > 0: after each anti-diagonal, stop when
+    the best cell so far beats the anti-diagonal's best live cell (lowest i) by more than
+    zdrop + |gap| times the difference of their diagonals (minimap2's Z-Drop)."""
     m, n = len(h), len(v)
     S = np.zeros((m + 1, n + 1), dtype=np.int64)
     live = np.zeros((m + 1, n + 1), dtype=bool)
@@ -96,6 +98,14 @@ def dense_xdrop(h, v, sim, gap, X, delta=0):
         if not any_live:
             break
         T = new_t
+        if zdrop:
+            on_d = [(int(S[i, d - i]), i) for i in range(lo, hi + 1) if live[i, d - i]]
+            top = max(v_ for v_, _ in on_d)
+            zi = min(i for v_, i in on_d if v_ == top)
+            diag_shift = abs((zi - best[1]) - ((d - zi) - best[2]))
+            if best[0] - top > zdrop + abs(gap) * diag_shift:
+                flags |= 2
+                break
     return best[0], best[1], best[2], flags, cells
 
 
@@ -280,6 +290,55 @@ def pin_dense_restatement(lib, trials=400, seed=23):
             (h, v, X, delta)
 
 
+def pin_zdrop_dense_restatement(lib, trials=500, seed=37):
+    """Z-Drop (the variant the paper names in Sec. 1; minimap2's definition) against the
+    dense restatement, on random and related small inputs, several Z and X."""
+    rng = np.random.default_rng(seed)
+    hits = 0
+    for t in range(trials):
+        prot = t % 5 == 4
+        a = 20 if prot else 4
+        m, n = int(rng.integers(0, 15)), int(rng.integers(0, 15))
+        h = rng.integers(0, a, m)
+        v = rng.integers(0, a, n)
+        if t % 2 == 0 and m and n:
+            # a matching prefix followed by noise, where the anti-diagonal maxima fall away
+            k = min(m, n, int(rng.integers(1, 8)))
+            v[:k] = h[:k]
+        sim, gap = (PROT_SIM, -2) if prot else (DNA_SIM, -1)
+        X = int(rng.integers(3, 40 if prot else 12))
+        z = int(rng.integers(1, 6))
+        delta = int(rng.choice([0, 0, 0, 4]))
+        got = ext(lib, h, v, sim, gap, X, delta, zdrop=z)
+        assert got == dense_xdrop(h, v, sim, gap, X, delta, zdrop=z), (h, v, X, z, delta)
+        hits += bool(got[3] & 2)
+    assert hits > trials // 10, hits   # the rule fires in a good share of the cases
+
+
+def pin_zdrop_closed_forms(lib, seed=41):
+    """Z beyond any reachable drop changes nothing; identical sequences never trigger it
+    (each anti-diagonal's best cell lies on the main diagonal, at most one gap below the
+    best); a long matching prefix followed by all mismatches triggers it as soon as the
+    drop exceeds Z + |gap| x the shift."""
+    rng = np.random.default_rng(seed)
+    for _ in range(40):
+        m, n = int(rng.integers(0, 30)), int(rng.integers(0, 30))
+        h, v = rng.integers(0, 4, m), rng.integers(0, 4, n)
+        X = int(rng.integers(0, 8))
+        assert ext(lib, h, v, DNA_SIM, -1, X, zdrop=1 << 29) == ext(lib, h, v, DNA_SIM, -1, X)
+        g = rng.integers(0, 4, m)
+        for z in (1, 2, 5):
+            assert ext(lib, g, g, DNA_SIM, -1, 50, zdrop=z) == ext(lib, g, g, DNA_SIM, -1, 50)
+    # A^8 then C^8 against A^8 then G^8, X large: the best is 8 at (8, 8) (d = 16); on
+    # d = 16 + k the best cell is 8 - ceil(k/2) (k/2 mismatches down the diagonal, or one
+    # more gap), on the diagonal for even k and one off it for odd k.  With Z = 2 the first
+    # anti-diagonal whose drop exceeds 2 + shift is d = 22 (drop 3, shift 0): stop there.
+    h = enc("A" * 8 + "C" * 8)
+    v = enc("A" * 8 + "G" * 8)
+    got = ext(lib, h, v, DNA_SIM, -1, 100, zdrop=2)
+    assert got[:4] == (8, 8, 8, 2), got
+
+
 def pin_restricted_without_overflow(lib, trials=120, seed=29):
     rng = np.random.default_rng(seed)
     for _ in range(trials):
@@ -300,7 +359,8 @@ def pin_restricted_without_overflow(lib, trials=120, seed=29):
 
 PINS = [pin_hand_traces, pin_x_infinite_is_full_dp, pin_identical_sequences, pin_closed_forms,
         pin_swap_symmetry, pin_integer_scaling, pin_left_is_right_on_reversed, pin_pair_total,
-        pin_protein_batch, pin_dense_restatement, pin_restricted_without_overflow]
+        pin_protein_batch, pin_dense_restatement, pin_restricted_without_overflow,
+        pin_zdrop_dense_restatement, pin_zdrop_closed_forms]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=lambda f: f.__name__)
@@ -338,13 +398,19 @@ MUTANTS = {
     "tie_break_last": ("if (c > T_new) {", "if (c >= T_new) {"),
     "cells_live_only": ("cells++;\n            int live = has && !(c < T - (int64_t)X);",
                         "int live = has && !(c < T - (int64_t)X); cells += live;"),
-    "left_offset": ("rc = orc_extend(hs > 0 ? H + hs - 1 : H,", "rc = orc_extend(hs > 0 ? H + hs : H,"),
+    "left_offset": ("rc = orc_extend_z(hs > 0 ? H + hs - 1 : H,", "rc = orc_extend_z(hs > 0 ? H + hs : H,"),
     "restricted_last_on_tie": ("(b < 0 || P1->val[i] > bv)", "(b < 0 || P1->val[i] >= bv)"),
     "restricted_no_flag": ("flags |= 1u;", ";"),
     "seed_not_scored": ("+ (int64_t)right[p].score + seed_score;", "+ (int64_t)right[p].score;"),
     "no_origin_cell": ("uint64_t cells = 1;", "uint64_t cells = 0;"),
     "centre_on_hi": ("int64_t centred = b - (int64_t)(delta / 2);", "int64_t centred = b;"),
     "matrix_sign_dropped": ("(int32_t)matrix[a * 20 + b]", "(int32_t)(uint8_t)matrix[a * 20 + b]"),
+    "zdrop_nonstrict": ("if (best - zv > (int64_t)z + (-(int64_t)gap) * shift)",
+                        "if (best - zv >= (int64_t)z + (-(int64_t)gap) * shift)"),
+    "zdrop_no_shift_term": ("(int64_t)z + (-(int64_t)gap) * shift)", "(int64_t)z)"),
+    "zdrop_last_on_tie": ("if (C->live[i] && (zi < 0 || C->val[i] > zv))",
+                          "if (C->live[i] && (zi < 0 || C->val[i] >= zv))"),
+    "zdrop_no_flag": ("{ flags |= 2u; break; }", "{ break; }"),
     "protein_scored_as_dna": ("alpha == 20 ? (int32_t)matrix[a * 20 + b] : (a == b ? match : mismatch)",
                               "(a == b ? match : mismatch)"),
 }

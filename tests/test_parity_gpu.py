@@ -181,6 +181,35 @@ def test_edges(ctx):
             assert_parity(xdrop.extend_host(ctx, b), b)
 
 
+@pytest.mark.parametrize("zdrop", [1, 3, 8, 40])
+def test_zdrop_random(ctx, zdrop):
+    """The Z-Drop rule (Sec. 1 names it; minimap2's definition) on top of X-Drop: random
+    tiny and ragged pairs, DNA and protein, several X, unrestricted and restricted."""
+    rng = np.random.default_rng(300 + zdrop)
+    for alphabet, gap in (("dna", -1), ("protein", -2)):
+        rows = random_pairs(rng, 250, alphabet, 120)
+        for X in (5, 30, X_INF):
+            for delta in (0, 16):
+                b = synth.from_strings(rows, alphabet=alphabet, gap=gap, X=X, delta=delta).with_params(zdrop=zdrop)
+                got = xdrop.extend_host(ctx, b)
+                assert_parity(got, b)
+
+
+@pytest.mark.parametrize("zdrop", [10, 50, 200])
+def test_zdrop_workloads(ctx, zdrop):
+    """Z-Drop on the workload shapes: long reads at X = 50 (wide random-walk bands that
+    Z-Drop ends early), protein, and the uneven batch with a memory-restricted window."""
+    batches = [synth.dna_longread(n_pairs=1500).with_params(X=50, zdrop=zdrop),
+               synth.protein(n_pairs=5000).with_params(zdrop=zdrop),
+               synth.uneven(n_pairs=60, delta=256).with_params(zdrop=zdrop)]
+    fired = 0
+    for b in batches:
+        got = xdrop.extend_host(ctx, b)
+        assert_parity(got, b)
+        fired += int(((got["left"]["flags"] | got["right"]["flags"]) & 2).sum())
+    assert fired > 0
+
+
 def test_dna_tiny_workload(ctx):
     b = synth.dna_tiny()
     assert_parity(xdrop.extend_host(ctx, b), b)
@@ -267,7 +296,7 @@ def _device_args(b):
     lens = torch.from_numpy(b.lengths.view(np.int32)).to(dev)
     pairs = torch.from_numpy(np.ascontiguousarray(b.pairs).view(np.int32)).to(dev)
     args = xdrop.BatchArgs(b.alphabet, codes, offs, lens, pairs, b.match, b.mismatch, b.gap,
-                           b.matrix, b.X, b.delta)
+                           b.matrix, b.X, b.delta, b.zdrop)
     out = torch.zeros(b.n_pairs * xdrop.RESULT_DTYPE.itemsize, dtype=torch.uint8, device=dev)
     return args, out
 

@@ -26,7 +26,7 @@ def _device_batch(b):
     lens = torch.from_numpy(b.lengths.view(np.int32)).to(dev)
     pairs = torch.from_numpy(np.ascontiguousarray(b.pairs).view(np.int32)).to(dev)
     return xdrop.BatchArgs(b.alphabet, codes, offs, lens, pairs, b.match, b.mismatch, b.gap,
-                           b.matrix, b.X, b.delta)
+                           b.matrix, b.X, b.delta, b.zdrop)
 
 
 @pytest.mark.parametrize("make", [
@@ -34,7 +34,8 @@ def _device_batch(b):
     lambda: synth.protein(n_pairs=1500),
     lambda: synth.uneven(n_pairs=40, delta=256),
     lambda: synth.from_strings([("ACGT", "ACGT", 0, 0, 4), ("A" * 50, "A" * 50, 25, 25, 1)], X=3),
-], ids=["dna_longread", "protein", "uneven_restricted", "edges"])
+    lambda: synth.dna_longread(n_pairs=200).with_params(X=50, zdrop=20),
+], ids=["dna_longread", "protein", "uneven_restricted", "edges", "zdrop"])
 def test_noalloc_matches_run_device_on_two_calls(make):
     b = make()
     args = _device_batch(b)
