@@ -113,6 +113,7 @@ struct Request {
     BatchView v;                 // parameters and sizes; pointers unused
     HostBuf in;
     size_t o_offs = 0, o_lens = 0, o_pairs = 0, in_bytes = 0;
+    size_t n_words = 0;          // packed residue words at the start of its pinned buffer
     size_t need = 0;             // device bytes admitted for it
     bool pairs_only = false;     // seed tuples on the resident sequence store
     std::vector<xd_result> out;
@@ -194,6 +195,80 @@ size_t par_copy_check(void* dst, const void* src, size_t n, int alpha) {
 }
 
 void par_memcpy(void* dst, const void* src, size_t n) { par_copy_check(dst, src, n, 0); }
+
+// Host packing of residue codes in the device store's layout, while they are staged:
+// DNA word w holds codes 16w .. 16w + 15, code t at bits 2t; protein word w holds codes
+// 6w .. 6w + 5, code t at bits 5t.  8 DNA codes (one byte each, 0..3) to 16 bits: pair the
+// bytes of each 16-bit lane, then the nibbles of each 32-bit lane, then the bytes.
+inline uint32_t pack8_dna(uint64_t x) {
+    x = (x | (x >> 6)) & 0x000F000F000F000Full;
+    x = (x | (x >> 12)) & 0x000000FF000000FFull;
+    return uint32_t((x | (x >> 24)) & 0xFFFFull);
+}
+
+size_t packed_words(uint64_t n_codes, int alpha) {
+    const uint64_t per = alpha == 4 ? 16 : 6;
+    return size_t((n_codes + per - 1) / per);
+}
+
+// Packs words [w0, w1) of n codes from src into dst; false if a code is outside the alphabet.
+bool pack_range(uint32_t* dst, const uint8_t* src, uint64_t n, int alpha, size_t w0, size_t w1) {
+    bool ok = true;
+    if (alpha == 4) {
+        for (size_t w = w0; w < w1; w++) {
+            const uint64_t base = uint64_t(w) * 16;
+            if (base + 16 <= n) {
+                uint64_t a, b;
+                std::memcpy(&a, src + base, 8);
+                std::memcpy(&b, src + base + 8, 8);
+                ok &= ((a | b) & 0xFCFCFCFCFCFCFCFCull) == 0;
+                dst[w] = pack8_dna(a) | (pack8_dna(b) << 16);
+            } else {
+                uint32_t word = 0;
+                for (uint64_t t = 0; base + t < n; t++) {
+                    const uint8_t c = src[base + t];
+                    ok &= c < 4;
+                    word |= uint32_t(c & 3u) << (2 * t);
+                }
+                dst[w] = word;
+            }
+        }
+    } else {
+        for (size_t w = w0; w < w1; w++) {
+            const uint64_t base = uint64_t(w) * 6;
+            uint32_t word = 0;
+            for (uint64_t t = 0; t < 6 && base + t < n; t++) {
+                const uint8_t c = src[base + t];
+                ok &= c < 20;
+                word |= uint32_t(c & 31u) << (5 * t);
+            }
+            dst[w] = word;
+        }
+    }
+    return ok;
+}
+
+// Packs n codes into dst (packed_words(n, alpha) words) with up to 16 host threads; false if
+// any code is outside the alphabet.
+bool par_pack_check(uint32_t* dst, const uint8_t* src, uint64_t n, int alpha) {
+    const size_t words = packed_words(n, alpha);
+    const size_t kMinParallel = size_t(2) << 20;   // words
+    if (words < kMinParallel) return pack_range(dst, src, n, alpha, 0, words);
+    const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    const size_t per = (words + hw - 1) / hw;
+    std::atomic<bool> ok{true};
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < hw; t++) {
+        const size_t a = t * per;
+        if (a >= words) break;
+        const size_t b = std::min(words, a + per);
+        th.emplace_back([&, a, b]() {
+            if (!pack_range(dst, src, n, alpha, a, b)) ok = false;
+        });
+    }
+    for (auto& x : th) x.join();
+    return ok.load();
+}
 
 }  // namespace
 
@@ -374,9 +449,9 @@ xd_status validate_host(xd_ctx* c, const xd_batch* b, const BatchView& v, uint32
 }
 
 // Escalation-record pool: 256 ints per unit on average (a 32-slot record takes 80, a
-// 512-slot one 1040), at most 64 Mi ints.
+// 512-slot one 1040), at most 256 Mi ints (1 GiB, reached by launches of several batches).
 constexpr uint64_t kRecIntsPerUnit = 256;
-constexpr uint64_t kRecPoolMax = uint64_t(1) << 26;
+constexpr uint64_t kRecPoolMax = uint64_t(1) << 28;
 
 struct ScratchPlan {
     size_t store, units, bucket, order, q, generic, rec, rec_of;
@@ -805,7 +880,7 @@ void launch_merged(xd_ctx* c, Slot& slot) {
     Range range("xd.launch");
     std::vector<Request*> take;
     const Request* first = c->pending.front();
-    uint64_t n_codes = 0, n_seqs = 0, n_pairs = 0;
+    uint64_t n_codes = 0, n_seqs = 0, n_pairs = 0, n_words = 0;
     for (auto it = c->pending.begin(); it != c->pending.end();) {
         Request* r = *it;
         const bool fits = take.empty() ||
@@ -816,6 +891,7 @@ void launch_merged(xd_ctx* c, Slot& slot) {
         if (fits) {
             take.push_back(r);
             n_codes += r->v.n_codes;
+            n_words += r->n_words;
             n_seqs += r->v.n_seqs;
             n_pairs += r->v.n_pairs;
             it = c->pending.erase(it);
@@ -830,7 +906,10 @@ void launch_merged(xd_ctx* c, Slot& slot) {
     v.n_pairs = uint32_t(n_pairs);
     v.max_len = 0;
     for (Request* r : take) v.max_len = std::max(v.max_len, r->v.max_len);
-    const size_t o_offs = align_up(n_codes, 256);
+    // the requests' packed residues one after the other (each from a word boundary), then the
+    // sequence tables and the seed tuples
+    const uint64_t per_word = v.alpha == 4 ? 16 : 6;
+    const size_t o_offs = align_up(4 * n_words, 256);
     const size_t o_lens = o_offs + align_up(8 * n_seqs, 256);
     const size_t o_pairs = o_lens + align_up(4 * n_seqs, 256);
     const size_t in_bytes = o_pairs + align_up(sizeof(xd_pair) * n_pairs, 256);
@@ -857,8 +936,8 @@ void launch_merged(xd_ctx* c, Slot& slot) {
         // like the device buffer; large code arrays are copied from the requests' buffers
         if ((e = grow_pinned(slot.h_stage, in_bytes)) != cudaSuccess) return cuda_err(e, "pinned stage buffer");
         char* h = static_cast<char*>(slot.h_stage.p);
-        uint64_t code_base = 0, seq_base = 0, pair_base = 0;
-        size_t run_a = 0, run_b = 0;   // staged code bytes not yet copied
+        uint64_t word_base = 0, seq_base = 0, pair_base = 0;
+        size_t run_a = 0, run_b = 0;   // staged word bytes not yet copied
         auto flush_run = [&]() -> cudaError_t {
             cudaError_t e2 = cudaSuccess;
             if (run_b > run_a) e2 = cudaMemcpyAsync(d + run_a, h + run_a, run_b - run_a, cudaMemcpyHostToDevice, st);
@@ -867,16 +946,18 @@ void launch_merged(xd_ctx* c, Slot& slot) {
         };
         for (Request* r : take) {
             const char* src = static_cast<const char*>(r->in.p);
-            const uint64_t nc = r->v.n_codes;
-            if (nc >= kGatherBelow) {
+            const size_t nb = 4 * r->n_words, at = 4 * word_base;
+            if (nb >= kGatherBelow) {
                 if ((e = flush_run()) != cudaSuccess) return cuda_err(e, "cudaMemcpyAsync");
-                e = cudaMemcpyAsync(d + code_base, src, nc, cudaMemcpyHostToDevice, st);
+                e = cudaMemcpyAsync(d + at, src, nb, cudaMemcpyHostToDevice, st);
                 if (e != cudaSuccess) return cuda_err(e, "cudaMemcpyAsync");
-                run_a = run_b = code_base + nc;
+                run_a = run_b = at + nb;
             } else {
-                std::memcpy(h + code_base, src, nc);
-                run_b = code_base + nc;
+                std::memcpy(h + at, src, nb);
+                run_b = at + nb;
             }
+            // residue positions of this request start at its first word
+            const uint64_t code_base = word_base * per_word;
             auto* offs = reinterpret_cast<uint64_t*>(h + o_offs) + seq_base;
             const auto* r_offs = reinterpret_cast<const uint64_t*>(src + r->o_offs);
             for (uint32_t q = 0; q < r->v.n_seqs; q++) offs[q] = r_offs[q] + code_base;
@@ -888,7 +969,7 @@ void launch_merged(xd_ctx* c, Slot& slot) {
                 prs[q].h_id += uint32_t(seq_base);
                 prs[q].v_id += uint32_t(seq_base);
             }
-            code_base += nc;
+            word_base += r->n_words;
             seq_base += r->v.n_seqs;
             pair_base += r->v.n_pairs;
         }
@@ -896,7 +977,11 @@ void launch_merged(xd_ctx* c, Slot& slot) {
         e = cudaMemcpyAsync(d + o_offs, h + o_offs, in_bytes - o_offs, cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return cuda_err(e, "cudaMemcpyAsync");
     }
-    v.codes = reinterpret_cast<const uint8_t*>(d);
+    // packed on the host: the pipeline reads the words directly (no packing kernel)
+    v.codes = nullptr;
+    v.n_codes = 0;
+    v.packed = reinterpret_cast<const uint32_t*>(d);
+    v.packed_words = std::max<uint64_t>(1, n_words);
     v.offsets = reinterpret_cast<const uint64_t*>(d + o_offs);
     v.lengths = reinterpret_cast<const uint32_t*>(d + o_lens);
     v.pairs = reinterpret_cast<const xd_pair*>(d + o_pairs);
@@ -1553,6 +1638,7 @@ xd_status xd_submit_pairs(xd_ctx* c, const xd_pairs_batch* pb, uint64_t* ticket)
     r->pairs_only = true;
     r->o_offs = r->o_lens = r->o_pairs = 0;
     r->in_bytes = in_bytes;
+    r->n_words = 0;
     r->need = need;
     cudaError_t e = cudaSetDevice(c->device);
     if (e == cudaSuccess) e = take_pinned(c, in_bytes, r->in);
@@ -1580,8 +1666,11 @@ xd_status xd_submit_batch(xd_ctx* c, const xd_batch* b, uint64_t* ticket) {
     uint32_t max_len = 0;
     if ((s = validate_host(c, b, v, &max_len)) != XD_OK) return s;
     v.max_len = max_len;
+    // the residues are packed while they are staged (the device store's layout), so the
+    // upload is a quarter (DNA) or five eighths (protein) of the codes
+    const size_t words = packed_words(b->n_codes, v.alpha);
     // admission by device memory: inputs, results and the scratch of a batch this size
-    const size_t o_offs = align_up(b->n_codes, 256);
+    const size_t o_offs = align_up(4 * words, 256);
     const size_t o_lens = o_offs + align_up(8ull * b->n_seqs, 256);
     const size_t o_pairs = o_lens + align_up(4ull * b->n_seqs, 256);
     const size_t in_bytes = o_pairs + align_up(sizeof(xd_pair) * b->n_pairs, 256);
@@ -1599,6 +1688,7 @@ xd_status xd_submit_batch(xd_ctx* c, const xd_batch* b, uint64_t* ticket) {
     r->o_lens = o_lens;
     r->o_pairs = o_pairs;
     r->in_bytes = in_bytes;
+    r->n_words = words;
     r->need = need;
     cudaError_t e = cudaSetDevice(c->device);
     if (e == cudaSuccess) e = take_pinned(c, in_bytes, r->in);
@@ -1611,15 +1701,15 @@ xd_status xd_submit_batch(xd_ctx* c, const xd_batch* b, uint64_t* ticket) {
     // when this returns
     lk.unlock();
     char* h = static_cast<char*>(r->in.p);
-    const size_t bad_block = par_copy_check(h, b->seq_codes, b->n_codes, v.alpha);
-    if (bad_block == SIZE_MAX) {
+    const bool codes_ok = par_pack_check(reinterpret_cast<uint32_t*>(h), b->seq_codes, b->n_codes, v.alpha);
+    if (codes_ok) {
         std::memcpy(h + o_offs, b->seq_offsets, 8ull * b->n_seqs);
         std::memcpy(h + o_lens, b->seq_lengths, 4ull * b->n_seqs);
         std::memcpy(h + o_pairs, b->pairs, sizeof(xd_pair) * b->n_pairs);
     }
     lk.lock();
-    if (bad_block != SIZE_MAX) {
-        size_t t = bad_block;
+    if (!codes_ok) {
+        size_t t = 0;
         while (t < b->n_codes && b->seq_codes[t] < v.alpha) t++;
         finish_request(c, r, XD_EINVAL, "");
         delete r;

@@ -207,7 +207,9 @@ def test_zdrop_workloads(ctx, zdrop):
         got = xdrop.extend_host(ctx, b)
         assert_parity(got, b)
         fired += int(((got["left"]["flags"] | got["right"]["flags"]) & 2).sum())
-    assert fired > 0
+    # every live cell is at least T - X, so no anti-diagonal drops by more than X: with
+    # Z >= X (X = 20, 49, 50 here) the rule can never end a side
+    assert fired > 0 if zdrop < 20 else fired == 0
 
 
 def test_dna_tiny_workload(ctx):
