@@ -102,7 +102,13 @@ def parse():
                     help="seconds per offered load of the serving run (0 = skip)")
     ap.add_argument("--serve-loads", default="0.25,0.5,0.9")
     ap.add_argument("--serve-inflight", type=int, default=3)
+    ap.add_argument("--serve-modes", default="continuous,per_batch,continuous_resident",
+                    help="serving modes to run (e.g. --serve 600 --serve-modes continuous for ten "
+                         "minutes per offered load)")
     ap.add_argument("--tune-table", default=None, help="tuning table written by xd_autotune")
+    ap.add_argument("--configs-tune-table", default=os.path.join(ROOT, "paper_2304_08662_gb300", "tuning", "gb300.txt"),
+                    help="tuning table under which the memory-restricted uneven batches of the configs "
+                         "record are also timed (skipped if the file does not exist)")
     ap.add_argument("--autotune", default=None, help="run xd_autotune on the workload first and write "
                                                       "the table to this path")
     ap.add_argument("--batches-per-launch", type=int, default=10,
@@ -244,10 +250,33 @@ def device_args(xdrop, torch, dev, b):
     return xdrop.BatchArgs(b.alphabet, *keep, b.match, b.mismatch, b.gap, b.matrix, b.X, b.delta)
 
 
-def config_record(xdrop, torch, ctx, dev, b, bpl, launches, oracle_pairs, peak_16, peak_32):
+def single_batch_record(xdrop, torch, ctx, dev, b, args, out, reps=3):
+    """One batch per launch on device-resident inputs: the results (after warm-up launches)
+    and the time per launch (CUDA events on the launching stream)."""
+    stream = torch.cuda.current_stream(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(reps):
+        xdrop.xd_run_device(ctx, args, out, stream.cuda_stream)
+    torch.cuda.synchronize(dev)
+    if xdrop.xd_device_status(ctx) != 0:
+        raise RuntimeError(f"device validation failed for {b.name}")
+    res = out[:b.n_pairs * xdrop.RESULT_DTYPE.itemsize].cpu().numpy().view(xdrop.RESULT_DTYPE).copy()
+    cells = float(res["left"]["cells"].sum() + res["right"]["cells"].sum())
+    ev0.record(stream)
+    for _ in range(reps):
+        xdrop.xd_run_device(ctx, args, out, stream.cuda_stream)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1) / reps
+    return res, {"ms_per_batch": ms, "gcups": cells / (ms * 1e-3) / 1e9, "pairs_per_s": b.n_pairs / (ms * 1e-3)}
+
+
+def config_record(xdrop, torch, ctx, dev, b, bpl, launches, oracle_pairs, peak_16, peak_32, tuned_ctx=None):
     """Short measurement of one workload: one batch per launch and bpl batches per launch
     (device-resident inputs, CUDA events on the launching stream), the dominant stage's
-    fraction of the integer roofline, and the oracle on a bounded sample."""
+    fraction of the integer roofline, and the oracle on a bounded sample.  With tuned_ctx
+    (a context built from a tuning table) the single-batch launch is also timed there and
+    its results must equal the default's bit for bit."""
     stream = torch.cuda.current_stream(dev)
     args = device_args(xdrop, torch, dev, b)
     out = torch.zeros(bpl * b.n_pairs * xdrop.RESULT_DTYPE.itemsize, dtype=torch.uint8, device=dev)
@@ -255,21 +284,14 @@ def config_record(xdrop, torch, ctx, dev, b, bpl, launches, oracle_pairs, peak_1
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     rec = {"pairs": b.n_pairs, "X": b.X, "delta_b": b.delta, "batches_per_launch": bpl}
     # one batch per launch
-    for _ in range(3):
-        xdrop.xd_run_device(ctx, args, out, stream.cuda_stream)
-    torch.cuda.synchronize(dev)
-    if xdrop.xd_device_status(ctx) != 0:
-        raise RuntimeError(f"device validation failed for {b.name}")
-    res = out[:b.n_pairs * xdrop.RESULT_DTYPE.itemsize].cpu().numpy().view(xdrop.RESULT_DTYPE)
+    res, rec["single_batch"] = single_batch_record(xdrop, torch, ctx, dev, b, args, out)
     cells = float(res["left"]["cells"].sum() + res["right"]["cells"].sum())
-    ev0.record(stream)
-    for _ in range(3):
-        xdrop.xd_run_device(ctx, args, out, stream.cuda_stream)
-    ev1.record(stream)
-    torch.cuda.synchronize(dev)
-    single_ms = ev0.elapsed_time(ev1) / 3
-    rec["single_batch"] = {"ms_per_batch": single_ms, "gcups": cells / (single_ms * 1e-3) / 1e9,
-                           "pairs_per_s": b.n_pairs / (single_ms * 1e-3)}
+    if tuned_ctx is not None:
+        t_res, t_rec = single_batch_record(xdrop, torch, tuned_ctx, dev, b, args, out)
+        t_rec["identical_to_default"] = bool(np.array_equal(t_res, res))
+        if not t_rec["identical_to_default"]:
+            raise RuntimeError(f"{b.name}: the tuned configuration changed the results")
+        rec["single_batch_tuned"] = t_rec
     # bpl batches per launch, timed with the stage events
     xdrop.xd_run_device_many(ctx, [args] * bpl, out, stream.cuda_stream)
     torch.cuda.synchronize(dev)
@@ -310,11 +332,13 @@ def config_record(xdrop, torch, ctx, dev, b, bpl, launches, oracle_pairs, peak_1
     return rec
 
 
-def configs_bench(xdrop, torch, ctx, dev, bpl, peak_16, peak_32, headline):
+def configs_bench(xdrop, torch, ctx, dev, bpl, peak_16, peak_32, headline, tune_table=None):
     """The other workloads, a few launches each; the headline's batch object is reused for
-    its X variants."""
+    its X variants.  With a tuning table, the memory-restricted uneven batches are also timed
+    under it (single-batch launches, the size the table was tuned at)."""
     out = {}
     uneven = None
+    tuned_ctx = xdrop.xd_create(dev.index or 0, tune_table=tune_table) if tune_table else None
     for name, kw in CONFIG_SET:
         if name == "dna_longread":
             b = headline.with_params(X=kw["X"])
@@ -328,7 +352,12 @@ def configs_bench(xdrop, torch, ctx, dev, bpl, peak_16, peak_32, headline):
         # sized to a few seconds of host work
         per = bpl if b.n_pairs <= 200_000 else max(1, bpl // 5)
         sample = {"dna_tiny": 1000, "protein": 50_000, "uneven": 5000}.get(name, 20_000)
-        out[k] = config_record(xdrop, torch, ctx, dev, b, per, 2, sample, peak_16, peak_32)
+        tc = tuned_ctx if name == "uneven" and b.delta > 0 else None
+        out[k] = config_record(xdrop, torch, ctx, dev, b, per, 2, sample, peak_16, peak_32, tuned_ctx=tc)
+        if tc is not None:
+            out[k]["tune_table"] = os.path.relpath(tune_table, ROOT)
+    if tuned_ctx is not None:
+        xdrop.xd_destroy(tuned_ctx)
     return out
 
 
@@ -377,11 +406,14 @@ def serve_run(xdrop, ctx, mix, rate_rps, duration, max_requests=None, submit=Non
             if t > duration or (max_requests and len(arrivals) >= max_requests):
                 break
         arrivals.append(t if not np.isinf(rate_rps) else 0.0)
-    reqs = [mix.next() for _ in arrivals]
+    # requests are drawn when they are sent (zero-copy views of the pools), so that runs of
+    # many minutes hold only the outstanding ones
+    n_req = len(arrivals)
+    req_pairs = [0] * n_req
     outstanding = []          # (ticket, k, out)
     lock = threading.Lock()
-    done_at = [None] * len(reqs)
-    cells = [0.0] * len(reqs)
+    done_at = [None] * n_req
+    cells = [0.0] * n_req
     submitted = threading.Event()
     errors = []
 
@@ -413,10 +445,12 @@ def serve_run(xdrop, ctx, mix, rate_rps, duration, max_requests=None, submit=Non
     th = threading.Thread(target=poller)
     th.start()
     t0 = time.perf_counter()
-    start = [0.0] * len(reqs)
-    sub_begin = [0.0] * len(reqs)
-    sub_end = [0.0] * len(reqs)
-    for k, (at, b) in enumerate(zip(arrivals, reqs)):
+    start = [0.0] * n_req
+    sub_begin = [0.0] * n_req
+    sub_end = [0.0] * n_req
+    for k, at in enumerate(arrivals):
+        b = mix.next()
+        req_pairs[k] = b.n_pairs
         now = time.perf_counter() - t0
         if at > now:
             time.sleep(at - now)
@@ -441,12 +475,12 @@ def serve_run(xdrop, ctx, mix, rate_rps, duration, max_requests=None, submit=Non
     t_end = max(done_at)
     lat = np.array([(d - s) * 1e3 for d, s in zip(done_at, start)])
     span = t_end - t0
-    pairs = sum(b.n_pairs for b in reqs)
+    pairs = sum(req_pairs)
     wait = np.array([(b_ - s_) * 1e3 for b_, s_ in zip(sub_begin, start)])
     sub = np.array([(e_ - b_) * 1e3 for e_, b_ in zip(sub_end, sub_begin)])
     run = np.array([(d - e_) * 1e3 for d, e_ in zip(done_at, sub_end)])
     pct = lambda a, q: float(np.percentile(a, q))  # noqa: E731
-    return {"requests": len(reqs), "pairs": pairs, "span_s": span,
+    return {"requests": n_req, "pairs": pairs, "span_s": span,
             "pairs_per_s": pairs / span, "gcups": sum(cells) / span / 1e9,
             "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "mean_ms": float(lat.mean()),
             "breakdown_ms": {"arrival_to_submit_p50": pct(wait, 50), "arrival_to_submit_p99": pct(wait, 99),
@@ -454,7 +488,8 @@ def serve_run(xdrop, ctx, mix, rate_rps, duration, max_requests=None, submit=Non
                              "submitted_to_done_p50": pct(run, 50), "submitted_to_done_p99": pct(run, 99)}}
 
 
-def serving_bench(xdrop, device, dna_pool, seconds, loads, inflight):
+def serving_bench(xdrop, device, dna_pool, seconds, loads, inflight,
+                  mode_names=("continuous", "per_batch", "continuous_resident")):
     """Continuous batching against one launch per request, at fractions of the peak."""
     prot_pool = synth.protein(n_pairs=200_000)
     mean_pairs = SERVE_MAX_PAIRS / np.log(SERVE_MAX_PAIRS + 1) - 0.5   # E[floor(exp(U(0, ln(N+1))))]
@@ -466,6 +501,9 @@ def serving_bench(xdrop, device, dna_pool, seconds, loads, inflight):
              "continuous_resident": dict(max_inflight=inflight, batching=1)}
     res["continuous_resident_note"] = ("the pools' reads added once to the resident sequence store; "
                                        "each request sends only its seed tuples")
+    for name in list(modes):
+        if name not in mode_names:
+            del modes[name]
     for name, kw in modes.items():
         ctx = xdrop.xd_create(device, **kw)
         try:
@@ -488,9 +526,10 @@ def serving_bench(xdrop, device, dna_pool, seconds, loads, inflight):
                       submit=submit)
             peak = serve_run(xdrop, ctx, RequestMix(dna_pool, prot_pool, 2), float("inf"), 0,
                              max_requests=240, submit=submit)
-            if name == "continuous":
+            if "peak_pairs_per_s" not in res:   # the loads are fractions of the first mode's peak
                 res["peak_pairs_per_s"] = peak["pairs_per_s"]
                 res["peak_gcups"] = peak["gcups"]
+                res["peak_mode"] = name
             out = {"saturated": peak, "loads": []}
             for ld in loads:
                 rate_pairs = ld * res["peak_pairs_per_s"]
@@ -502,6 +541,7 @@ def serving_bench(xdrop, device, dna_pool, seconds, loads, inflight):
             st = xdrop.xd_get_stats(ctx)
             out["launches"] = st["host_launches"]
             out["requests_launched"] = st["host_requests"]
+            out["launches_with_several_parameter_sets"] = st["mixed_launches"]
             res[name] = out
         finally:
             xdrop.xd_destroy(ctx)
@@ -718,7 +758,8 @@ def main():
         serving = None
         if rank == 0 and a.serve > 0 and a.workload == "dna_longread":
             loads = [float(x) for x in a.serve_loads.split(",") if x]
-            serving = serving_bench(xdrop, local, b, a.serve, loads, a.serve_inflight)
+            serving = serving_bench(xdrop, local, b, a.serve, loads, a.serve_inflight,
+                                    tuple(m for m in a.serve_modes.split(",") if m))
 
         cpu = None
         if rank == 0 and not a.no_cpu:
@@ -726,7 +767,8 @@ def main():
 
         configs = None
         if rank == 0 and not a.no_configs and a.workload == "dna_longread" and a.pairs is None and a.x is None:
-            configs = configs_bench(xdrop, torch, ctx, dev, bpl, peak16, peak32, b)
+            table = a.configs_tune_table if a.configs_tune_table and os.path.exists(a.configs_tune_table) else None
+            configs = configs_bench(xdrop, torch, ctx, dev, bpl, peak16, peak32, b, tune_table=table)
 
         if rank == 0:
             line = {"metric": "GCUPS", "value": value, "unit": "GCUPS", "n_gpus": world,

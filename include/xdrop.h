@@ -138,6 +138,7 @@ typedef struct {
     uint64_t host_requests;      /* host batches those launches ran */
     uint64_t graph_captures;     /* device-entry pipelines captured as CUDA graphs */
     uint64_t graph_replays;      /* device-entry batches run by replaying a graph */
+    uint64_t mixed_launches;     /* host launches that carried several parameter sets */
 } xd_stats;
 
 /* Create a context on cfg->device (NULL cfg = defaults).  A context plays the part of the
@@ -151,12 +152,14 @@ xd_status xd_create(const xd_config* cfg, xd_ctx** out);
  * to pinned staging memory before returning, so the caller may free its buffers at once.
  * On XD_OK *ticket identifies the batch for xd_poll.  A dispatcher thread of the context
  * launches waiting batches whenever one of the max_inflight launch slots is free; with
- * continuous batching, every waiting batch with the same scoring, X and delta_b joins that
- * launch (up to max_batch_pairs), so batches that arrive while others run share the next
- * launch.  Each batch's results are the same whether it ran alone or merged.  Launches
- * overlap on the device (copies, packing and tails of one with the extension kernel of
- * another); the fused persistent extension kernels of different launches run one after
- * another.  Errors: XD_EINVAL (codes out of the alphabet, a seed outside its sequence, X < 0,
+ * continuous batching, every waiting batch joins that launch (up to max_batch_pairs in
+ * all): batches with the same alphabet, scoring, X, delta_b and z_drop as one batch of the
+ * hot path, and up to four such parameter sets per launch (DNA and protein, several X), each
+ * set's kernels on a stream of its own so that they run side by side on the device.  So
+ * batches that arrive while others run share the next launch.  Each batch's results are the
+ * same whether it ran alone or merged.  Launches overlap on the device as well (copies and
+ * tails of one with the extension kernels of another); the fused persistent extension
+ * kernels (large DNA sets) run one after another.  Errors: XD_EINVAL (codes out of the alphabet, a seed outside its sequence, X < 0,
  * a protein batch without matrix, scores that could leave the exact integer range),
  * XD_ENOMEM (admitted but unfinished batches would exceed store_bytes_cap, or 65536 batches
  * are outstanding: nothing was queued; retry after polling), XD_EDEVICE. */
@@ -328,7 +331,8 @@ xd_status xd_probe(xd_ctx* ctx, int32_t op, double* rate);
  * the persistent grid and its role mix -- three runs each on a stream of its own, and keeps the
  * fastest for the sample's bucket: alphabet x X (<= 15, <= 30, more) x longest side
  * (<= 2,048, <= 20,000, more) x size (< 8,192, < 65,536, < 1,048,576, more side extensions
- * in one launch).  Every
+ * in one launch) x memory-restricted window (unrestricted, delta_b <= 512, <= 2,048, more;
+ * Sec. 3.3).  Every
  * candidate must reproduce the first candidate's results bit for bit, else the call fails
  * with XD_EDEVICE and keeps nothing.  The winner applies to later batches of the context;
  * if path is not NULL or empty it is also merged into the text table at path (created if

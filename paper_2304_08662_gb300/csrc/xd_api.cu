@@ -119,15 +119,28 @@ struct Request {
     std::vector<xd_result> out;
 };
 
-// An in-flight launch: one or more requests merged into one batch on the slot's stream.
+// Parameter sets (alphabet, scoring, X, delta_b, Z) one launch may carry.
+constexpr int kSlotGroups = 4;
+
+// An in-flight launch: one or more requests merged into one upload and one result copy; the
+// requests of each parameter set form one batch of the hot path (the first on the slot's
+// stream, the others on streams of their own that fork after the upload and join before
+// the result copy).
 struct Slot {
     bool busy = false;
     uint32_t n_pairs = 0;
+    int n_groups = 0;                  // parameter sets of the in-flight launch
     std::vector<Request*> reqs;
     std::vector<uint32_t> pair_base;   // first result of each request in the merged batch
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
+    cudaEvent_t uploaded = nullptr;    // created at the first launch of several sets
     Scratch s;
+    struct Side {                      // the second and later parameter sets
+        cudaStream_t stream = nullptr;
+        cudaEvent_t joined = nullptr;
+        Scratch s;
+    } side[kSlotGroups - 1];
     DevBuf d_in, d_results;
     HostBuf h_stage, h_out;
 };
@@ -288,7 +301,7 @@ struct GraphKey {
 // One tuned configuration: the register-level chain and its launch parameters for batches of
 // one alphabet, X bucket and length bucket.
 struct TuneEntry {
-    int alpha = 4, xb = 0, lb = 0, sb = 2;
+    int alpha = 4, xb = 0, lb = 0, sb = 2, db = 0;
     TierConfig cfg{};
     float ms = 0;
 };
@@ -347,7 +360,8 @@ struct xd_ctx {
     std::thread dispatcher;
     bool stop = false;
     bool stop_timed_out = false;
-    uint64_t merged_launches = 0, merged_requests = 0;
+    uint64_t merged_launches = 0, merged_requests = 0, mixed_launches = 0;
+    int mix_groups = kSlotGroups;      // parameter sets per launch (1: one set per launch)
     // the fused persistent kernel's blocks wait on one another, so two of them never run at
     // the same time: each waits for the previous one through this event
     cudaEvent_t coop_done = nullptr;
@@ -560,6 +574,7 @@ void default_tiers(xd_ctx* c) {
     t.wait_limit_ms = std::max(0, env_int("XD_TEST_WAIT_MS", 0));
     t.phantom_producer = env_int("XD_TEST_PHANTOM_PRODUCER", 0) != 0;
     t.band_warps = env_int("XD_BAND_WARPS", 8);
+    t.fused4 = env_int("XD_FUSED4", 1) != 0;
     set_chain(t, {kG1C32, kG16C16, kG32C16, kG32C32});
     // X <= 15: narrower first windows (measured at X = 10: 20 slots 195, 24 slots 184,
     // 32 slots 152 GCUPS); 20 slots up to X = 12, 24 slots up to X = 15
@@ -602,6 +617,10 @@ void default_tiers(xd_ctx* c) {
     c->tiers_huge = t;
     set_chain(c->tiers_huge, {kG1C32, kG4C32, kG8C32, kG32C32});
     c->tiers_huge.fused_minb = env_int("XD_FUSED_MINB", 3);
+    // the 32 x 32 level as a separate launch: a fourth role in the grid (XD_FUSED4_HUGE=1)
+    // measured level with it (951 - 984 against 963 GCUPS at X = 20, box noise), and the
+    // grid's own rate drops by the wide level's lower fill
+    c->tiers_huge.fused4 = env_int("XD_FUSED4_HUGE", 0) != 0 && t.fused4;
     // every warp starts in the first level (the wide sides wait for the bulk of the narrow ones;
     // the other batches of the launch cover their chains)
     c->tiers_huge.every1 = std::max(0, env_int("XD_EVERY1", 0));
@@ -621,6 +640,10 @@ void default_tiers(xd_ctx* c) {
         parse_chain(ch, c->tiers_latency_mid);
         parse_chain(ch, c->tiers_latency_prot);
     }
+    if (const char* ch = std::getenv("XD_CHAIN_HUGE")) {
+        parse_chain(ch, c->tiers_huge);
+        c->tiers_huge_small_x = c->tiers_huge_tiny_x = c->tiers_huge;
+    }
     if (const char* ch = std::getenv("XD_CHAIN")) {
         TierConfig forced = t;
         if (parse_chain(ch, forced))
@@ -631,6 +654,8 @@ void default_tiers(xd_ctx* c) {
 
 int x_bucket(int32_t X) { return X <= 15 ? 0 : X <= 30 ? 1 : 2; }
 int len_bucket(uint32_t max_len) { return max_len <= 2048 ? 0 : max_len <= 20000 ? 1 : 2; }
+// Memory-restricted window: 0 unrestricted, 1 up to 512 cells, 2 up to 2048, 3 wider.
+int delta_bucket(uint32_t delta) { return delta == 0 ? 0 : delta <= 512 ? 1 : delta <= 2048 ? 2 : 3; }
 int size_bucket(uint32_t n_pairs) {
     const uint64_t u = uint64_t(n_pairs) * 2;
     return u < 8192 ? 0 : u < kLatencyUnits ? 1 : u < kHugeUnits ? 2 : 3;
@@ -639,8 +664,9 @@ int size_bucket(uint32_t n_pairs) {
 const TierConfig& tiers_for(const xd_ctx* c, const BatchView& b) {
     if (c->force_tiers) return *c->force_tiers;
     const int xb = x_bucket(b.X), lb = len_bucket(b.max_len), sb = size_bucket(b.n_pairs);
+    const int db = delta_bucket(uint32_t(b.delta));
     for (const TuneEntry& t : c->tuned)
-        if (t.alpha == b.alpha && t.xb == xb && t.lb == lb && t.sb == sb) return t.cfg;
+        if (t.alpha == b.alpha && t.xb == xb && t.lb == lb && t.sb == sb && t.db == db) return t.cfg;
     const uint64_t units = uint64_t(b.n_pairs) * 2;
     if (units < c->latency_units) {
         if (b.alpha == 20) return c->tiers_latency_prot;
@@ -873,23 +899,46 @@ void finish_request(xd_ctx* c, Request* r, xd_status st, const std::string& msg)
     c->admitted -= std::min(c->admitted, uint64_t(r->need));
 }
 
-// Launch the oldest waiting request on a free slot, together with every later waiting
-// request of the same parameters while the merged batch stays under the size caps.
-// Called with the context lock held.
+// Launch the oldest waiting request on a free slot, together with later waiting requests
+// while the launch stays under the size caps: every request with the oldest one's
+// parameters, and requests with other parameters (another alphabet, scoring, X, delta_b or
+// Z) as further parameter sets, up to kSlotGroups sets per launch.  The launch has one
+// upload and one result copy; each parameter set is one batch of the hot path on a stream of
+// its own, so the sets' kernels run side by side on the device (fused persistent grids still
+// take turns through coop_done).  Called with the context lock held.
 void launch_merged(xd_ctx* c, Slot& slot) {
     Range range("xd.launch");
-    std::vector<Request*> take;
-    const Request* first = c->pending.front();
+    struct Group {
+        const Request* first = nullptr;
+        std::vector<Request*> reqs;
+        uint64_t words = 0, seqs = 0, pairs = 0, codes = 0;
+        uint32_t max_len = 0;
+    };
+    std::vector<Group> groups;
     uint64_t n_codes = 0, n_seqs = 0, n_pairs = 0, n_words = 0;
     for (auto it = c->pending.begin(); it != c->pending.end();) {
         Request* r = *it;
-        const bool fits = take.empty() ||
-                          (c->merge && same_params(r->v, first->v) && r->pairs_only == first->pairs_only &&
-                           n_pairs + r->v.n_pairs <= c->max_batch_pairs &&
-                           n_codes + r->v.n_codes <= c->max_batch_codes &&
-                           n_seqs + r->v.n_seqs <= 0xffffffffull);
+        int g = -1;
+        bool fits = groups.empty();
+        if (!fits && c->merge && n_pairs + r->v.n_pairs <= c->max_batch_pairs &&
+            n_codes + r->v.n_codes <= c->max_batch_codes && n_seqs + r->v.n_seqs <= 0xffffffffull) {
+            for (size_t k = 0; k < groups.size() && g < 0; k++)
+                if (same_params(r->v, groups[k].first->v) && r->pairs_only == groups[k].first->pairs_only) g = int(k);
+            fits = g >= 0 || int(groups.size()) < c->mix_groups;
+        }
         if (fits) {
-            take.push_back(r);
+            if (g < 0) {
+                groups.emplace_back();
+                groups.back().first = r;
+                g = int(groups.size()) - 1;
+            }
+            Group& G = groups[size_t(g)];
+            G.reqs.push_back(r);
+            G.words += r->n_words;
+            G.seqs += r->v.n_seqs;
+            G.pairs += r->v.n_pairs;
+            G.codes += r->v.n_codes;
+            G.max_len = std::max(G.max_len, r->v.max_len);
             n_codes += r->v.n_codes;
             n_words += r->n_words;
             n_seqs += r->v.n_seqs;
@@ -900,15 +949,12 @@ void launch_merged(xd_ctx* c, Slot& slot) {
         }
         if (!c->merge) break;
     }
-    BatchView v = first->v;
-    v.n_codes = n_codes;
-    v.n_seqs = uint32_t(n_seqs);
-    v.n_pairs = uint32_t(n_pairs);
-    v.max_len = 0;
-    for (Request* r : take) v.max_len = std::max(v.max_len, r->v.max_len);
+    // the requests in launch order: parameter set by parameter set, each set's requests in
+    // arrival order, so that every set's words, sequences and pairs are contiguous
+    std::vector<Request*> take;
+    for (const Group& G : groups) take.insert(take.end(), G.reqs.begin(), G.reqs.end());
     // the requests' packed residues one after the other (each from a word boundary), then the
     // sequence tables and the seed tuples
-    const uint64_t per_word = v.alpha == 4 ? 16 : 6;
     const size_t o_offs = align_up(4 * n_words, 256);
     const size_t o_lens = o_offs + align_up(8 * n_seqs, 256);
     const size_t o_pairs = o_lens + align_up(4 * n_seqs, 256);
@@ -926,6 +972,16 @@ void launch_merged(xd_ctx* c, Slot& slot) {
     if ((e = grow(slot.d_in, in_bytes)) != cudaSuccess) return cuda_err(e, "device input buffer");
     if ((e = grow(slot.d_results, out_bytes)) != cudaSuccess) return cuda_err(e, "device result buffer");
     if ((e = grow_pinned(slot.h_out, out_bytes)) != cudaSuccess) return cuda_err(e, "pinned result buffer");
+    for (size_t g = 1; g < groups.size(); g++) {
+        Slot::Side& sd = slot.side[g - 1];
+        if (!sd.stream && (e = cudaStreamCreateWithFlags(&sd.stream, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_err(e, "parameter-set stream");
+        if (!sd.joined && (e = cudaEventCreateWithFlags(&sd.joined, cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_err(e, "parameter-set event");
+    }
+    if (groups.size() > 1 && !slot.uploaded &&
+        (e = cudaEventCreateWithFlags(&slot.uploaded, cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_err(e, "upload event");
     char* d = static_cast<char*>(slot.d_in.p);
     if (take.size() == 1) {
         // one request: its pinned buffer already has the device layout
@@ -944,68 +1000,93 @@ void launch_merged(xd_ctx* c, Slot& slot) {
             run_a = run_b;
             return e2;
         };
-        for (Request* r : take) {
-            const char* src = static_cast<const char*>(r->in.p);
-            const size_t nb = 4 * r->n_words, at = 4 * word_base;
-            if (nb >= kGatherBelow) {
-                if ((e = flush_run()) != cudaSuccess) return cuda_err(e, "cudaMemcpyAsync");
-                e = cudaMemcpyAsync(d + at, src, nb, cudaMemcpyHostToDevice, st);
-                if (e != cudaSuccess) return cuda_err(e, "cudaMemcpyAsync");
-                run_a = run_b = at + nb;
-            } else {
-                std::memcpy(h + at, src, nb);
-                run_b = at + nb;
+        for (const Group& G : groups) {
+            // positions and sequence ids count from the parameter set's first word and sequence
+            const uint64_t per_word = G.first->v.alpha == 4 ? 16 : 6;
+            const uint64_t g_word0 = word_base, g_seq0 = seq_base;
+            for (Request* r : G.reqs) {
+                const char* src = static_cast<const char*>(r->in.p);
+                const size_t nb = 4 * r->n_words, at = 4 * word_base;
+                if (nb >= kGatherBelow) {
+                    if ((e = flush_run()) != cudaSuccess) return cuda_err(e, "cudaMemcpyAsync");
+                    e = cudaMemcpyAsync(d + at, src, nb, cudaMemcpyHostToDevice, st);
+                    if (e != cudaSuccess) return cuda_err(e, "cudaMemcpyAsync");
+                    run_a = run_b = at + nb;
+                } else {
+                    std::memcpy(h + at, src, nb);
+                    run_b = at + nb;
+                }
+                const uint64_t code_base = (word_base - g_word0) * per_word;
+                auto* offs = reinterpret_cast<uint64_t*>(h + o_offs) + seq_base;
+                const auto* r_offs = reinterpret_cast<const uint64_t*>(src + r->o_offs);
+                for (uint32_t q = 0; q < r->v.n_seqs; q++) offs[q] = r_offs[q] + code_base;
+                std::memcpy(reinterpret_cast<uint32_t*>(h + o_lens) + seq_base, src + r->o_lens, 4ull * r->v.n_seqs);
+                auto* prs = reinterpret_cast<xd_pair*>(h + o_pairs) + pair_base;
+                const auto* r_prs = reinterpret_cast<const xd_pair*>(src + r->o_pairs);
+                const uint32_t id_base = uint32_t(seq_base - g_seq0);
+                for (uint32_t q = 0; q < r->v.n_pairs; q++) {
+                    prs[q] = r_prs[q];
+                    prs[q].h_id += id_base;
+                    prs[q].v_id += id_base;
+                }
+                word_base += r->n_words;
+                seq_base += r->v.n_seqs;
+                pair_base += r->v.n_pairs;
             }
-            // residue positions of this request start at its first word
-            const uint64_t code_base = word_base * per_word;
-            auto* offs = reinterpret_cast<uint64_t*>(h + o_offs) + seq_base;
-            const auto* r_offs = reinterpret_cast<const uint64_t*>(src + r->o_offs);
-            for (uint32_t q = 0; q < r->v.n_seqs; q++) offs[q] = r_offs[q] + code_base;
-            std::memcpy(reinterpret_cast<uint32_t*>(h + o_lens) + seq_base, src + r->o_lens, 4ull * r->v.n_seqs);
-            auto* prs = reinterpret_cast<xd_pair*>(h + o_pairs) + pair_base;
-            const auto* r_prs = reinterpret_cast<const xd_pair*>(src + r->o_pairs);
-            for (uint32_t q = 0; q < r->v.n_pairs; q++) {
-                prs[q] = r_prs[q];
-                prs[q].h_id += uint32_t(seq_base);
-                prs[q].v_id += uint32_t(seq_base);
-            }
-            word_base += r->n_words;
-            seq_base += r->v.n_seqs;
-            pair_base += r->v.n_pairs;
         }
         if ((e = flush_run()) != cudaSuccess) return cuda_err(e, "cudaMemcpyAsync");
         e = cudaMemcpyAsync(d + o_offs, h + o_offs, in_bytes - o_offs, cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return cuda_err(e, "cudaMemcpyAsync");
     }
-    // packed on the host: the pipeline reads the words directly (no packing kernel)
-    v.codes = nullptr;
-    v.n_codes = 0;
-    v.packed = reinterpret_cast<const uint32_t*>(d);
-    v.packed_words = std::max<uint64_t>(1, n_words);
-    v.offsets = reinterpret_cast<const uint64_t*>(d + o_offs);
-    v.lengths = reinterpret_cast<const uint32_t*>(d + o_lens);
-    v.pairs = reinterpret_cast<const xd_pair*>(d + o_pairs);
-    if (first->pairs_only) {
-        // seed tuples on the resident store: its packed residues and tables, no upload
-        const SeqStore& ss = c->store[v.alpha == 4 ? 0 : 1];
-        v.codes = nullptr;
-        v.n_codes = 0;
-        v.packed = static_cast<const uint32_t*>(ss.words.p);
-        v.packed_words = ss.used_words;
-        v.offsets = static_cast<const uint64_t*>(ss.d_off.p);
-        v.lengths = static_cast<const uint32_t*>(ss.d_len.p);
-        v.n_seqs = uint32_t(ss.off.size());
-    }
+    if (groups.size() > 1 && (e = cudaEventRecord(slot.uploaded, st)) != cudaSuccess)
+        return cuda_err(e, "cudaEventRecord");
     auto* d_res = static_cast<xd_result*>(slot.d_results.p);
-    xd_status ps = run_pipeline(c, slot.s, v, d_res, st, c->coop_done);
-    if (ps != XD_OK) return fail_all(ps, c->err);
+    uint64_t word_base = 0, seq_base = 0, pair_base = 0;
+    for (size_t g = 0; g < groups.size(); g++) {
+        const Group& G = groups[g];
+        BatchView v = G.first->v;
+        v.n_codes = 0;
+        v.n_seqs = uint32_t(G.seqs);
+        v.n_pairs = uint32_t(G.pairs);
+        v.max_len = G.max_len;
+        // packed on the host: the pipeline reads the words directly (no packing kernel)
+        v.codes = nullptr;
+        v.packed = reinterpret_cast<const uint32_t*>(d + 4 * word_base);
+        v.packed_words = std::max<uint64_t>(1, G.words);
+        v.offsets = reinterpret_cast<const uint64_t*>(d + o_offs) + seq_base;
+        v.lengths = reinterpret_cast<const uint32_t*>(d + o_lens) + seq_base;
+        v.pairs = reinterpret_cast<const xd_pair*>(d + o_pairs) + pair_base;
+        if (G.first->pairs_only) {
+            // seed tuples on the resident store: its packed residues and tables, no upload
+            const SeqStore& ss = c->store[v.alpha == 4 ? 0 : 1];
+            v.packed = static_cast<const uint32_t*>(ss.words.p);
+            v.packed_words = ss.used_words;
+            v.offsets = static_cast<const uint64_t*>(ss.d_off.p);
+            v.lengths = static_cast<const uint32_t*>(ss.d_len.p);
+            v.n_seqs = uint32_t(ss.off.size());
+        }
+        cudaStream_t gs = g == 0 ? st : slot.side[g - 1].stream;
+        Scratch& sc = g == 0 ? slot.s : slot.side[g - 1].s;
+        if (g > 0 && (e = cudaStreamWaitEvent(gs, slot.uploaded, 0)) != cudaSuccess)
+            return cuda_err(e, "cudaStreamWaitEvent");
+        xd_status ps = run_pipeline(c, sc, v, d_res + pair_base, gs, c->coop_done);
+        if (ps != XD_OK) return fail_all(ps, c->err);
+        // the set's validation word after the results (one word per set)
+        e = cudaMemcpyAsync(static_cast<char*>(slot.h_out.p) + out_bytes - 16 + 4 * g, sc.err.p, 4,
+                            cudaMemcpyDeviceToHost, gs);
+        if (e == cudaSuccess && g > 0) e = cudaEventRecord(slot.side[g - 1].joined, gs);
+        if (e == cudaSuccess && g > 0) e = cudaStreamWaitEvent(st, slot.side[g - 1].joined, 0);
+        if (e != cudaSuccess) return cuda_err(e, "parameter-set join");
+        word_base += G.words;
+        seq_base += G.seqs;
+        pair_base += G.pairs;
+    }
     if ((e = cudaMemcpyAsync(slot.h_out.p, d_res, sizeof(xd_result) * n_pairs, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(static_cast<char*>(slot.h_out.p) + out_bytes - 16, slot.s.err.p, 4,
-                             cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
         (e = cudaEventRecord(slot.done, st)) != cudaSuccess)
         return cuda_err(e, "result copy");
     slot.busy = true;
     slot.n_pairs = uint32_t(n_pairs);
+    slot.n_groups = int(groups.size());
     slot.reqs = take;
     slot.pair_base.clear();
     uint32_t base = 0;
@@ -1016,13 +1097,18 @@ void launch_merged(xd_ctx* c, Slot& slot) {
     }
     c->merged_launches += 1;
     c->merged_requests += take.size();
+    c->mixed_launches += groups.size() > 1 ? 1 : 0;
 }
 
 // Copy a finished slot's results to its requests.  Context lock held.
 void retire_slot(xd_ctx* c, Slot& slot, cudaError_t status) {
     const size_t out_bytes = sizeof(xd_result) * size_t(slot.n_pairs) + 16;
     uint32_t flags = 0;
-    if (status == cudaSuccess) std::memcpy(&flags, static_cast<char*>(slot.h_out.p) + out_bytes - 16, 4);
+    for (int g = 0; status == cudaSuccess && g < slot.n_groups; g++) {
+        uint32_t f = 0;
+        std::memcpy(&f, static_cast<char*>(slot.h_out.p) + out_bytes - 16 + 4 * g, 4);
+        flags |= f;
+    }
     for (size_t k = 0; k < slot.reqs.size(); k++) {
         Request* r = slot.reqs[k];
         if (status != cudaSuccess) {
@@ -1091,15 +1177,16 @@ void dispatch_loop(xd_ctx* c) {
 
 // ---------------------------------------------------------------- tuning table
 
-// One line per entry:  alpha=4 xb=1 lb=1 chain=1,4,5,6 chunk=1 fused=1 every1=4 every2=16 every3=0 minb=2 ms=63.2
+// One line per entry:  alpha=4 xb=1 lb=1 sb=2 db=0 chain=1,4,5,6 chunk=1 fused=1 every1=4 every2=16 every3=0
+// minb=2 long=2 band=8 ms=63.2
 std::string format_entry(const TuneEntry& t) {
     std::string chain;
     for (int k = 0; k < t.cfg.n_levels; k++) chain += (k ? "," : "") + std::to_string(t.cfg.variant[k]);
     char buf[256];
     std::snprintf(buf, sizeof(buf),
-                  "alpha=%d xb=%d lb=%d sb=%d chain=%s chunk=%d fused=%d every1=%d every2=%d every3=%d minb=%d long=%d "
-                  "band=%d ms=%.4f",
-                  t.alpha, t.xb, t.lb, t.sb, chain.c_str(), t.cfg.chunk, t.cfg.fused ? 1 : 0, t.cfg.every1,
+                  "alpha=%d xb=%d lb=%d sb=%d db=%d chain=%s chunk=%d fused=%d every1=%d every2=%d every3=%d minb=%d "
+                  "long=%d band=%d ms=%.4f",
+                  t.alpha, t.xb, t.lb, t.sb, t.db, chain.c_str(), t.cfg.chunk, t.cfg.fused ? 1 : 0, t.cfg.every1,
                   t.cfg.every2, t.cfg.every3, t.cfg.fused_minb, t.cfg.long_permille, t.cfg.band_warps, double(t.ms));
     return buf;
 }
@@ -1137,6 +1224,7 @@ bool parse_entry(const std::string& line, const TierConfig& base, TuneEntry& out
             else if (k == "xb") out.xb = x;
             else if (k == "lb") out.lb = x;
             else if (k == "sb") out.sb = x;
+            else if (k == "db") out.db = x;
             else if (k == "chunk") out.cfg.chunk = std::max(1, std::min(x, 64));
             else if (k == "fused") out.cfg.fused = x != 0;
             else if (k == "every1") out.cfg.every1 = x == 1 ? 2 : std::max(0, x);   // 1: no warp in role 0
@@ -1150,7 +1238,8 @@ bool parse_entry(const std::string& line, const TierConfig& base, TuneEntry& out
     }
     if (!have_chain) { why = "entry without chain"; return false; }
     if (out.alpha != 4 && out.alpha != 20) { why = "alpha must be 4 or 20"; return false; }
-    if (out.xb < 0 || out.xb > 2 || out.lb < 0 || out.lb > 2 || out.sb < 0 || out.sb > 3) {
+    if (out.xb < 0 || out.xb > 2 || out.lb < 0 || out.lb > 2 || out.sb < 0 || out.sb > 3 || out.db < 0 ||
+        out.db > 3) {
         why = "bucket out of range";
         return false;
     }
@@ -1194,7 +1283,7 @@ xd_status load_table(xd_ctx* c, const char* path, std::vector<TuneEntry>& out) {
 
 void put_entry(std::vector<TuneEntry>& v, const TuneEntry& t) {
     for (TuneEntry& e : v)
-        if (e.alpha == t.alpha && e.xb == t.xb && e.lb == t.lb && e.sb == t.sb) {
+        if (e.alpha == t.alpha && e.xb == t.xb && e.lb == t.lb && e.sb == t.sb && e.db == t.db) {
             e = t;
             return;
         }
@@ -1276,6 +1365,7 @@ xd_status xd_create(const xd_config* cfg, xd_ctx** out) {
     int inflight = cfg && cfg->max_inflight > 0 ? cfg->max_inflight : 3;
     c->slots.resize(inflight);
     c->merge = !(cfg && cfg->batching < 0);
+    c->mix_groups = std::max(1, std::min(kSlotGroups, env_int("XD_MIX_GROUPS", kSlotGroups)));
     c->graphs = env_int("XD_GRAPHS", 1) != 0;
     if (cfg && cfg->max_batch_pairs) c->max_batch_pairs = cfg->max_batch_pairs;
     const char* mode = std::getenv("XD_TIERS");
@@ -1771,6 +1861,7 @@ xd_status xd_get_stats(const xd_ctx* c, xd_stats* out) {
     out->host_requests = c->merged_requests;
     out->graph_captures = c->graph_captures;
     out->graph_replays = c->graph_replays;
+    out->mixed_launches = c->mixed_launches;
     return XD_OK;
 }
 
@@ -1945,6 +2036,7 @@ xd_status xd_autotune(xd_ctx* c, const xd_batch* b, const char* path, float* bes
     best.xb = x_bucket(v.X);
     best.lb = len_bucket(v.max_len);
     best.sb = size_bucket(v.n_pairs);
+    best.db = delta_bucket(uint32_t(v.delta));
     best.cfg = base;
     best.ms = 1e30f;
     auto consider = [&](const TierConfig& cand) -> xd_status {
@@ -2005,8 +2097,9 @@ xd_status xd_autotune(xd_ctx* c, const xd_batch* b, const char* path, float* bes
         if (!f) return fail(c, XD_EINVAL, std::string("cannot write tuning table ") + path);
         std::fprintf(f, "# xdrop-gb300 tuning table: alpha (4 DNA, 20 protein), X bucket (0: X <= 15, 1: <= 30,\n"
                         "# 2: more), length bucket (0: longest side <= 2048, 1: <= 20000, 2: more), size bucket\n"
-                        "# (0: < 8192 side extensions, 1: < 65536, 2: < 1048576, 3: more), chain of register-level\n"
-                        "# variants, queue chunk, fused grid and its role mix, measured ms\n");
+                        "# (0: < 8192 side extensions, 1: < 65536, 2: < 1048576, 3: more), window bucket (0:\n"
+                        "# unrestricted, 1: delta_b <= 512, 2: <= 2048, 3: more), chain of register-level variants,\n"
+                        "# queue chunk, fused grid and its role mix, band-tier warps per side, measured ms\n");
         for (const TuneEntry& t : table) std::fprintf(f, "%s\n", format_entry(t).c_str());
         std::fclose(f);
     }
@@ -2037,6 +2130,12 @@ xd_status xd_destroy(xd_ctx* c) {
         if (s.h_out.p) cudaFreeHost(s.h_out.p);
         if (s.stream) cudaStreamDestroy(s.stream);
         if (s.done) cudaEventDestroy(s.done);
+        if (s.uploaded) cudaEventDestroy(s.uploaded);
+        for (Slot::Side& sd : s.side) {
+            release(sd.s);
+            if (sd.stream) cudaStreamDestroy(sd.stream);
+            if (sd.joined) cudaEventDestroy(sd.joined);
+        }
     }
     release(c->dev);
     release(c->stats);

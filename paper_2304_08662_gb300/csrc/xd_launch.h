@@ -58,6 +58,7 @@ struct TierConfig {
     int wait_limit_ms;                  // fused grid: live-queue wait limit (0 = default, 10 s)
     bool phantom_producer;              // failure-detection test: one producer never finishes
     int band_warps;                     // band tier: warps per side (1 - 32; 0 = default 8)
+    bool fused4;                        // a compiled four-level grid is used when the chain has one
 };
 
 // Runs register level `level` of the chain: pulls the cost-ordered list (level 0) or
@@ -77,6 +78,7 @@ cudaError_t launch_fused_levels(const Problem& P, const Queues& Q, const TierCon
 int fused_roles(const TierConfig& cfg, int alpha);
 // The fused grids with 32-slot wide levels (xd_tiers_wide.cu).
 cudaError_t launch_fused_wide(const Problem& P, const Queues& Q, const TierConfig& cfg, int n_sm, cudaStream_t st);
+cudaError_t launch_fused_wide4(const Problem& P, const Queues& Q, const TierConfig& cfg, int n_sm, cudaStream_t st);
 
 // DNA levels (xd_tiers_dna.cu) and protein instantiations (xd_tiers_prot.cu), reached
 // through the launchers above.

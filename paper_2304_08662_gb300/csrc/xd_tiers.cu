@@ -62,9 +62,10 @@ bool fused_supported(const TierConfig& c, int alpha) {
 
 // Four-role grids compiled (packed scores only).
 static bool fused4_supported(const TierConfig& c, int alpha) {
-    if (c.n_levels < 4) return false;
+    if (c.n_levels < 4 || !c.fused4) return false;
     const int a = c.variant[0], b = c.variant[1], d = c.variant[2], e = c.variant[3];
     if (alpha == 20) return a == kG4C16 && b == kG8C16 && d == kG16C16 && e == kG32C32;
+    if (a == kG1C32 && b == kG4C32 && d == kG8C32 && (e == kG16C32 || e == kG32C32 || e == kG32C16)) return true;
     return (a == kG1C32 && b == kG8C16 && d == kG16C16 && e == kG32C16) ||
            (a == kG1C24 && b == kG8C16 && d == kG16C16 && e == kG32C16) ||
            (a == kG1C20 && b == kG8C16 && d == kG16C16 && e == kG32C16) ||
@@ -86,6 +87,7 @@ static cudaError_t launch_fused4_levels(const Problem& P, const Queues& Q, const
             return launch_fused4<4, 16, 8, 16, 16, 16, 32, 32, 2, kProt16, 0, 4>(P, Q, cfg, n_sm, st);
         return cudaErrorInvalidValue;
     }
+    if (a == kG1C32 && b == kG4C32 && d == kG8C32) return launch_fused_wide4(P, Q, cfg, n_sm, st);
     if (a == kG1C32 && b == kG8C16 && d == kG16C16 && e == kG32C16)
         return launch_fused4<1, 32, 8, 16, 16, 16, 32, 16, 4, kDna16, 8, 4>(P, Q, cfg, n_sm, st);
     if (a == kG1C24 && b == kG8C16 && d == kG16C16 && e == kG32C16)

@@ -18,4 +18,17 @@ cudaError_t launch_fused_wide(const Problem& P, const Queues& Q, const TierConfi
                                : launch_fused<1, 32, 4, 32, 8, 32, 2, kDna16>(P, Q, cfg, n_sm, st);
 }
 
+// Four levels in one grid: the 32-slot wide levels, then 16 x 32, 32 x 32 or 32 x 16 as the
+// fourth role, whose sides (bands wider than 254 cells, the longest serial chains of a
+// launch) then start as soon as they escalate instead of after the grid.
+cudaError_t launch_fused_wide4(const Problem& P, const Queues& Q, const TierConfig& cfg, int n_sm, cudaStream_t st) {
+    if (!packed_ok(P) || P.alpha != 4) return cudaErrorInvalidValue;
+    switch (cfg.variant[3]) {
+        case kG16C32: return launch_fused4<1, 32, 4, 32, 8, 32, 16, 32, 3, kDna16, 0, 4>(P, Q, cfg, n_sm, st);
+        case kG32C32: return launch_fused4<1, 32, 4, 32, 8, 32, 32, 32, 3, kDna16, 0, 4>(P, Q, cfg, n_sm, st);
+        case kG32C16: return launch_fused4<1, 32, 4, 32, 8, 32, 32, 16, 3, kDna16, 0, 4>(P, Q, cfg, n_sm, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 }  // namespace xd

@@ -53,7 +53,7 @@ class xd_stats(ctypes.Structure):
                 ("units_tier", ctypes.c_uint64 * 3), ("escalations", ctypes.c_uint64),
                 ("kernel_launches", ctypes.c_uint64), ("host_launches", ctypes.c_uint64),
                 ("host_requests", ctypes.c_uint64), ("graph_captures", ctypes.c_uint64),
-                ("graph_replays", ctypes.c_uint64)]
+                ("graph_replays", ctypes.c_uint64), ("mixed_launches", ctypes.c_uint64)]
 
 
 class xd_timing(ctypes.Structure):
@@ -229,7 +229,7 @@ def xd_get_stats(ctx):
             "units_tier": list(s.units_tier), "escalations": s.escalations,
             "kernel_launches": s.kernel_launches, "host_launches": s.host_launches,
             "host_requests": s.host_requests, "graph_captures": s.graph_captures,
-            "graph_replays": s.graph_replays}
+            "graph_replays": s.graph_replays, "mixed_launches": s.mixed_launches}
 
 
 def xd_set_timing(ctx, enable=True):

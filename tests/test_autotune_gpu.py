@@ -1,8 +1,8 @@
 """Autotuner through the C ABI: tuning changes speed, never results.
 
 xd_autotune times candidate register-level configurations (lanes per side and window of
-each level, queue chunk, fused role mix) on a sample and keeps the fastest per alphabet,
-X bucket and length bucket; the table it writes is loaded by xd_create.  Every candidate
+each level, queue chunk, fused role mix, band-tier warps) on a sample and keeps the fastest
+per alphabet, X, length, size and window bucket; the table it writes is loaded by xd_create.  Every candidate
 is the same method, so the library itself checks that all candidates agree bit for bit;
 here a context built from the table must give the default context's results.
 """
@@ -74,11 +74,36 @@ def test_table_merges_buckets(tmp_path):
     assert sorted(r["xb"] for r in rows) == ["0", "2"]
 
 
+def test_table_keys_the_restricted_window(tmp_path):
+    """Memory-restricted batches (Sec. 3.3) are tuned per window bucket: the uneven batch at
+    delta_b = 256 and 4096 gives two entries, and each tuned context keeps the results."""
+    table = tmp_path / "tune.txt"
+    u = synth.uneven(n_pairs=80)
+    ctx = xdrop.xd_create(0)
+    try:
+        for d in (256, 4096, 300):      # 300 falls in the bucket of 256 and replaces its entry
+            xdrop.xd_autotune(ctx, xdrop.BatchArgs.from_host(u.with_params(delta=d)), table)
+    finally:
+        xdrop.xd_destroy(ctx)
+    rows = _entries(table)
+    assert sorted(r["db"] for r in rows) == ["1", "3"], rows
+    plain = xdrop.xd_create(0)
+    tuned = xdrop.xd_create(0, tune_table=str(table))
+    try:
+        for d in (256, 4096):
+            b = u.with_params(delta=d)
+            assert xdrop.extend_host(plain, b).tobytes() == xdrop.extend_host(tuned, b).tobytes()
+    finally:
+        xdrop.xd_destroy(plain)
+        xdrop.xd_destroy(tuned)
+
+
 def test_malformed_table_is_rejected(tmp_path):
     bad = tmp_path / "bad.txt"
-    bad.write_text("alpha=4 xb=1 lb=1 chain=1,99\n")
-    with pytest.raises(xdrop.XdError) as e:
-        xdrop.xd_create(0, tune_table=str(bad))
-    assert e.value.status == xdrop.XD_EINVAL
+    for line in ("alpha=4 xb=1 lb=1 chain=1,99\n", "alpha=4 xb=1 lb=1 db=4 chain=1,6\n"):
+        bad.write_text(line)
+        with pytest.raises(xdrop.XdError) as e:
+            xdrop.xd_create(0, tune_table=str(bad))
+        assert e.value.status == xdrop.XD_EINVAL
     with pytest.raises(xdrop.XdError):
         xdrop.xd_create(0, tune_table=str(tmp_path / "missing.txt"))

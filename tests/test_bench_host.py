@@ -104,3 +104,62 @@ def test_cpu_baseline_fields():
     assert d["kind"] == "oracle" and d["cores"] == 2 and d["unit"] == "GCUPS"
     assert d["value"] > 0 and d["value_1_core"] > 0
     assert d["sample"].startswith("40 ") and d["sample_1_core"].startswith("2 ")
+
+
+# ---- the serving loop's host side, against a fake library (no GPU)
+
+class _FakeLib:
+    """Stands in for the binding: each request finishes `delay` seconds after it is sent;
+    the first submit of every third request is refused for memory (the loop retries)."""
+    XD_OK, XD_PENDING, XD_ENOMEM = 0, 1, 3
+    RESULT_DTYPE = np.dtype([("left", [("cells", np.uint64)]), ("right", [("cells", np.uint64)])])
+
+    class XdError(Exception):
+        def __init__(self, status):
+            super().__init__(status)
+            self.status = status
+
+    def __init__(self, delay):
+        self.delay = delay
+        self.sent = {}
+        self.refused = 0
+        self.n = 0
+
+    def submit(self, b):
+        self.n += 1
+        if self.n % 3 == 0 and self.refused < self.n // 3:
+            self.refused += 1
+            raise self.XdError(self.XD_ENOMEM)
+        tk = len(self.sent) + 1
+        self.sent[tk] = (bench.time.perf_counter(), b.n_pairs)
+        return tk
+
+    def xd_poll(self, ctx, tk, out, wait_ms):
+        t, n = self.sent[tk]
+        if bench.time.perf_counter() - t < self.delay:
+            return self.XD_PENDING
+        out["left"]["cells"] = 2
+        out["right"]["cells"] = 3
+        return self.XD_OK
+
+
+class _CountingMix:
+    def __init__(self):
+        self.drawn = 0
+
+    def next(self):
+        self.drawn += 1
+        return synth.from_strings([("ACGT", "ACGT", 0, 0, 1)] * (1 + self.drawn % 4))
+
+
+@pytest.mark.parametrize("rate", [200.0, float("inf")])
+def test_serve_run_host_loop(rate):
+    lib = _FakeLib(delay=0.004)
+    mix = _CountingMix()
+    r = bench.serve_run(lib, None, mix, rate, 0.2, max_requests=40, submit=lib.submit)
+    n = r["requests"]
+    assert mix.drawn == n > 0 and lib.refused > 0
+    assert r["pairs"] == sum(1 + k % 4 for k in range(1, n + 1))
+    # every request took at least the fake's delay from its scheduled arrival
+    assert r["p50_ms"] >= 4.0 and r["p99_ms"] >= r["p50_ms"]
+    assert r["gcups"] > 0 and r["pairs_per_s"] > 0

@@ -145,7 +145,7 @@ def test_full_size_uneven_restricted_all_pairs(ctx, uneven, uneven_unrestricted,
 
 def _ctx_env(env):
     keys = ("XD_FUSED", "XD_FUSED_PROT", "XD_EVERY1", "XD_EVERY2", "XD_EVERY3", "XD_LONG_PERMILLE", "XD_CHAIN",
-            "XD_FUSED_MINB")
+            "XD_FUSED_MINB", "XD_FUSED4")
     old = {k: os.environ.get(k) for k in keys}
     for k in keys:
         os.environ.pop(k, None)
@@ -160,17 +160,23 @@ def _ctx_env(env):
                 os.environ[k] = v
 
 
-@pytest.mark.parametrize("X,chain,minb", [(10, None, None), (20, None, None), (50, None, None),
-                                          (20, "1,3,4,5,6", None), (20, "1,7,8,6", "3"), (10, "1,7,8,6", "3"),
-                                          (50, "1,7,8,6", "3")])
-def test_full_size_fused_grid_equals_level_launches(X, chain, minb):
+@pytest.mark.parametrize("X,chain,minb,roles", [(10, None, None, 4), (20, None, None, 4), (50, None, None, 4),
+                                                (20, "1,3,4,5,6", None, 4), (20, "1,7,8,6", "3", 4),
+                                                (10, "1,7,8,6", "3", 4), (50, "1,7,8,6", "3", 4),
+                                                (20, "1,7,8,6", "3", 3), (20, "1,7,8,9", "3", 4),
+                                                (20, "1,7,8,5", "3", 4)])
+def test_full_size_fused_grid_equals_level_launches(X, chain, minb, roles):
     """Every one of the 100,000 long-read pairs: the persistent grid whose warps run
     different group shapes at once (and the long-side role) must give exactly the results of
-    one launch per register level; also the four-role grid (windows 32, 128, 256, 512)."""
+    one launch per register level; also the four-role grids (windows 32, 128, 256, 512 and the
+    32-slot wide levels followed by 16 x 32, 32 x 32 or 32 x 16), and the three-role grid
+    followed by a separate launch of the fourth level."""
     b = synth.dna_longread().with_params(X=X)
     extra = {"XD_CHAIN": chain, "XD_EVERY3": "8"} if chain else {}
     if minb:
         extra["XD_FUSED_MINB"] = minb
+    if roles == 3:
+        extra["XD_FUSED4"] = "0"
     fused = _ctx_env({"XD_EVERY1": "2", "XD_EVERY2": "4", "XD_LONG_PERMILLE": "5", **extra})
     split = _ctx_env({"XD_FUSED": "0", **({"XD_CHAIN": chain} if chain else {})})
     try:

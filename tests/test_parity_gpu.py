@@ -32,11 +32,11 @@ MODES = {"tiered": {}, "generic": {"XD_TIERS": "generic"},
          "split": {"XD_LATENCY_UNITS": "0", "XD_FUSED": "0"},
          # DNA through the four-role fused grid (windows 32, 128, 256, 512)
          "four_roles": {"XD_LATENCY_UNITS": "0", "XD_CHAIN": "1,3,4,5,6", "XD_EVERY1": "16"},
-         # the chains of launches with a million or more sides (1 x 32, 4 x 32, 8 x 32 in the
-         # three-block grid, then 32 x 32), here on every batch size
-         "huge": {"XD_LATENCY_UNITS": "0", "XD_HUGE_UNITS": "0", "XD_EVERY1": "4"}}
+         # the chains of launches with a million or more sides (1 x 32, 4 x 32, 8 x 32 and
+         # 32 x 32 in the four-role three-block grid), here on every batch size
+         "huge": {"XD_LATENCY_UNITS": "0", "XD_HUGE_UNITS": "0", "XD_EVERY1": "4", "XD_EVERY3": "8"}}
 ENV_KEYS = ("XD_TIERS", "XD_FUSED", "XD_FUSED_PROT", "XD_LATENCY_UNITS", "XD_CHAIN", "XD_CHAIN_PROT",
-            "XD_CHAIN_SMALL", "XD_EVERY1", "XD_HUGE_UNITS", "XD_BAND_WARPS")
+            "XD_CHAIN_SMALL", "XD_EVERY1", "XD_EVERY3", "XD_HUGE_UNITS", "XD_BAND_WARPS")
 
 
 def _ctx(mode, env=None):

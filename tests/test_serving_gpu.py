@@ -2,8 +2,9 @@
 the mix.
 
 A request is one host batch (xd_submit_batch).  The context's dispatcher merges requests
-that wait for a launch slot and share scoring, X and delta_b into one launch, and launches
-on different slots overlap on the device.  Merging must not change any result: every
+that wait for a launch slot into one launch (those with the same parameters into one batch
+of the hot path, up to four parameter sets side by side), and launches on different slots
+overlap on the device.  Merging must not change any result: every
 field is an integer, so "the same" means bit-identical, here and against the oracle.
 """
 import threading
@@ -83,6 +84,44 @@ def test_mix_equals_alone(pools):
     # requests were merged: fewer launches than requests
     assert st["host_launches"] < len(batches), st
     assert st["host_requests"] == len(batches)
+
+
+def test_mixed_parameter_launch(pools):
+    """Requests of several parameter sets in one launch: DNA at X = 10, 20 and 50 (one with
+    Z-Drop), protein, a memory-restricted DNA request.  One slot, so the requests sent while
+    the first launch runs wait together and leave in launches of up to four sets whose
+    kernels run side by side; every result equals the request's run alone, bit for bit, and
+    a sample of them the oracle."""
+    dna, prot = pools
+    blocker = dna.pair_range(0, 2000)
+    mixed = [dna.pair_range(2000, 2100), prot.pair_range(0, 300), dna.pair_range(2100, 2150).with_params(X=10),
+             dna.pair_range(2150, 2400), prot.pair_range(300, 340), dna.pair_range(2400, 2500).with_params(X=50),
+             dna.pair_range(2500, 2600).with_params(delta=64), dna.pair_range(2600, 2700).with_params(zdrop=5),
+             prot.pair_range(340, 1340), dna.pair_range(2700, 2710).with_params(X=10)]
+    batches = [blocker] + mixed
+    ref = _alone(batches)
+    ctx = xdrop.xd_create(0, max_inflight=1)
+    try:
+        tickets = [xdrop.xd_submit_batch(ctx, xdrop.BatchArgs.from_host(b)) for b in batches]
+        got = []
+        for b, t in zip(batches, tickets):
+            out = np.zeros(b.n_pairs, dtype=xdrop.RESULT_DTYPE)
+            assert xdrop.xd_poll(ctx, t, out, -1) == xdrop.XD_OK
+            got.append(out)
+        st = xdrop.xd_get_stats(ctx)
+    finally:
+        assert xdrop.xd_destroy(ctx) == xdrop.XD_OK
+    for k, (g, r) in enumerate(zip(got, ref)):
+        _assert_same(g, r, f"request {k} ({batches[k].name}) differs in a mixed launch")
+    assert st["mixed_launches"] >= 1, st
+    assert st["host_launches"] < len(batches), st
+    for k in (1, 2, 7):
+        b = batches[k]
+        L, R, T = oracle.run_batch(b, threads=8)
+        for side, refs in (("left", L), ("right", R)):
+            for f in FIELDS:
+                assert np.array_equal(got[k][side][f], refs[f]), (b.name, side, f)
+        assert np.array_equal(got[k]["total"], T)
 
 
 def test_mix_matches_oracle(pools):
