@@ -750,7 +750,10 @@ def main():
             e2e_s = (time.perf_counter() - t0) / a.steps
             _, (e2e_s,) = job_totals(dist, dev, [0], [e2e_s])
             assert np.array_equal(hout, res), "host and device entry points disagree"
-            h2d = int(b.codes.nbytes + b.offsets.nbytes + b.lengths.nbytes + b.pairs.nbytes)
+            # what crosses to the device: the residues as packed while they are staged (2-bit
+            # DNA, 16 per word; 5-bit protein, 6 per word), the sequence table and the tuples
+            per_word = 16 if b.alphabet == "dna" else 6
+            h2d = int(4 * -(-b.codes.size // per_word) + b.offsets.nbytes + b.lengths.nbytes + b.pairs.nbytes)
             e2e = {"value": job_cells / e2e_s / 1e9, "unit": "GCUPS", "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": int(hout.nbytes), "ms_per_step": e2e_s * 1e3,
                    "in_flight": in_flight}
