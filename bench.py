@@ -82,8 +82,9 @@ def packed_scores(b):
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20,
+                    help="batches timed (in launches of --batches-per-launch)")
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="dna_longread", choices=sorted(synth.WORKLOADS))
     ap.add_argument("--x", type=int, default=None, help="X (default: the workload's)")
@@ -102,6 +103,12 @@ def parse():
                     help="seconds per offered load of the serving run (0 = skip)")
     ap.add_argument("--serve-loads", default="0.25,0.5,0.9")
     ap.add_argument("--serve-inflight", type=int, default=3)
+    ap.add_argument("--slots", type=int, default=1,
+                    help="launch slots of the main context (0: the library's default, 3); with one slot, "
+                         "host batches that wait while it runs leave together in one merged launch")
+    ap.add_argument("--e2e-inflight", type=int, default=20,
+                    help="host batches the e2e measurement keeps submitted ahead of the one it polls "
+                         "(measured: 2 -> 397, 10 -> 615-654, 20 -> 667-736 GCUPS with one slot)")
     ap.add_argument("--serve-modes", default="continuous,per_batch,continuous_resident",
                     help="serving modes to run (e.g. --serve 600 --serve-modes continuous for ten "
                          "minutes per offered load)")
@@ -597,7 +604,7 @@ def main():
 
     b = make_batch(a, rank)
     cells_paper = paper_cells(b)
-    ctx = xdrop.xd_create(local, tune_table=a.tune_table)
+    ctx = xdrop.xd_create(local, tune_table=a.tune_table, max_inflight=a.slots)
     try:
         if a.autotune:
             tuned_ms = xdrop.xd_autotune(ctx, xdrop.BatchArgs.from_host(b), a.autotune)
@@ -723,10 +730,10 @@ def main():
         if not a.no_e2e:
             hargs = xdrop.BatchArgs.from_host(b)
             hout = np.zeros(b.n_pairs, dtype=xdrop.RESULT_DTYPE)
-            # two batches in flight: the next batch's host staging and upload overlap the
-            # current one's launch (every copy stays inside the timed region); the host-side
-            # staging copy, not the device, sets this rate
-            in_flight = 2
+            # batches in flight: the next batches' host staging and upload overlap the
+            # current launch (every copy stays inside the timed region), and batches that
+            # wait together leave in one merged launch
+            in_flight = max(1, a.e2e_inflight)
 
             def e2e_pass(n):
                 pending = []
@@ -756,7 +763,7 @@ def main():
             h2d = int(4 * -(-b.codes.size // per_word) + b.offsets.nbytes + b.lengths.nbytes + b.pairs.nbytes)
             e2e = {"value": job_cells / e2e_s / 1e9, "unit": "GCUPS", "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": int(hout.nbytes), "ms_per_step": e2e_s * 1e3,
-                   "in_flight": in_flight}
+                   "in_flight": in_flight, "slots": a.slots or 3}
 
         serving = None
         if rank == 0 and a.serve > 0 and a.workload == "dna_longread":
