@@ -594,10 +594,22 @@ void default_tiers(xd_ctx* c) {
     // X = 50 on the long-read batch)
     c->tiers_large_x.fused = env_int("XD_FUSED_LARGE", 0) != 0 && t.fused;
     c->tiers_protein = t;
-    // measured on 1,000,000 protein pairs: 4 x 16 -> 8 x 16 -> 32 x 32 (268 GCUPS) ahead of
-    // 4 x 16 -> 16 x 16 -> 32 x 32 (248)
-    set_chain(c->tiers_protein, {kG4C16, kG8C16, kG32C32});
-    c->tiers_protein.fused = env_int("XD_FUSED_PROT", 0) != 0;   // separate launches measured faster
+    if (env_int("XD_FUSED_PROT", 1) != 0 && t.fused) {
+        // measured on two 1,000,000-pair protein batches per launch: the persistent grid of the
+        // 16-slot levels 4 x 16 -> 8 x 16 -> 16 x 16 (128 registers, four blocks per SM), every
+        // warp starting in the first level, then 32 x 32: 366 GCUPS against 355 for one launch
+        // per level of 4 x 16 -> 8 x 16 -> 32 x 32 (242 with one warp in 8 starting in the second
+        // level, 159 with the 32 x 32 level as a fourth role)
+        set_chain(c->tiers_protein, {kG4C16, kG8C16, kG16C16, kG32C32});
+        c->tiers_protein.fused4 = false;
+        c->tiers_protein.every1 = 0;
+        c->tiers_protein.every2 = 0;
+    } else {
+        // one launch per level: 4 x 16 -> 8 x 16 -> 32 x 32 (268 GCUPS on the 32-bit build) ahead
+        // of 4 x 16 -> 16 x 16 -> 32 x 32 (248)
+        set_chain(c->tiers_protein, {kG4C16, kG8C16, kG32C32});
+        c->tiers_protein.fused = false;
+    }
     // small batches (measured on long-read and protein batches of 1,000 - 30,000 pairs):
     // DNA below half the threshold 32 lanes x 16 slots, above it 16 x 8 first; protein 32 x 8
     c->tiers_latency = t;
@@ -1316,7 +1328,7 @@ std::vector<TierConfig> chain_candidates(const TierConfig& base, int alpha) {
                   {kG8C16, kG32C32},                  {kG1C24, kG16C16, kG32C16, kG32C32},
                   {kG1C32, kG8C16, kG16C16, kG32C16, kG32C32}};
     else
-        chains = {{kG4C16, kG16C16, kG32C32}, {kG1C16, kG4C16, kG16C16, kG32C32},
+        chains = {{kG4C16, kG16C16, kG32C32}, {kG1C16, kG4C16, kG16C16, kG32C32}, {kG4C16, kG8C16, kG16C16, kG32C32},
                   {kG8C16, kG32C16, kG32C32}, {kG4C16, kG8C16, kG32C16, kG32C32},
                   {kG32C16, kG32C32},         {kG32C8, kG32C32},
                   {kG8C8, kG32C32}};

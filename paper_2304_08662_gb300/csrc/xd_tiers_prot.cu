@@ -26,7 +26,8 @@ cudaError_t launch_level_prot(const Problem& P, const Queues& Q, int variant, in
 }
 
 bool fused_supported_prot(int a, int b, int d) {
-    return (a == kG4C16 && b == kG16C16 && d == kG32C32) || (a == kG1C16 && b == kG4C16 && d == kG16C16);
+    return (a == kG4C16 && b == kG16C16 && d == kG32C32) || (a == kG1C16 && b == kG4C16 && d == kG16C16) ||
+           (a == kG4C16 && b == kG8C16 && d == kG16C16);
 }
 
 cudaError_t launch_fused_levels_prot(const Problem& P, const Queues& Q, const TierConfig& cfg, int n_sm,
@@ -35,6 +36,8 @@ cudaError_t launch_fused_levels_prot(const Problem& P, const Queues& Q, const Ti
     if (!packed_ok(P)) return cudaErrorInvalidValue;   // protein grids are compiled packed only
     if (a == kG4C16 && b == kG16C16 && d == kG32C32) return launch_fused<4, 16, 16, 16, 32, 32, 2, kProt16>(P, Q, cfg, n_sm, st);
     if (a == kG1C16 && b == kG4C16 && d == kG16C16) return launch_fused<1, 16, 4, 16, 16, 16, 3, kProt16>(P, Q, cfg, n_sm, st);
+    // 16-slot levels only: 128 registers, four blocks per SM, like the separate level launches
+    if (a == kG4C16 && b == kG8C16 && d == kG16C16) return launch_fused<4, 16, 8, 16, 16, 16, 4, kProt16>(P, Q, cfg, n_sm, st);
     return cudaErrorInvalidValue;
 }
 

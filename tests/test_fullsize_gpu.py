@@ -145,7 +145,7 @@ def test_full_size_uneven_restricted_all_pairs(ctx, uneven, uneven_unrestricted,
 
 def _ctx_env(env):
     keys = ("XD_FUSED", "XD_FUSED_PROT", "XD_EVERY1", "XD_EVERY2", "XD_EVERY3", "XD_LONG_PERMILLE", "XD_CHAIN",
-            "XD_FUSED_MINB", "XD_FUSED4")
+            "XD_FUSED_MINB", "XD_FUSED4", "XD_CHAIN_PROT")
     old = {k: os.environ.get(k) for k in keys}
     for k in keys:
         os.environ.pop(k, None)
@@ -209,3 +209,15 @@ def test_full_size_longread_ten_batches_per_launch_all_pairs(ctx, oracle_all, X)
     ref = oracle_all(b)
     for j in range(k):
         _all_parity(res[j * b.n_pairs:(j + 1) * b.n_pairs].copy(), b, ref)
+
+
+def test_full_size_protein_fused_grid_all_pairs(oracle_all):
+    """1,000,000 protein pairs through the persistent grid of the 16-slot protein levels
+    (4 x 16 -> 8 x 16 -> 16 x 16, then 32 x 32): every pair against the oracle."""
+    b = synth.protein()
+    ctx = _ctx_env({"XD_FUSED_PROT": "1", "XD_CHAIN_PROT": "2,3,4,6", "XD_FUSED4": "0"})
+    try:
+        got = _run_device(ctx, b)
+    finally:
+        xdrop.xd_destroy(ctx)
+    _all_parity(got, b, oracle_all(b))
