@@ -47,8 +47,9 @@ def test_wait_that_runs_out_is_reported_and_context_survives():
         assert e.value.status == xdrop.XD_EDEVICE
         assert "flags 8" in str(e.value)                 # bit 3: a bounded device wait gave up
         assert time.perf_counter() - t0 < 20
-        # the same context still runs batches that do not use the fused grid
-        p = synth.protein(n_pairs=300)
+        # the same context still runs batches that do not use a fused grid (DNA at X > 30 runs
+        # one launch per register level)
+        p = synth.dna_longread(n_pairs=300).with_params(X=50)
         out = xdrop.extend_host(bad, p)
         L, R, T = oracle.run_batch(p, threads=8)
         assert np.array_equal(out["total"], T)
