@@ -624,11 +624,13 @@ void default_tiers(xd_ctx* c) {
         tc->blocks_per_sm[kG32C16] = 3;
     c->latency_units = uint32_t(std::max(0, env_int("XD_LATENCY_UNITS", int(kLatencyUnits))));
     c->huge_units = uint32_t(std::max(0, env_int("XD_HUGE_UNITS", int(kHugeUnits))));
-    // huge DNA launches: 1 x 32 -> 4 x 32 -> 8 x 32 in the three-block grid, then 32 x 32 and
+    // huge DNA launches: 1 x 32 -> 4 x 32 -> 8 x 32 in the four-block grid, then 32 x 32 and
     // the band tier (measured on ten long-read batches per launch, X = 10 and 20)
     c->tiers_huge = t;
     set_chain(c->tiers_huge, {kG1C32, kG4C32, kG8C32, kG32C32});
-    c->tiers_huge.fused_minb = env_int("XD_FUSED_MINB", 3);
+    // four blocks per SM (128 registers, 16 warps per SM): measured 1,019-1,021 GCUPS against
+    // 958-967 with three blocks (168 registers) on ten long-read batches per launch, X = 20
+    c->tiers_huge.fused_minb = env_int("XD_FUSED_MINB", 4);
     // the 32 x 32 level as a separate launch: a fourth role in the grid (XD_FUSED4_HUGE=1)
     // measured level with it (951 - 984 against 963 GCUPS at X = 20, box noise), and the
     // grid's own rate drops by the wide level's lower fill

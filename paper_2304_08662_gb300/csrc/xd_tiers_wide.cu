@@ -1,8 +1,8 @@
 // Register tiers: fused DNA grids (16-bit packed scores) whose wide levels have 32 slots per
 // lane -- 1 x 16 / 1 x 20 / 1 x 24 / 1 x 32 -> 4 x 32 -> 8 x 32 (windows 128 and 256 for the wide
 // sides, with the fewest lanes per side), and 1 x 16 -> 2 x 32 -> 8 x 32.  These are the chains of launches whose time is set by the
-// total work; they need 166-168 registers, built for three blocks per SM (and the 1 x 32 one
-// also for two).
+// total work; built for four blocks per SM (128 registers; the default of launches of 2^20 or
+// more side extensions), three (166-168 registers) and, for the 1 x 32 one, two.
 #include "xd_group.cuh"
 
 namespace xd {
@@ -12,8 +12,13 @@ cudaError_t launch_fused_wide(const Problem& P, const Queues& Q, const TierConfi
     const int a = cfg.variant[0], b = cfg.variant[1];
     if (a == kG1C16 && b == kG2C32) return launch_fused<1, 16, 2, 32, 8, 32, 3, kDna16>(P, Q, cfg, n_sm, st);
     if (a == kG1C16) return launch_fused<1, 16, 4, 32, 8, 32, 3, kDna16>(P, Q, cfg, n_sm, st);
-    if (a == kG1C20) return launch_fused<1, 20, 4, 32, 8, 32, 3, kDna16>(P, Q, cfg, n_sm, st);
-    if (a == kG1C24) return launch_fused<1, 24, 4, 32, 8, 32, 3, kDna16>(P, Q, cfg, n_sm, st);
+    if (a == kG1C20)
+        return cfg.fused_minb == 4 ? launch_fused<1, 20, 4, 32, 8, 32, 4, kDna16>(P, Q, cfg, n_sm, st)
+                                   : launch_fused<1, 20, 4, 32, 8, 32, 3, kDna16>(P, Q, cfg, n_sm, st);
+    if (a == kG1C24)
+        return cfg.fused_minb == 4 ? launch_fused<1, 24, 4, 32, 8, 32, 4, kDna16>(P, Q, cfg, n_sm, st)
+                                   : launch_fused<1, 24, 4, 32, 8, 32, 3, kDna16>(P, Q, cfg, n_sm, st);
+    if (cfg.fused_minb == 4) return launch_fused<1, 32, 4, 32, 8, 32, 4, kDna16>(P, Q, cfg, n_sm, st);
     return cfg.fused_minb == 3 ? launch_fused<1, 32, 4, 32, 8, 32, 3, kDna16>(P, Q, cfg, n_sm, st)
                                : launch_fused<1, 32, 4, 32, 8, 32, 2, kDna16>(P, Q, cfg, n_sm, st);
 }

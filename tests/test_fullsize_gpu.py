@@ -164,7 +164,8 @@ def _ctx_env(env):
                                                 (20, "1,3,4,5,6", None, 4), (20, "1,7,8,6", "3", 4),
                                                 (10, "1,7,8,6", "3", 4), (50, "1,7,8,6", "3", 4),
                                                 (20, "1,7,8,6", "3", 3), (20, "1,7,8,9", "3", 4),
-                                                (20, "1,7,8,5", "3", 4)])
+                                                (20, "1,7,8,5", "3", 4), (20, "1,7,8,6", "4", 3),
+                                                (10, "15,7,8,6", "4", 3), (20, "14,7,8,6", "4", 3)])
 def test_full_size_fused_grid_equals_level_launches(X, chain, minb, roles):
     """Every one of the 100,000 long-read pairs: the persistent grid whose warps run
     different group shapes at once (and the long-side role) must give exactly the results of
