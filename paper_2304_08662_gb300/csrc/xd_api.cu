@@ -646,7 +646,13 @@ void default_tiers(xd_ctx* c) {
     c->tiers_huge_tiny_x = c->tiers_huge;
     set_chain(c->tiers_huge_tiny_x, {kG1C20, kG4C32, kG8C32, kG32C32});
     // X > 30: the chain of large batches (measured faster than the 32-slot wide levels at X = 50)
-    c->tiers_huge_large_x = c->tiers_large_x;
+    c->tiers_huge_large_x = t;
+    // measured on ten long-read batches per launch at X = 50, one launch per level:
+    // 4 x 16 -> 8 x 32 -> 16 x 32 -> 32 x 32 (four blocks per SM for the first level) 899 GCUPS,
+    // against 708 for the chain of large batches (4 x 16 -> 16 x 16 -> 32 x 32) and 660 for the
+    // four-block wide grid of X <= 30
+    set_chain(c->tiers_huge_large_x, {kG4C16, kG8C32, kG16C32, kG32C32});
+    c->tiers_huge_large_x.fused = false;
     // overrides for experiments: comma-separated variant ids
     if (const char* ch = std::getenv("XD_CHAIN_PROT")) parse_chain(ch, c->tiers_protein);
     if (const char* ch = std::getenv("XD_CHAIN_SMALL")) {

@@ -190,7 +190,7 @@ def test_full_size_fused_grid_equals_level_launches(X, chain, minb, roles):
     assert diff.size == 0, f"{diff.size} pairs differ, first {diff[:10].tolist()}"
 
 
-@pytest.mark.parametrize("X", [10, 20])
+@pytest.mark.parametrize("X", [10, 20, 50])
 def test_full_size_longread_ten_batches_per_launch_all_pairs(ctx, oracle_all, X):
     """Ten long-read batches of 100,000 pairs in one pass (xd_run_device_many), the launch
     the bench times by default: every pair of every batch against the oracle."""
